@@ -1,0 +1,350 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: closed forms (free field,
+Abelian clover field), algebraic invariants (Clifford algebra, gamma5-hermiticity, gauge
+covariance), the paper's exact identities on dense matrices (det factorisation and the inverse
+on supp P of Sec. 1, Eq. 5, Eq. 6), its Gaussian integral and variance (Eq. 3, Eq. 4) by
+sampling, and the published known-answer vectors of Philox4x32-10.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import core as oc
+from oracle import dense as od
+from paper_1211_1214_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def g5():
+    return np.diag([1.0, 1.0, -1.0, -1.0]).astype(np.complex128)
+
+
+def apply_spin(M, v):
+    """Apply a 4x4 spin matrix to a field of shape (V, 4, 3)."""
+    return np.einsum("ab,xbc->xac", M, v)
+
+
+def coords(dims):
+    return np.stack(np.meshgrid(*[np.arange(d) for d in dims], indexing="ij"), axis=-1).reshape(-1, 4)
+
+
+# ----------------------------------------------------------------------------- gamma matrices
+
+def test_gamma_clifford_and_chiral_basis():
+    g = [oc.gamma(mu) for mu in range(4)]
+    for a in range(4):
+        assert np.allclose(g[a], g[a].conj().T)
+        for b in range(4):
+            assert np.allclose(g[a] @ g[b] + g[b] @ g[a], 2.0 * (a == b) * np.eye(4))
+    assert np.allclose(g[0] @ g[1] @ g[2] @ g[3], g5())
+
+
+# ----------------------------------------------------------------------------- Philox
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        out = oc.philox4x32_10(v[0:4], v[4:6])
+        assert list(out) == v[6:10]
+
+
+def test_noise_moments():
+    """E eta = 0, E eta^2 = 0, E|eta|^2 = 1: the measure of Eq. 3 normalised to one."""
+    eta = oc.noise_packed(seed=2, hit0=0, nhit=4, n=50000).reshape(-1)
+    n = eta.size
+    assert abs(np.mean(eta)) < 5 / np.sqrt(n)
+    assert abs(np.mean(eta * eta)) < 5 / np.sqrt(n)
+    assert abs(np.mean(np.abs(eta) ** 2) - 1.0) < 5 / np.sqrt(n)
+    # the real part is N(0, 1/2): fourth moment 3/4
+    assert abs(np.mean(eta.real ** 4) - 0.75) < 10 * np.sqrt(105 / 16 - 9 / 16) / np.sqrt(n)
+
+
+# ----------------------------------------------------------------------------- free field
+
+@pytest.mark.parametrize("antiperiodic", [False, True])
+def test_free_field_plane_wave(antiperiodic):
+    """U = 1: D e^{ipx} chi = [m + sum_mu (1 - cos p_mu) + i sum_mu g_mu sin p_mu] e^{ipx} chi."""
+    dims = (6, 4, 2, 8)
+    V = int(np.prod(dims))
+    U = np.broadcast_to(np.eye(3, dtype=np.complex128), (V, 4, 3, 3)).copy()
+    lat = oc.Lattice(dims, (2, 2, 2, 2), U, csw=1.7, antiperiodic_t=antiperiodic)
+    X = coords(dims)
+    rng = np.random.default_rng(5)
+    g = [oc.gamma(mu) for mu in range(4)]
+    m = 0.13
+    for n in [(0, 0, 0, 0), (1, 0, 1, 3), (2, 3, 1, 5), (5, 1, 0, 7)]:
+        p = np.array([2 * np.pi * n[mu] / dims[mu] for mu in range(4)])
+        if antiperiodic:
+            p[0] += np.pi / dims[0]
+        chi = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+        phase = np.exp(1j * X @ p)
+        psi = phase[:, None, None] * chi[None]
+        Dp = (m + np.sum(1 - np.cos(p))) * np.eye(4) + 1j * sum(g[mu] * np.sin(p[mu]) for mu in range(4))
+        want = phase[:, None, None] * (Dp @ chi)[None]
+        got = lat.apply(m, psi)
+        assert np.max(np.abs(got - want)) < 1e-13
+
+
+def test_free_field_spectrum_multiplicity():
+    """Dense spectrum at U = 1: m + sum(1 - cos p) +- i sqrt(sum sin^2 p), each 6-fold per momentum."""
+    dims = (4, 2, 2, 4)
+    V = int(np.prod(dims))
+    U = np.broadcast_to(np.eye(3, dtype=np.complex128), (V, 4, 3, 3)).copy()
+    lat = oc.Lattice(dims, (2, 2, 2, 2), U, csw=1.0)
+    m = 0.07
+    ev = np.linalg.eigvals(od.dense_D(lat, m))
+    want = []
+    for n in np.ndindex(*dims):
+        p = 2 * np.pi * np.array(n) / np.array(dims)
+        re = m + np.sum(1 - np.cos(p))
+        im = np.sqrt(np.sum(np.sin(p) ** 2))
+        want += [re + 1j * im] * 6 + [re - 1j * im] * 6
+    want = np.array(want)
+    key = lambda z: np.lexsort((np.round(z.imag, 9), np.round(z.real, 9)))
+    assert np.allclose(np.sort_complex(np.round(ev, 9)), np.sort_complex(np.round(want, 9)), atol=1e-8)
+
+
+# ----------------------------------------------------------------------------- clover term
+
+@pytest.mark.parametrize("plane", [(0, 1), (1, 3), (2, 0)])
+def test_clover_abelian_constant_field(plane):
+    """Constant Abelian field: every leaf is e^{i phi q}, so Fhat_{mu nu} = i sin(phi q) and
+    C = -(csw/2) sigma_{mu nu} (x) diag(sin(phi q_a)) at every site."""
+    mu, nu = plane
+    dims = (4, 6, 4, 8)
+    V = int(np.prod(dims))
+    X = coords(dims)
+    q = np.array([1.0, -2.0, 1.0])
+    phi = 2 * np.pi * 1 / (dims[mu] * dims[nu])
+    U = np.broadcast_to(np.eye(3, dtype=np.complex128), (V, 4, 3, 3)).copy()
+    for a in range(3):
+        U[:, nu, a, a] = np.exp(1j * phi * q[a] * X[:, mu])
+        last = X[:, mu] == dims[mu] - 1
+        U[last, mu, a, a] = np.exp(-1j * phi * q[a] * dims[mu] * X[last, nu])
+    csw = 1.3
+    lat = oc.Lattice(dims, (2, 2, 2, 2), U, csw=csw)
+    g = [oc.gamma(k) for k in range(4)]
+    sigma = 0.5j * (g[mu] @ g[nu] - g[nu] @ g[mu])
+    want = -(csw / 2) * np.kron(sigma, np.diag(np.sin(phi * q)))
+    for x in [0, 17, V // 2 + 3, V - 1]:
+        assert np.max(np.abs(lat.clover(x) - want)) < 1e-13
+
+
+def test_clover_hermitian_commutes_gamma5_and_vanishes_at_unit_links():
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, seed=1)
+    lat = oc.Lattice(dims, (2, 2, 2, 2), U, csw=1.0)
+    G5 = np.kron(g5(), np.eye(3))
+    for x in [0, 5, 100, 255]:
+        C = lat.clover(x)
+        assert np.max(np.abs(C - C.conj().T)) < 1e-14
+        assert np.max(np.abs(G5 @ C - C @ G5)) < 1e-14
+        assert np.max(np.abs(C)) > 1e-3
+    V = 256
+    lat1 = oc.Lattice(dims, (2, 2, 2, 2), np.broadcast_to(np.eye(3), (V, 4, 3, 3)).astype(np.complex128), csw=1.0)
+    assert np.max(np.abs(lat1.clover(7))) == 0.0
+
+
+# ----------------------------------------------------------------------------- invariants at random U
+
+@pytest.fixture(scope="module")
+def c1():
+    """4^4 lattice, blocks 2^4, eps = 0.3, seed 1, csw = 1.0, m1 = 0.20, m2 = 0.19."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, seed=1)
+    return oc.Lattice(dims, (2, 2, 2, 2), U, csw=1.0)
+
+
+def test_gamma5_hermiticity(c1):
+    """<x, g5 D g5 y> = <D x, y>, with D^dag written out independently in the oracle."""
+    x = synth.spinor_field(c1.dims, seed=11)
+    y = synth.spinor_field(c1.dims, seed=12)
+    m = 0.2
+    lhs = np.vdot(x, apply_spin(g5(), c1.apply(m, apply_spin(g5(), y))))
+    rhs = np.vdot(c1.apply(m, x), y)
+    assert abs(lhs - rhs) < 1e-13 * abs(rhs)
+    # the adjoint the oracle applies equals g5 D g5
+    assert np.max(np.abs(c1.apply(m, y, dagger=True) - apply_spin(g5(), c1.apply(m, apply_spin(g5(), y))))) < 1e-13
+
+
+def test_gauge_covariance():
+    """D[U^g] (g psi) = g D[U] psi with U^g_mu(x) = g(x) U_mu(x) g(x+mu)^dag."""
+    dims = (4, 4, 2, 6)
+    V = int(np.prod(dims))
+    U = synth.gauge_field(dims, 0.4, seed=3)
+    g = synth.gauge_transform(dims, seed=4)
+    X = coords(dims)
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        Y = X.copy()
+        Y[:, mu] = (Y[:, mu] + 1) % dims[mu]
+        ym = ((Y[:, 0] * dims[1] + Y[:, 1]) * dims[2] + Y[:, 2]) * dims[3] + Y[:, 3]
+        Ug[:, mu] = g @ U[:, mu] @ g[ym].conj().transpose(0, 2, 1)
+    lat = oc.Lattice(dims, (2, 2, 2, 2), U, csw=1.4)
+    latg = oc.Lattice(dims, (2, 2, 2, 2), Ug, csw=1.4)
+    psi = synth.spinor_field(dims, seed=9)
+    gpsi = np.einsum("xab,xsb->xsa", g, psi)
+    lhs = latg.apply(0.1, gpsi)
+    rhs = np.einsum("xab,xsb->xsa", g, lat.apply(0.1, psi))
+    assert np.max(np.abs(lhs - rhs)) < 1e-13
+
+
+# ----------------------------------------------------------------------------- block structure (Eq. 1, Sec. 1)
+
+def test_blocks_are_block_diagonal(c1):
+    """D_bb couples only sites of the same black block; D_bw only sites of neighbouring blocks."""
+    D = od.dense_D(c1, 0.2)
+    X = coords(c1.dims)
+    blk = ((X[:, 0] // 2 * 2 + X[:, 1] // 2) * 2 + X[:, 2] // 2) * 2 + X[:, 3] // 2
+    col = c1.colour()
+    assert np.all(col == (X // 2).sum(axis=1) % 2)
+    nz = np.abs(D.reshape(c1.V, 12, c1.V, 12)).max(axis=(1, 3)) > 0
+    i, j = np.nonzero(nz)
+    same_colour = col[i] == col[j]
+    assert np.all(blk[i][same_colour] == blk[j][same_colour])
+    # 4^4 with 2^4 blocks: supp P is every black site (P = all black sites)
+    assert np.all(c1.suppP() == (col == 0))
+
+
+def test_det_factorisation(c1):
+    """det D = det Dhat det D_ww det D_bb (Sec. 1), and det D is real (gamma5-hermiticity)."""
+    for m in (0.2, 0.19, -0.3):
+        D = od.dense_D(c1, m)
+        Dbb, Dbw, Dwb, Dww = od.blocks(c1, m)
+        s, ld = od.logdet(D)
+        s1, l1 = od.logdet(od.schur(c1, m))
+        s2, l2 = od.logdet(Dbb)
+        s3, l3 = od.logdet(Dww)
+        assert abs(ld - (l1 + l2 + l3)) < 1e-9 * abs(ld)
+        assert abs(s - s1 * s2 * s3) < 1e-8
+        assert abs(s.imag) < 1e-8
+
+
+def test_schur_inverse_on_supp_P():
+    """On supp P: (P Dhat P)^-1 = P (1 - Dcal_bw D_wb) P and det(P Dhat P) = det Dhat (Sec. 1)."""
+    # blocks 4x4x2x2 (one block in y and z, which wrap onto themselves): sites with t and x
+    # inside the block have no white neighbour, so supp P is a proper subset of the black sites
+    dims = (8, 8, 2, 2)
+    U = synth.gauge_field(dims, 0.3, seed=7)
+    lat = oc.Lattice(dims, (4, 4, 2, 2), U, csw=1.2)
+    b, w, p = od.component_sets(lat)
+    assert 0 < len(p) < len(b)
+    m = 0.15
+    D = od.dense_D(lat, m)
+    Dinv = np.linalg.inv(D)
+    Dcal_bw = Dinv[np.ix_(b, w)]
+    Dwb = D[np.ix_(w, b)]
+    # D_wb P = D_wb: columns of D_wb outside supp P vanish
+    pos = np.searchsorted(b, p)
+    outside = np.setdiff1d(np.arange(len(b)), pos)
+    assert np.max(np.abs(Dwb[:, outside])) == 0.0
+    S = od.schur(lat, m)
+    A = S[np.ix_(pos, pos)]
+    want = (np.eye(len(b)) - Dcal_bw @ Dwb)[np.ix_(pos, pos)]
+    assert np.max(np.abs(np.linalg.inv(A) - want)) < 1e-10
+    assert abs(od.logdet(A)[1] - od.logdet(S)[1]) < 1e-9
+
+
+def test_even_odd_is_the_l1_case():
+    """Blocks of length 1 give the even-odd Schur complement: D_bb is site-diagonal on even sites."""
+    dims = (4, 2, 2, 4)
+    U = synth.gauge_field(dims, 0.3, seed=2)
+    lat = oc.Lattice(dims, (1, 1, 1, 1), U, csw=1.0)
+    X = coords(dims)
+    assert np.all(lat.colour() == X.sum(axis=1) % 2)
+    Dbb, _, _, _ = od.blocks(lat, 0.1)
+    nb = Dbb.shape[0] // 12
+    R = Dbb.reshape(nb, 12, nb, 12)
+    off = R.copy()
+    for k in range(nb):
+        off[k, :, k, :] = 0
+    assert np.max(np.abs(off)) == 0.0
+    assert np.all(lat.suppP() == (lat.colour() == 0))
+
+
+# ----------------------------------------------------------------------------- mass structure (Eq. 5, Eq. 6)
+
+def test_mass_shift_spectrum(c1):
+    """D(m1) - D(m2) = dm; lambda(M) = 1 + dm/lambda(D(m2)); det M^-1 = prod lambda/(lambda + dm)."""
+    m1, m2 = 0.20, 0.19
+    dm = m1 - m2
+    D1, D2 = od.dense_D(c1, m1), od.dense_D(c1, m2)
+    assert np.max(np.abs(D1 - D2 - dm * np.eye(D1.shape[0]))) < 1e-15
+    lam = np.linalg.eigvals(D2)
+    M = np.linalg.solve(D2, D1)
+    lamM = np.linalg.eigvals(M)
+    want = 1 + dm / lam
+    # match each eigenvalue of M to the prediction
+    d = np.abs(lamM[:, None] - want[None, :]).min(axis=1)
+    assert d.max() < 1e-9
+    s, ldM = np.linalg.slogdet(M)
+    assert abs(-ldM - np.sum(np.log(np.abs(lam / (lam + dm))))) < 1e-9
+
+
+# ----------------------------------------------------------------------------- solver and estimator
+
+def test_cgnr_block_solve_matches_dense(c1):
+    D = od.dense_D(c1, 0.19)
+    b_idx, w_idx, _ = od.component_sets(c1)
+    rhs = synth.spinor_field(c1.dims, seed=21)
+    col = c1.colour()
+    rhs[col == 1] = 0
+    x, it, rel = c1.solve(0.19, rhs, sel=oc.BLACK, tol=1e-13)
+    assert rel <= 1e-13
+    want = np.linalg.solve(D[np.ix_(b_idx, b_idx)], rhs.reshape(-1)[b_idx])
+    assert np.max(np.abs(x.reshape(-1)[b_idx] - want)) < 1e-11 * np.max(np.abs(want))
+    assert np.max(np.abs(x[col == 1])) == 0.0
+
+
+def test_exponent_matches_dense(c1):
+    """Oracle e_j (five CGNR solves, resolvent form of r) against eta^dag (Mh^dag Mh - 1) eta."""
+    m1, m2 = 0.20, 0.19
+    Mh = od.ratio_matrix(c1, m1, m2)
+    A1, A2 = od.schur_on_P(c1, m1), od.schur_on_P(c1, m2)
+    n = Mh.shape[0]
+    eta_p = oc.noise_packed(seed=2, hit0=0, nhit=3, n=n)
+    for j in range(3):
+        res = c1.exponent(m1, m2, c1.unpack(eta_p[j]))
+        e_dense = od.exponent(Mh, eta_p[j])[0]
+        assert abs(res["e"] - e_dense) < 1e-10 * max(abs(e_dense), 1.0)
+        r_dense = (A1 - A2) @ eta_p[j]
+        assert np.max(np.abs(c1.pack(res["r"]) - r_dense)) < 1e-11 * np.max(np.abs(r_dense))
+        d_dense = Mh @ eta_p[j] - eta_p[j]
+        assert np.max(np.abs(c1.pack(res["delta"]) - d_dense)) < 1e-10 * np.max(np.abs(d_dense))
+
+
+def test_zero_mass_shift_gives_zero_exponent(c1):
+    eta_p = oc.noise_packed(seed=3, hit0=0, nhit=1, n=len(c1.suppP_sites()) * 12)[0]
+    res = c1.exponent(0.2, 0.2, c1.unpack(eta_p))
+    assert res["e"] == 0.0
+    assert np.max(np.abs(res["r"])) == 0.0
+
+
+def test_estimator_mean_and_variance():
+    """Eq. 3: mean of exp(-e_j) -> 1/det(Mh^dag Mh); Eq. 4: its variance, by sampling the
+    oracle's own Philox noise (a wrong noise normalisation or exponent fails both)."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, seed=1)
+    lat = oc.Lattice(dims, (2, 2, 2, 2), U, csw=1.0)
+    m1, m2 = 0.20, 0.15
+    Mh = od.ratio_matrix(lat, m1, m2)
+    W = od.inv_det_MdagM(Mh)
+    var = od.stochastic_variance(Mh)
+    ns = 12000
+    eta = oc.noise_packed(seed=77, hit0=0, nhit=ns, n=Mh.shape[0])
+    e = od.exponent(Mh, eta)
+    w = np.exp(-e)
+    # the test is sensitive: a noise of the wrong variance moves the mean by many standard errors
+    assert abs(np.log(W)) > 20 * np.sqrt(var / ns) / W
+    assert abs(w.mean() - W) < 4 * np.sqrt(var / ns)
+    # sample variance against Eq. 4 (fourth moment finite for this spectrum; 25% slack)
+    assert abs(w.var() / var - 1) < 0.25
+    # the oracle's C estimator agrees with the dense exponent on a few of these samples
+    for j in range(2):
+        res = lat.exponent(m1, m2, lat.unpack(eta[j]))
+        assert abs(res["e"] - e[j]) < 1e-10 * max(abs(e[j]), 1.0)
