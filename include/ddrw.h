@@ -1,0 +1,149 @@
+/*
+ * ddrw.h -- C ABI of the GB300 library for the domain-decomposed stochastic estimate of fermion
+ * determinant ratios (Finkenrath, Knechtli, Leder, "Application of Domain Decomposition to the
+ * Evaluation of Fermion Determinant Ratios", Lattice 2012).
+ *
+ * What the library computes (all references are to that paper):
+ *
+ *   D(m)     the O(a)-improved Wilson-clover Dirac operator (Sec. 1, Sec. 2), in the form
+ *            D(m) = (4 + m) + C - 1/2 sum_mu [(1 - g_mu) U_mu(x) T_+mu + (1 + g_mu) U_mu(x-mu)^dag T_-mu],
+ *            C = csw (i/4) sum_{mu nu} sigma_{mu nu} Fhat_{mu nu}; the mass enters additively so that
+ *            M = D^-1(m2) D(m1) = 1 + dm D^-1(m2) with dm = m1 - m2 (Eq. 2, Eq. 6);
+ *   blocks   the lattice is cut into hypercubic blocks of length l, coloured black/white like a
+ *            checkerboard (block 0 black); D = [[D_bb, D_bw], [D_wb, D_ww]] (Eq. 1);
+ *   Dhat     the Schur complement 1 - D_bb^-1 D_bw D_ww^-1 D_wb, restricted to the support of the
+ *            projector P with D_wb P = D_wb (Sec. 1): A(m) = P Dhat(m) P;
+ *   estimate 1/det(Mh^dag Mh) ~ (1/N_hit) sum_j exp(-eta_j^dag (Mh^dag Mh - 1) eta_j) with
+ *            Mh = A(m2)^-1 A(m1) and complex Gaussian eta_j (Eq. 3, Eq. 8 with N = 1).
+ *
+ * Conventions at the boundary
+ *   - dims = {T, X, Y, Z}; lexicographic site index ((t*X + x)*Y + y)*Z + z.
+ *   - gauge field: double U[V][4][3][3][2] (complex, row-major 3x3, mu = t, x, y, z), SU(3) links.
+ *   - spinor field: double psi[nrhs][V][4][3][2]; spins in the chiral basis (g5 = diag(1,1,-1,-1),
+ *     g0 = [[0,-1],[-1,0]], g_k = [[0,-i s_k],[i s_k,0]] in 2x2 spin blocks).
+ *   - packed supp-P vector: double v[nrhs][n_P][4][3][2], the supp-P sites (black sites with a
+ *     neighbour in a white block) in ascending lexicographic order; n_P from ddrw_suppP_size().
+ *   - Pointers may be host or device memory: the library asks the CUDA runtime which one each
+ *     pointer is.  Host buffers are staged through the context's device workspace.
+ *   - The caller owns every buffer it passes; the library never frees or keeps them.  The context
+ *     owns its internal copies of the gauge field and clover term and its workspaces.
+ *   - Every call is stream-ordered on the context's stream and returns when its results are in
+ *     the output buffers (the call synchronises the stream before returning).
+ *
+ * Errors: every call returns a ddrw_status; no call aborts or exits.  A message for the last
+ * error of a context is available from ddrw_last_error().  A call that fails leaves its outputs
+ * unspecified unless stated otherwise.
+ */
+#ifndef DDRW_H
+#define DDRW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ddrw_ctx ddrw_ctx;
+
+typedef enum {
+    DDRW_OK = 0,
+    DDRW_EINVAL = 1,    /* bad argument: null pointer, bad size, unsupported geometry */
+    DDRW_ENOMEM = 2,    /* device allocation failed */
+    DDRW_ECUDA = 3,     /* a CUDA call failed (message names it) */
+    DDRW_ENOCONV = 4,   /* a solver hit its iteration cap; outputs hold the last iterate */
+    DDRW_ENUMERIC = 5,  /* NaN or Inf in a reduction */
+    DDRW_EDOMAIN = 6,   /* the estimate is outside its domain of definition */
+    DDRW_ESTATE = 7     /* call out of order (e.g. no gauge field loaded) */
+} ddrw_status;
+
+typedef enum {
+    DDRW_FP64 = 0,       /* every kernel in FP64 */
+    DDRW_MIXED_FP32 = 1, /* inner solves in FP32 storage and arithmetic, FP64 defect correction */
+    DDRW_MIXED_FP16 = 2  /* inner solves in FP16 storage, FP32 arithmetic, FP64 defect correction */
+} ddrw_prec;
+
+typedef enum { DDRW_BLACK = 0, DDRW_WHITE = 1, DDRW_ALL = 2 } ddrw_colour;
+
+typedef struct {
+    int iters_outer;          /* outer Krylov iterations (summed over defect-correction cycles) */
+    int cycles;               /* defect-correction cycles (1 for the FP64 path) */
+    int fp64_dslash_calls;    /* full-lattice FP64 operator applications */
+    int block_iters_max;      /* largest iteration count of any block solve */
+    double true_rel_residual; /* max over right-hand sides of ||b - D x|| / ||b||, recomputed in FP64 */
+    double seconds;           /* wall time of the call */
+} ddrw_solve_info;
+
+/* Create a context on CUDA device `device` for a T x X x Y x Z lattice cut into hypercubic blocks
+ * of length block[0] = block[1] = block[2] = block[3] = l (Eq. 1; Sec. 2 uses 6^4 and 8^4 blocks).
+ * l must be 2, 4, 6 or 8, divide every dimension, and leave an even number (>= 2) of blocks in
+ * each direction, so that neighbouring blocks always have opposite colours.  cuda_stream is a
+ * cudaStream_t (NULL: the context creates its own).  DDRW_EINVAL on a bad geometry. */
+ddrw_status ddrw_create(ddrw_ctx **out, const int dims[4], const int block[4], int device, void *cuda_stream);
+void ddrw_destroy(ddrw_ctx *ctx);
+const char *ddrw_last_error(const ddrw_ctx *ctx);
+
+/* Sites of supp P (black sites with a neighbour in a white block, Sec. 1), and the volume. */
+ddrw_status ddrw_suppP_size(ddrw_ctx *ctx, long *n_sites);
+ddrw_status ddrw_volume(ddrw_ctx *ctx, long *n_sites);
+
+/* Load the gauge field U[V][4][3][3][2] (host or device); builds the clover term with the csw of
+ * the last ddrw_set_params() (csw = 0 before it).  The field is copied; the caller keeps U. */
+ddrw_status ddrw_load_gauge(ddrw_ctx *ctx, const double *U);
+
+/* csw (clover coefficient), m1 (ensemble mass) and m2 (target mass) of W(U, m1, m2) (Eq. 2),
+ * and the time boundary condition of the quark fields (0 periodic, 1 antiperiodic).  Rebuilds the
+ * clover term and the per-mass inverses of the site-diagonal part. */
+ddrw_status ddrw_set_params(ddrw_ctx *ctx, double csw, double m1, double m2, int antiperiodic_t);
+
+/* Solver settings: precision of the inner solves, relative true-residual target of the outer
+ * (full-lattice) solve (default 1e-10), relative residual target of the block solves (default
+ * 1e-13), and the iteration cap of every solver (default 20000). */
+ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, double tol_block, int maxiter);
+
+/* out = D(m) in for nrhs full-lattice spinor fields, in FP64. */
+ddrw_status ddrw_apply_D(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs);
+
+/* out = D_{rows,cols}(m) in: the block of Eq. 1 with rows in colour `rows` and columns in colour
+ * `cols` (DDRW_BLACK, DDRW_WHITE or DDRW_ALL); rows outside `rows` are set to zero.  D_bb and
+ * D_ww are the block-diagonal block operators, D_bw and D_wb the hops between blocks. */
+ddrw_status ddrw_apply_block(ddrw_ctx *ctx, int rows, int cols, double m, const double *in, double *out, int nrhs);
+
+/* x = D_cc(m)^-1 b for colour c = DDRW_BLACK or DDRW_WHITE: all blocks of the colour are solved
+ * in one persistent kernel, each block to relative residual tol_block.  b and x are full-lattice
+ * fields; only the sites of colour c are read and written (x is zero elsewhere). */
+ddrw_status ddrw_solve_block(ddrw_ctx *ctx, int colour, double m, const double *b, double *x, int nrhs,
+                             ddrw_solve_info *info);
+
+/* x = D(m)^-1 b for full-lattice fields, to the outer tolerance. */
+ddrw_status ddrw_solve_D(ddrw_ctx *ctx, double m, const double *b, double *x, int nrhs, ddrw_solve_info *info);
+
+/* out = A(m) in with A(m) = P Dhat(m) P (Sec. 1), on packed supp-P vectors. */
+ddrw_status ddrw_apply_schur(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs);
+
+/* r = (A(m1) - A(m2)) eta on packed supp-P vectors, in the resolvent form
+ * r = dm P D_bb(m1)^-1 [D_bw a12 + D_bb(m2)^-1 D_bw a2], u = D_wb eta, a2 = D_ww(m2)^-1 u,
+ * a12 = D_ww(m1)^-1 a2 (no cancellation between the two masses). */
+ddrw_status ddrw_apply_dA(ddrw_ctx *ctx, const double *eta, double *r, int nrhs, ddrw_solve_info *info);
+
+/* x = A(m)^-1 b on packed supp-P vectors: one full-lattice solve D(m) y = (0_b ; D_wb b) and
+ * x = b - P y_b, from Dhat^-1 = 1 - P Dcal_bw D_wb (Sec. 1). */
+ddrw_status ddrw_solve_schur(ddrw_ctx *ctx, double m, const double *b, double *x, int nrhs, ddrw_solve_info *info);
+
+/* nhit packed complex Gaussian noise vectors with E|eta_k|^2 = 1 (Eq. 3): component k of hit h
+ * from Philox4x32-10 with counter (k, hit_offset + h, 0, 0) and key (seed mod 2^32, seed >> 32),
+ * u1 = (w0 + 1) 2^-32, u2 = w1 2^-32, eta_k = sqrt(-ln u1) exp(2 pi i u2). */
+ddrw_status ddrw_noise(ddrw_ctx *ctx, uint64_t seed, uint64_t hit_offset, int nhit, double *eta);
+
+/* The stochastic estimate of Eq. 3 / Eq. 8 (N = 1) for the Schur complement: for each of nhit
+ * noise vectors (from ddrw_noise(seed, hit_offset) when eta == NULL, else the caller's packed
+ * vectors) exponents[j] = eta_j^dag (Mh^dag Mh - 1) eta_j = ||delta_j||^2 + 2 Re <eta_j, delta_j>
+ * with delta_j = A(m2)^-1 (A(m1) - A(m2)) eta_j.  *logW = log((1/nhit) sum_j exp(-e_j)) (FP64
+ * log-sum-exp) and *rel_var = sample variance of exp(-e_j) / W^2 (both optional).  delta (optional,
+ * packed) receives the delta_j.  DDRW_ENOCONV if a solve missed its tolerance (outputs filled). */
+ddrw_status ddrw_estimate(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64_t hit_offset, const double *eta,
+                          double *exponents, double *logW, double *rel_var, double *delta, ddrw_solve_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDRW_H */

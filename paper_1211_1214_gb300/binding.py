@@ -1,0 +1,201 @@
+"""Python binding of the C ABI in ``include/ddrw.h`` (argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/libddrw.so``; this module only converts
+arrays to pointers and status codes to exceptions.  Arrays may be torch tensors (CUDA or CPU) or
+numpy arrays, of dtype complex128 or float64 (interleaved re, im), C-contiguous.  If the library
+is missing, loading fails with an error: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FP64, MIXED_FP32, MIXED_FP16 = 0, 1, 2
+BLACK, WHITE, ALL = 0, 1, 2
+
+_STATUS = {0: "DDRW_OK", 1: "DDRW_EINVAL", 2: "DDRW_ENOMEM", 3: "DDRW_ECUDA", 4: "DDRW_ENOCONV",
+           5: "DDRW_ENUMERIC", 6: "DDRW_EDOMAIN", 7: "DDRW_ESTATE"}
+
+#: every entry point declared in include/ddrw.h
+EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", "ddrw_volume", "ddrw_load_gauge",
+           "ddrw_set_params", "ddrw_set_solver", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
+           "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate"]
+
+
+class DDRWError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters_outer", ctypes.c_int), ("cycles", ctypes.c_int), ("fp64_dslash_calls", ctypes.c_int),
+                ("block_iters_max", ctypes.c_int), ("true_rel_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (build it first with ``paper_1211_1214_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is not built; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)
+    st = ctypes.c_int
+    sig = {
+        "ddrw_create": (st, [ctypes.POINTER(vp), ip, ip, ctypes.c_int, vp]),
+        "ddrw_destroy": (None, [vp]),
+        "ddrw_last_error": (ctypes.c_char_p, [vp]),
+        "ddrw_suppP_size": (st, [vp, ctypes.POINTER(ctypes.c_long)]),
+        "ddrw_volume": (st, [vp, ctypes.POINTER(ctypes.c_long)]),
+        "ddrw_load_gauge": (st, [vp, dp]),
+        "ddrw_set_params": (st, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+        "ddrw_set_solver": (st, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+        "ddrw_apply_D": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
+        "ddrw_apply_block": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int]),
+        "ddrw_solve_block": (st, [vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
+        "ddrw_solve_D": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
+        "ddrw_apply_schur": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
+        "ddrw_apply_dA": (st, [vp, dp, dp, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
+        "ddrw_solve_schur": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
+        "ddrw_noise": (st, [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, dp]),
+        "ddrw_estimate": (st, [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp, dp, dp, dp,
+                               ctypes.POINTER(SolveInfo)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Data pointer of a contiguous complex128/float64 torch tensor or numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if str(a.dtype) not in ("torch.complex128", "torch.float64"):
+            raise ValueError("tensor must be complex128 or float64")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if a.dtype not in (np.complex128, np.float64):
+            raise ValueError("array must be complex128 or float64")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class Context:
+    """One ``ddrw_ctx``: a lattice with its blocks on one GPU.  Methods mirror the C calls."""
+
+    def __init__(self, dims, block, device: int = 0, stream: int | None = None):
+        self.L = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.block = tuple(int(b) for b in (block if hasattr(block, "__len__") else [block] * 4))
+        h = ctypes.c_void_p()
+        st = self.L.ddrw_create(ctypes.byref(h), (ctypes.c_int * 4)(*self.dims), (ctypes.c_int * 4)(*self.block),
+                                int(device), ctypes.c_void_p(stream) if stream else None)
+        if st != 0:
+            raise DDRWError(st, f"ddrw_create(dims={self.dims}, block={self.block})")
+        self._h = h
+        n = ctypes.c_long()
+        self.L.ddrw_suppP_size(self._h, ctypes.byref(n))
+        self.nP = n.value
+        self.L.ddrw_volume(self._h, ctypes.byref(n))
+        self.V = n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.L.ddrw_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.L.ddrw_last_error(self._h)
+            raise DDRWError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def load_gauge(self, U):
+        self._check(self.L.ddrw_load_gauge(self._h, _ptr(U)), "ddrw_load_gauge")
+
+    def set_params(self, csw, m1, m2, antiperiodic_t=False):
+        self._check(self.L.ddrw_set_params(self._h, float(csw), float(m1), float(m2), int(antiperiodic_t)),
+                    "ddrw_set_params")
+
+    def set_solver(self, prec=FP64, tol_outer=1e-10, tol_block=1e-13, maxiter=20000):
+        self._check(self.L.ddrw_set_solver(self._h, int(prec), float(tol_outer), float(tol_block), int(maxiter)),
+                    "ddrw_set_solver")
+
+    def apply_D(self, m, x, out, nrhs=1):
+        self._check(self.L.ddrw_apply_D(self._h, float(m), _ptr(x), _ptr(out), int(nrhs)), "ddrw_apply_D")
+
+    def apply_block(self, rows, cols, m, x, out, nrhs=1):
+        self._check(self.L.ddrw_apply_block(self._h, int(rows), int(cols), float(m), _ptr(x), _ptr(out), int(nrhs)),
+                    "ddrw_apply_block")
+
+    def solve_block(self, colour, m, b, x, nrhs=1):
+        info = SolveInfo()
+        st = self.L.ddrw_solve_block(self._h, int(colour), float(m), _ptr(b), _ptr(x), int(nrhs), ctypes.byref(info))
+        self._check(st, "ddrw_solve_block")
+        return info.as_dict()
+
+    def solve_D(self, m, b, x, nrhs=1):
+        info = SolveInfo()
+        st = self.L.ddrw_solve_D(self._h, float(m), _ptr(b), _ptr(x), int(nrhs), ctypes.byref(info))
+        self._check(st, "ddrw_solve_D")
+        return info.as_dict()
+
+    def apply_schur(self, m, x, out, nrhs=1):
+        self._check(self.L.ddrw_apply_schur(self._h, float(m), _ptr(x), _ptr(out), int(nrhs)), "ddrw_apply_schur")
+
+    def apply_dA(self, eta, r, nrhs=1):
+        info = SolveInfo()
+        self._check(self.L.ddrw_apply_dA(self._h, _ptr(eta), _ptr(r), int(nrhs), ctypes.byref(info)), "ddrw_apply_dA")
+        return info.as_dict()
+
+    def solve_schur(self, m, b, x, nrhs=1):
+        info = SolveInfo()
+        st = self.L.ddrw_solve_schur(self._h, float(m), _ptr(b), _ptr(x), int(nrhs), ctypes.byref(info))
+        self._check(st, "ddrw_solve_schur")
+        return info.as_dict()
+
+    def noise(self, seed, hit_offset, nhit, eta):
+        self._check(self.L.ddrw_noise(self._h, ctypes.c_uint64(seed), ctypes.c_uint64(hit_offset), int(nhit),
+                                      _ptr(eta)), "ddrw_noise")
+
+    def estimate(self, nhit, seed=2, hit_offset=0, eta=None, delta=None):
+        """Returns (exponents as numpy float64 array, logW, rel_var, solve info dict)."""
+        e = np.zeros(nhit, dtype=np.float64)
+        lw = np.zeros(1, dtype=np.float64)
+        rv = np.zeros(1, dtype=np.float64)
+        info = SolveInfo()
+        st = self.L.ddrw_estimate(self._h, int(nhit), ctypes.c_uint64(seed), ctypes.c_uint64(hit_offset), _ptr(eta),
+                                  _ptr(e), _ptr(lw), _ptr(rv), _ptr(delta), ctypes.byref(info))
+        self._check(st, "ddrw_estimate")
+        return e, float(lw[0]), float(rv[0]), info.as_dict()

@@ -1,0 +1,453 @@
+// api.cu -- the C ABI (include/ddrw.h): context, geometry tables, parameters, operator
+// applications.  Solvers and the estimate live in solver.cu and estimate.cu.
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+
+#include "ctx.h"
+
+namespace ddrw {
+
+ddrw_status set_error(ddrw_ctx *ctx, ddrw_status st, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+ddrw_status set_cuda_error(ddrw_ctx *ctx, cudaError_t e, const char *what, const char *file, int line)
+{
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    return set_error(ctx, e == cudaErrorMemoryAllocation ? DDRW_ENOMEM : DDRW_ECUDA, buf);
+}
+
+ddrw_status workspace(ddrw_ctx *ctx, const char *name, size_t bytes, void **out)
+{
+    DevBuf &b = ctx->ws[name];
+    if (b.bytes < bytes) {
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        cudaError_t e = cudaMalloc(&b.p, bytes);
+        if (e != cudaSuccess) {
+            b.p = nullptr;
+            return set_cuda_error(ctx, e, "cudaMalloc(workspace)", __FILE__, __LINE__);
+        }
+        b.bytes = bytes;
+    }
+    *out = b.p;
+    return DDRW_OK;
+}
+
+GeomDev geom_dev(const ddrw_ctx *ctx)
+{
+    GeomDev g;
+    for (int mu = 0; mu < 4; mu++) {
+        g.L[mu] = ctx->dims[mu];
+        g.NB[mu] = ctx->NB[mu];
+    }
+    g.nblk = ctx->nblk;
+    g.nblk_c = ctx->nblk_c;
+    g.vh = ctx->vh;
+    g.V = ctx->V;
+    g.blk_nb = ctx->d_blk_nb;
+    g.blk_org = ctx->d_blk_org;
+    g.blk_index = ctx->d_blk_index;
+    g.tsign = ctx->antiperiodic ? -1 : 1;
+    return g;
+}
+
+ddrw_status mass_inverse(ddrw_ctx *ctx, double m, MassInv **out)
+{
+    for (auto &mi : ctx->inv)
+        if (mi.m == m) {
+            *out = &mi;
+            return DDRW_OK;
+        }
+    MassInv mi;
+    mi.m = m;
+    DDRW_CUDA_CHECK(cudaMalloc(&mi.A64, sizeof(double2) * 36 * (size_t)ctx->V));
+    cudaError_t e = cudaMalloc(&mi.A32, sizeof(float4) * 18 * (size_t)ctx->V);
+    if (e != cudaSuccess) {
+        cudaFree(mi.A64);
+        return set_cuda_error(ctx, e, "cudaMalloc(A32)", __FILE__, __LINE__);
+    }
+    build_inverse(ctx, m, mi);
+    DDRW_CUDA_CHECK(cudaGetLastError());
+    ctx->inv.push_back(mi);
+    *out = &ctx->inv.back();
+    return DDRW_OK;
+}
+
+static void free_inverses(ddrw_ctx *ctx)
+{
+    for (auto &mi : ctx->inv) {
+        cudaFree(mi.A64);
+        cudaFree(mi.A32);
+    }
+    ctx->inv.clear();
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+ddrw_status stage_in(ddrw_ctx *ctx, const void *user, size_t bytes, const char *name, const void **dev)
+{
+    if (is_device_ptr(user)) {
+        *dev = user;
+        return DDRW_OK;
+    }
+    void *p;
+    ddrw_status st = workspace(ctx, name, bytes, &p);
+    if (st) return st;
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(p, user, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    *dev = p;
+    return DDRW_OK;
+}
+
+ddrw_status stage_out(ddrw_ctx *ctx, void *user, size_t bytes, const char *name, void **dev, bool *host)
+{
+    if (is_device_ptr(user)) {
+        *dev = user;
+        *host = false;
+        return DDRW_OK;
+    }
+    *host = true;
+    return workspace(ctx, name, bytes, dev);
+}
+
+ddrw_status finish_out(ddrw_ctx *ctx, void *user, const void *dev, size_t bytes, bool host)
+{
+    if (host) DDRW_CUDA_CHECK(cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    return DDRW_OK;
+}
+
+ddrw_status sync(ddrw_ctx *ctx)
+{
+    DDRW_CUDA_CHECK(cudaGetLastError());
+    DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    return DDRW_OK;
+}
+
+// internal index from global coordinates (host mirror of the device function)
+long host_internal_index(const ddrw_ctx *ctx, const std::vector<int> &blk_index, const int *x)
+{
+    int l = ctx->l;
+    int b[4], c[4];
+    for (int mu = 0; mu < 4; mu++) {
+        b[mu] = x[mu] / l;
+        c[mu] = x[mu] - b[mu] * l;
+    }
+    int B = ((b[0] * ctx->NB[1] + b[1]) * ctx->NB[2] + b[2]) * ctx->NB[3] + b[3];
+    int lb = ((c[0] * l + c[1]) * l + c[2]) * l + c[3];
+    int p = (x[0] + x[1] + x[2] + x[3]) & 1;
+    long vbh = (long)l * l * l * l / 2;
+    return (long)p * ctx->vh + (long)blk_index[B] * vbh + (lb >> 1);
+}
+
+// zero the sites of one colour (both parities) in nrhs FP64 fields
+__global__ void k_zero_colour(double2 *f, long V, long vh, long lo, long n, int nrhs)
+{
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long per = 2 * n;  // both parities
+    if (i >= per * 12 * nrhs) return;
+    long r = i / (per * 12);
+    long rem = i - r * per * 12;
+    long k = rem / per;
+    long j = rem - k * per;
+    long p = j / n;
+    long s = p * vh + lo + (j - p * n);
+    f[(r * 12 + k) * V + s] = make_double2(0.0, 0.0);
+}
+
+void zero_colour64(ddrw_ctx *ctx, double2 *f, int colour, int nrhs)
+{
+    long vbh = (long)ctx->l * ctx->l * ctx->l * ctx->l / 2;
+    long n = (long)ctx->nblk_c * vbh;
+    long lo = colour == DDRW_BLACK ? 0 : n;
+    long tot = 2 * n * 12 * nrhs;
+    k_zero_colour<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(f, ctx->V, ctx->vh, lo, n, nrhs);
+}
+
+}  // namespace ddrw
+
+using namespace ddrw;
+
+extern "C" {
+
+ddrw_status ddrw_create(ddrw_ctx **out, const int dims[4], const int block[4], int device, void *cuda_stream)
+{
+    if (!out || !dims || !block) return DDRW_EINVAL;
+    *out = nullptr;
+    int l = block[0];
+    for (int mu = 0; mu < 4; mu++) {
+        if (block[mu] != l) return DDRW_EINVAL;
+        if (dims[mu] <= 0 || dims[mu] % l) return DDRW_EINVAL;
+        int nb = dims[mu] / l;
+        if (nb < 2 || nb % 2) return DDRW_EINVAL;
+    }
+    if (l != 2 && l != 4 && l != 6 && l != 8) return DDRW_EINVAL;
+    ddrw_ctx *ctx = new ddrw_ctx();
+    ctx->l = l;
+    ctx->V = 1;
+    for (int mu = 0; mu < 4; mu++) {
+        ctx->dims[mu] = dims[mu];
+        ctx->NB[mu] = dims[mu] / l;
+        ctx->V *= dims[mu];
+    }
+    if (ctx->V > (1L << 30)) {
+        delete ctx;
+        return DDRW_EINVAL;
+    }
+    ctx->vh = ctx->V / 2;
+    ctx->nblk = ctx->NB[0] * ctx->NB[1] * ctx->NB[2] * ctx->NB[3];
+    ctx->nblk_c = ctx->nblk / 2;
+    ctx->device = device;
+    auto fail = [&](ddrw_status st) {
+        ddrw_destroy(ctx);
+        return st;
+    };
+    if (cudaSetDevice(device) != cudaSuccess) return fail(DDRW_ECUDA);
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(DDRW_ECUDA);
+        ctx->own_stream = true;
+    }
+
+    // block tables: colour-major numbering, black blocks first
+    int nb = ctx->nblk;
+    std::vector<int> number(nb), org(4 * nb), nbr(8 * nb);
+    int nblack = 0, nwhite = 0;
+    for (int B = 0; B < nb; B++) {
+        int r = B, c[4];
+        for (int mu = 3; mu >= 0; mu--) {
+            c[mu] = r % ctx->NB[mu];
+            r /= ctx->NB[mu];
+        }
+        int colour = (c[0] + c[1] + c[2] + c[3]) & 1;
+        number[B] = colour == 0 ? nblack++ : ctx->nblk_c + nwhite++;
+    }
+    if (nblack != ctx->nblk_c || nwhite != ctx->nblk_c) return fail(DDRW_EINVAL);
+    for (int B = 0; B < nb; B++) {
+        int r = B, c[4];
+        for (int mu = 3; mu >= 0; mu--) {
+            c[mu] = r % ctx->NB[mu];
+            r /= ctx->NB[mu];
+        }
+        int k = number[B];
+        for (int mu = 0; mu < 4; mu++) org[4 * k + mu] = c[mu] * l;
+        for (int mu = 0; mu < 4; mu++)
+            for (int d = 0; d < 2; d++) {
+                int cc[4] = {c[0], c[1], c[2], c[3]};
+                cc[mu] = (cc[mu] + (d == 0 ? 1 : -1) + ctx->NB[mu]) % ctx->NB[mu];
+                int B2 = ((cc[0] * ctx->NB[1] + cc[1]) * ctx->NB[2] + cc[2]) * ctx->NB[3] + cc[3];
+                nbr[8 * k + 2 * mu + d] = number[B2];
+            }
+    }
+    // supp P: black sites on a block face (the neighbouring block across any face is white)
+    std::vector<int> suppP;
+    for (long x = 0; x < ctx->V; x++) {
+        long r = x;
+        int c[4];
+        for (int mu = 3; mu >= 0; mu--) {
+            c[mu] = (int)(r % dims[mu]);
+            r /= dims[mu];
+        }
+        int colour = (c[0] / l + c[1] / l + c[2] / l + c[3] / l) & 1;
+        if (colour) continue;
+        bool face = false;
+        for (int mu = 0; mu < 4; mu++) {
+            int cm = c[mu] % l;
+            if (cm == 0 || cm == l - 1) face = true;
+        }
+        if (face) suppP.push_back((int)host_internal_index(ctx, number, c));
+    }
+    ctx->nP = (long)suppP.size();
+    if (cudaMalloc(&ctx->d_blk_nb, sizeof(int) * 8 * nb) != cudaSuccess ||
+        cudaMalloc(&ctx->d_blk_org, sizeof(int) * 4 * nb) != cudaSuccess ||
+        cudaMalloc(&ctx->d_blk_index, sizeof(int) * nb) != cudaSuccess ||
+        cudaMalloc(&ctx->d_suppP, sizeof(int) * (suppP.size() + 1)) != cudaSuccess)
+        return fail(DDRW_ENOMEM);
+    cudaMemcpy(ctx->d_blk_nb, nbr.data(), sizeof(int) * 8 * nb, cudaMemcpyHostToDevice);
+    cudaMemcpy(ctx->d_blk_org, org.data(), sizeof(int) * 4 * nb, cudaMemcpyHostToDevice);
+    cudaMemcpy(ctx->d_blk_index, number.data(), sizeof(int) * nb, cudaMemcpyHostToDevice);
+    if (!suppP.empty()) cudaMemcpy(ctx->d_suppP, suppP.data(), sizeof(int) * suppP.size(), cudaMemcpyHostToDevice);
+
+    size_t V = ctx->V;
+    if (cudaMalloc(&ctx->U64, sizeof(double2) * 36 * V) != cudaSuccess ||
+        cudaMalloc(&ctx->U32, sizeof(float4) * 12 * V) != cudaSuccess ||
+        cudaMalloc(&ctx->C64, sizeof(double2) * 36 * V) != cudaSuccess ||
+        cudaMalloc(&ctx->C32, sizeof(float4) * 18 * V) != cudaSuccess)
+        return fail(DDRW_ENOMEM);
+    if (cudaMallocHost(&ctx->h_pinned, 1 << 20) != cudaSuccess) return fail(DDRW_ENOMEM);
+    ctx->h_pinned_bytes = 1 << 20;
+    if (cudaGetLastError() != cudaSuccess) return fail(DDRW_ECUDA);
+    *out = ctx;
+    return DDRW_OK;
+}
+
+void ddrw_destroy(ddrw_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->d_blk_nb);
+    cudaFree(ctx->d_blk_org);
+    cudaFree(ctx->d_blk_index);
+    cudaFree(ctx->d_suppP);
+    cudaFree(ctx->U64);
+    cudaFree(ctx->U32);
+    cudaFree(ctx->C64);
+    cudaFree(ctx->C32);
+    free_inverses(ctx);
+    for (auto &kv : ctx->ws) cudaFree(kv.second.p);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *ddrw_last_error(const ddrw_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+ddrw_status ddrw_suppP_size(ddrw_ctx *ctx, long *n)
+{
+    if (!ctx || !n) return DDRW_EINVAL;
+    *n = ctx->nP;
+    return DDRW_OK;
+}
+
+ddrw_status ddrw_volume(ddrw_ctx *ctx, long *n)
+{
+    if (!ctx || !n) return DDRW_EINVAL;
+    *n = ctx->V;
+    return DDRW_OK;
+}
+
+static ddrw_status rebuild(ddrw_ctx *ctx)
+{
+    build_clover(ctx);
+    DDRW_CUDA_CHECK(cudaGetLastError());
+    free_inverses(ctx);
+    MassInv *mi;
+    ddrw_status st = mass_inverse(ctx, ctx->m1, &mi);
+    if (st) return st;
+    if (ctx->m2 != ctx->m1) st = mass_inverse(ctx, ctx->m2, &mi);
+    if (st) return st;
+    return sync(ctx);
+}
+
+ddrw_status ddrw_load_gauge(ddrw_ctx *ctx, const double *U)
+{
+    if (!ctx || !U) return set_error(ctx, DDRW_EINVAL, "null argument");
+    cudaSetDevice(ctx->device);
+    const void *dU;
+    ddrw_status st = stage_in(ctx, U, sizeof(double) * 72 * (size_t)ctx->V, "stage_gauge", &dU);
+    if (st) return st;
+    pack_gauge(ctx, (const double *)dU);
+    DDRW_CUDA_CHECK(cudaGetLastError());
+    ctx->have_gauge = true;
+    st = rebuild(ctx);
+    // the staging buffer for the gauge field is large and used once: release it
+    auto it = ctx->ws.find("stage_gauge");
+    if (it != ctx->ws.end()) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(it->second.p);
+        ctx->ws.erase(it);
+    }
+    return st;
+}
+
+ddrw_status ddrw_set_params(ddrw_ctx *ctx, double csw, double m1, double m2, int antiperiodic_t)
+{
+    if (!ctx) return DDRW_EINVAL;
+    if (!(csw == csw) || !(m1 == m1) || !(m2 == m2)) return set_error(ctx, DDRW_EINVAL, "NaN parameter");
+    cudaSetDevice(ctx->device);
+    ctx->csw = csw;
+    ctx->m1 = m1;
+    ctx->m2 = m2;
+    ctx->antiperiodic = antiperiodic_t ? 1 : 0;
+    if (!ctx->have_gauge) return DDRW_OK;
+    return rebuild(ctx);
+}
+
+ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, double tol_block, int maxiter)
+{
+    if (!ctx) return DDRW_EINVAL;
+    if (prec < DDRW_FP64 || prec > DDRW_MIXED_FP16) return set_error(ctx, DDRW_EINVAL, "unknown precision");
+    if (!(tol_outer > 0) || !(tol_block > 0) || maxiter <= 0) return set_error(ctx, DDRW_EINVAL, "bad tolerance");
+    ctx->prec = prec;
+    ctx->tol_outer = tol_outer;
+    ctx->tol_block = tol_block;
+    ctx->maxiter = maxiter;
+    return DDRW_OK;
+}
+
+ddrw_status ddrw_apply_block(ddrw_ctx *ctx, int rows, int cols, double m, const double *in, double *out, int nrhs)
+{
+    if (!ctx || !in || !out || nrhs <= 0) return set_error(ctx, DDRW_EINVAL, "bad argument");
+    if (rows < 0 || rows > 2 || cols < 0 || cols > 2) return set_error(ctx, DDRW_EINVAL, "bad colour");
+    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
+    cudaSetDevice(ctx->device);
+    size_t ubytes = sizeof(double) * 24 * (size_t)ctx->V * nrhs;
+    size_t fbytes = sizeof(double2) * 12 * (size_t)ctx->V * nrhs;
+    const void *din;
+    void *dout;
+    bool host_out;
+    double2 *fin, *fout;
+    ddrw_status st;
+    if ((st = stage_in(ctx, in, ubytes, "stage_in", &din))) return st;
+    if ((st = stage_out(ctx, out, ubytes, "stage_out", &dout, &host_out))) return st;
+    if ((st = workspace(ctx, "api_f0", fbytes, (void **)&fin))) return st;
+    if ((st = workspace(ctx, "api_f1", fbytes, (void **)&fout))) return st;
+    pack_spinor64(ctx, (const double *)din, fin, nrhs);
+
+    DslashCall c;
+    c.in = fin;
+    c.x = fin;
+    c.out = fout;
+    c.rstride = 12 * ctx->V;
+    c.nrhs = nrhs;
+    c.mass = m;
+    c.alpha = 1.0;
+    c.beta = -0.5;
+    c.par0 = 0;
+    c.npar = 2;
+    if (rows != DDRW_ALL && cols != DDRW_ALL) {
+        DDRW_CUDA_CHECK(cudaMemsetAsync(fout, 0, fbytes, ctx->stream));
+        c.blk0 = rows == DDRW_BLACK ? 0 : ctx->nblk_c;
+        c.nblk = ctx->nblk_c;
+        if (rows == cols) {
+            c.diag = 1;
+            c.hopsel = 1;
+        } else {
+            c.diag = 0;
+            c.hopsel = 2;
+        }
+        dslash64(ctx, c);
+    } else {
+        if (cols != DDRW_ALL) zero_colour64(ctx, fin, 1 - cols, nrhs);
+        c.diag = 1;
+        c.hopsel = 0;
+        c.blk0 = 0;
+        c.nblk = ctx->nblk;
+        dslash64(ctx, c);
+        if (rows != DDRW_ALL) zero_colour64(ctx, fout, 1 - rows, nrhs);
+    }
+    unpack_spinor64(ctx, fout, (double *)dout, nrhs);
+    if ((st = finish_out(ctx, out, dout, ubytes, host_out))) return st;
+    return sync(ctx);
+}
+
+ddrw_status ddrw_apply_D(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs)
+{
+    return ddrw_apply_block(ctx, DDRW_ALL, DDRW_ALL, m, in, out, nrhs);
+}
+
+}  // extern "C"

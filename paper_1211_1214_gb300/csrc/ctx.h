@@ -1,0 +1,119 @@
+// ctx.h -- the library context (host side) and helpers shared by the .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ddrw.h"
+#include "ddrw_internal.cuh"
+
+namespace ddrw {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Per-mass inverse of the site-diagonal part A(m) = (4 + m) + C, in every storage precision.
+struct MassInv {
+    double m;
+    double2 *A64 = nullptr;  // [2][18][V]
+    float4 *A32 = nullptr;   // [2][9][V]
+};
+
+}  // namespace ddrw
+
+struct ddrw_ctx {
+    // geometry
+    int dims[4];
+    int l;
+    int NB[4];
+    long V, vh;
+    int nblk, nblk_c;
+    int *d_blk_nb = nullptr, *d_blk_org = nullptr, *d_blk_index = nullptr;
+    long nP = 0;
+    int *d_suppP = nullptr;  // internal site index of the k-th supp-P site (lexicographic order)
+
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    // parameters
+    double csw = 0.0, m1 = 0.0, m2 = 0.0;
+    int antiperiodic = 0;
+    bool have_gauge = false;
+    ddrw_prec prec = DDRW_FP64;
+    double tol_outer = 1e-10, tol_block = 1e-13;
+    int maxiter = 20000;
+
+    // resident fields
+    double2 *U64 = nullptr;  // [4][9][V]
+    float4 *U32 = nullptr;   // [4][3][V] two-row
+    double2 *C64 = nullptr;  // [2][18][V]
+    float4 *C32 = nullptr;   // [2][9][V]
+    std::vector<ddrw::MassInv> inv;
+
+    // workspaces by name (grow-only)
+    std::map<std::string, ddrw::DevBuf> ws;
+    double *h_pinned = nullptr;  // small pinned host buffer for scalars
+    size_t h_pinned_bytes = 0;
+
+    std::string err;
+};
+
+namespace ddrw {
+
+ddrw_status set_error(ddrw_ctx *ctx, ddrw_status st, const std::string &msg);
+ddrw_status set_cuda_error(ddrw_ctx *ctx, cudaError_t e, const char *what, const char *file, int line);
+
+// device workspace of at least `bytes`, reused across calls under `name`
+ddrw_status workspace(ddrw_ctx *ctx, const char *name, size_t bytes, void **out);
+
+GeomDev geom_dev(const ddrw_ctx *ctx);
+
+// mass-dependent inverse of A(m), built on first use
+ddrw_status mass_inverse(ddrw_ctx *ctx, double m, MassInv **out);
+
+// host/device staging of caller buffers (see the pointer rules of include/ddrw.h)
+bool is_device_ptr(const void *p);
+ddrw_status stage_in(ddrw_ctx *ctx, const void *user, size_t bytes, const char *name, const void **dev);
+ddrw_status stage_out(ddrw_ctx *ctx, void *user, size_t bytes, const char *name, void **dev, bool *host);
+ddrw_status finish_out(ddrw_ctx *ctx, void *user, const void *dev, size_t bytes, bool host);
+ddrw_status sync(ddrw_ctx *ctx);
+void zero_colour64(ddrw_ctx *ctx, double2 *f, int colour, int nrhs);
+
+// ---- launchers (all on ctx->stream)
+// Full-lattice FP64 fields: element (rhs r, plane k, site s) at f[r * 12 V + k * V + s].
+void pack_spinor64(ddrw_ctx *ctx, const double *user, double2 *f, int nrhs);
+void unpack_spinor64(ddrw_ctx *ctx, const double2 *f, double *user, int nrhs);
+void pack_P64(ddrw_ctx *ctx, const double2 *f, double *packed, int nrhs);
+void unpack_P64(ddrw_ctx *ctx, const double *packed, double2 *f, int nrhs);  // zero outside supp P
+
+void pack_gauge(ddrw_ctx *ctx, const double *Ulex);  // fills U64 and U32
+void build_clover(ddrw_ctx *ctx);                    // fills C64 and C32 from U64
+void build_inverse(ddrw_ctx *ctx, double m, MassInv &mi);
+
+// Hopping + clover kernel (K4/K5), policy-generic:
+//   out = POST( alpha * DIAG(x) + beta * sum_mu [hops of `in` selected by hopsel] )
+//   DIAG: 0 none, 1 A(m) x, 2 x;  POST: 0 none, 1 A(m)^-1 (per-mass inverse)
+//   hopsel: 0 all hops, 1 hops inside a block, 2 hops between blocks.
+// Output sites: parities par0 .. par0+npar-1, blocks blk0 .. blk0+nblk-1.
+struct DslashCall {
+    const void *in = nullptr;
+    const void *x = nullptr;
+    void *out = nullptr;
+    long rstride = 0;  // elements between right-hand sides
+    int nrhs = 1;
+    double mass = 0.0;
+    const void *Ainv = nullptr;
+    double alpha = 0.0, beta = 0.0;
+    int diag = 0, post = 0, hopsel = 0;
+    int par0 = 0, npar = 2, blk0 = 0, nblk = 0;
+};
+void dslash64(ddrw_ctx *ctx, const DslashCall &c);
+void dslash32(ddrw_ctx *ctx, const DslashCall &c);
+
+}  // namespace ddrw

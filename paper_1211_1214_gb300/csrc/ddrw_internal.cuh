@@ -1,0 +1,372 @@
+// ddrw_internal.cuh -- layouts, geometry and per-site arithmetic shared by the CUDA kernels.
+//
+// Operator (the Wilson-clover Dirac operator the paper uses, Sec. 1 and Sec. 2; normalisation in
+// the mass-additive form that M = 1 + dm D^-1(m2) of Eq. 6 needs):
+//
+//   (D(m) psi)(x) = A(m)(x) psi(x) - 1/2 sum_mu [ (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu) ]
+//   A(m)(x)       = (4 + m) + C(x),   C = csw (i/4) sum_{mu nu} sigma_{mu nu} Fhat_{mu nu}
+//
+// Chiral basis: g_mu = [[0, e_mu], [e_mu^dag, 0]] in 2x2 spin blocks with e_0 = -1 and
+// e_k = -i sigma_k, so g5 = diag(1, 1, -1, -1) and C is two Hermitian 6x6 blocks (spins 0,1 and
+// spins 2,3), each indexed by 3*(spin within the pair) + colour.
+//
+// Internal site order ("block-major, even-odd split"): with hypercubic blocks of length BL,
+//
+//   s = p * V/2 + blk * BL^4/2 + h,
+//
+// p the site parity (t+x+y+z) mod 2, blk the block number with all black blocks first (colour
+// of a block = sum of its block coordinates mod 2, block 0 black), h = (in-block lexicographic
+// index) / 2.  Every block origin has even coordinates, so the in-block parity is the global
+// parity; the sites of one block and one parity are contiguous, and so are the sites of one
+// colour and one parity.
+//
+// Fields are structure-of-arrays over sites: plane k of site s at base[k * stride + s], each
+// element 16 bytes (double2 / float4), one field per right-hand side.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ddrw {
+
+// ----------------------------------------------------------------------------- geometry
+
+struct GeomDev {
+    int L[4];          // T, X, Y, Z
+    int NB[4];         // blocks per direction (all even, >= 2)
+    int nblk;          // number of blocks
+    int nblk_c;        // blocks of one colour
+    long vh;           // V / 2
+    long V;
+    const int *blk_nb;  // [nblk][8]: neighbour block in direction 2*mu (+mu) and 2*mu+1 (-mu)
+    const int *blk_org; // [nblk][4]: coordinates of the block origin
+    const int *blk_index; // [nblk]: block number of the block with lexicographic block index B
+    int tsign;          // -1: antiperiodic in time, +1: periodic
+};
+
+template <int BL> struct BlockShape {
+    static constexpr int VB = BL * BL * BL * BL;
+    static constexpr int VBH = VB / 2;
+    static constexpr int ROWH = BL / 2;  // half-sites per z-row
+};
+
+template <int BL> struct Site {
+    int p, blk, h;
+    int c[4];  // in-block coordinates
+};
+
+template <int BL>
+__device__ __forceinline__ void decode_site(long s, const GeomDev &g, Site<BL> &st)
+{
+    st.p = (s >= g.vh) ? 1 : 0;
+    long r = s - (long)st.p * g.vh;
+    st.blk = (int)(r / BlockShape<BL>::VBH);
+    st.h = (int)(r - (long)st.blk * BlockShape<BL>::VBH);
+    int row = st.h / BlockShape<BL>::ROWH;
+    int izh = st.h - row * BlockShape<BL>::ROWH;
+    st.c[2] = row % BL;
+    row /= BL;
+    st.c[1] = row % BL;
+    st.c[0] = row / BL;
+    st.c[3] = 2 * izh + ((st.c[0] + st.c[1] + st.c[2] + st.p) & 1);
+}
+
+// Neighbour of st one step in direction mu (dir = +1/-1).  *cross is set when the hop leaves the
+// block; *phase is the boundary sign of the hop.
+template <int BL>
+__device__ __forceinline__ long neighbour(const Site<BL> &st, int mu, int dir, const GeomDev &g, bool *cross,
+                                          int *phase)
+{
+    int c0 = st.c[0], c1 = st.c[1], c2 = st.c[2], c3 = st.c[3];
+    int cm = st.c[mu] + dir;
+    int blk = st.blk;
+    *cross = false;
+    *phase = 1;
+    if (cm < 0 || cm >= BL) {
+        *cross = true;
+        blk = g.blk_nb[st.blk * 8 + 2 * mu + (dir < 0 ? 1 : 0)];
+        if (mu == 0 && g.tsign < 0) {
+            int t = g.blk_org[st.blk * 4] + st.c[0];
+            if ((dir > 0 && t == g.L[0] - 1) || (dir < 0 && t == 0)) *phase = -1;
+        }
+        cm = (cm < 0) ? BL - 1 : 0;
+    }
+    if (mu == 0) c0 = cm;
+    else if (mu == 1) c1 = cm;
+    else if (mu == 2) c2 = cm;
+    else c3 = cm;
+    int lb = ((c0 * BL + c1) * BL + c2) * BL + c3;
+    return (long)(1 - st.p) * g.vh + (long)blk * BlockShape<BL>::VBH + (lb >> 1);
+}
+
+// lexicographic site index of an internal site (boundary layout)
+template <int BL>
+__device__ __forceinline__ long lex_index(const Site<BL> &st, const GeomDev &g)
+{
+    const int *o = g.blk_org + st.blk * 4;
+    int t = o[0] + st.c[0], x = o[1] + st.c[1], y = o[2] + st.c[2], z = o[3] + st.c[3];
+    return (((long)t * g.L[1] + x) * g.L[2] + y) * g.L[3] + z;
+}
+
+// internal index of the site with global coordinates (t, x, y, z), all in range
+template <int BL>
+__device__ __forceinline__ long internal_index(const GeomDev &g, int t, int x, int y, int z)
+{
+    int bt = t / BL, bx = x / BL, by = y / BL, bz = z / BL;
+    int B = ((bt * g.NB[1] + bx) * g.NB[2] + by) * g.NB[3] + bz;
+    int blk = g.blk_index[B];
+    int lb = (((t - bt * BL) * BL + (x - bx * BL)) * BL + (y - by * BL)) * BL + (z - bz * BL);
+    int p = (t + x + y + z) & 1;
+    return (long)p * g.vh + (long)blk * BlockShape<BL>::VBH + (lb >> 1);
+}
+
+// ----------------------------------------------------------------------------- complex arithmetic
+
+template <typename R> struct cpx {
+    R re, im;
+};
+
+template <typename R> __device__ __forceinline__ cpx<R> mk(R a, R b) { return cpx<R>{a, b}; }
+template <typename R> __device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R> __device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R> __device__ __forceinline__ cpx<R> operator-(cpx<R> a) { return {-a.re, -a.im}; }
+template <typename R> __device__ __forceinline__ cpx<R> operator*(R s, cpx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R> __device__ __forceinline__ cpx<R> cmul(cpx<R> a, cpx<R> b)
+{
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R> __device__ __forceinline__ cpx<R> cmulc(cpx<R> a, cpx<R> b)  // conj(a) * b
+{
+    return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+template <typename R> __device__ __forceinline__ cpx<R> timesI(cpx<R> a) { return {-a.im, a.re}; }
+template <typename R> __device__ __forceinline__ cpx<R> timesMinusI(cpx<R> a) { return {a.im, -a.re}; }
+
+template <typename R> struct Spinor {
+    cpx<R> v[4][3];
+};
+template <typename R> struct Half {
+    cpx<R> v[2][3];
+};
+template <typename R> struct Link {
+    cpx<R> m[3][3];
+};
+
+template <typename R> __device__ __forceinline__ void zero(Spinor<R> &s)
+{
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) s.v[a][c] = {R(0), R(0)};
+}
+
+// ----------------------------------------------------------------------------- spin projection
+// (1 - g_mu) psi = (h, -e_mu^dag h) with h = psi_u - e_mu psi_d;
+// (1 + g_mu) psi = (h,  e_mu^dag h) with h = psi_u + e_mu psi_d.
+// sign = -1 selects (1 - g_mu), sign = +1 selects (1 + g_mu).
+
+template <int MU, int SIGN, typename R>
+__device__ __forceinline__ void project(const Spinor<R> &p, Half<R> &h)
+{
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        cpx<R> d0 = p.v[2][c], d1 = p.v[3][c];
+        cpx<R> e0, e1;  // e_mu psi_d
+        if (MU == 0) { e0 = -d0; e1 = -d1; }
+        else if (MU == 1) { e0 = timesMinusI(d1); e1 = timesMinusI(d0); }
+        else if (MU == 2) { e0 = -d1; e1 = d0; }
+        else { e0 = timesMinusI(d0); e1 = timesI(d1); }
+        if (SIGN > 0) { h.v[0][c] = p.v[0][c] + e0; h.v[1][c] = p.v[1][c] + e1; }
+        else { h.v[0][c] = p.v[0][c] - e0; h.v[1][c] = p.v[1][c] - e1; }
+    }
+}
+
+// acc += coef * (1 +- g_mu)-reconstruction of the half spinor w
+template <int MU, int SIGN, typename R>
+__device__ __forceinline__ void reconstruct_add(Spinor<R> &acc, const Half<R> &w)
+{
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        cpx<R> w0 = w.v[0][c], w1 = w.v[1][c];
+        cpx<R> f0, f1;  // e_mu^dag w
+        if (MU == 0) { f0 = -w0; f1 = -w1; }
+        else if (MU == 1) { f0 = timesI(w1); f1 = timesI(w0); }
+        else if (MU == 2) { f0 = w1; f1 = -w0; }
+        else { f0 = timesI(w0); f1 = timesMinusI(w1); }
+        acc.v[0][c] = acc.v[0][c] + w0;
+        acc.v[1][c] = acc.v[1][c] + w1;
+        if (SIGN > 0) { acc.v[2][c] = acc.v[2][c] + f0; acc.v[3][c] = acc.v[3][c] + f1; }
+        else { acc.v[2][c] = acc.v[2][c] - f0; acc.v[3][c] = acc.v[3][c] - f1; }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void link_mul(const Link<R> &U, const Half<R> &h, Half<R> &w)
+{
+#pragma unroll
+    for (int s = 0; s < 2; s++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            cpx<R> t = cmul(U.m[a][0], h.v[s][0]);
+            t = t + cmul(U.m[a][1], h.v[s][1]);
+            t = t + cmul(U.m[a][2], h.v[s][2]);
+            w.v[s][a] = t;
+        }
+}
+
+template <typename R>
+__device__ __forceinline__ void link_dag_mul(const Link<R> &U, const Half<R> &h, Half<R> &w)
+{
+#pragma unroll
+    for (int s = 0; s < 2; s++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            cpx<R> t = cmulc(U.m[0][a], h.v[s][0]);
+            t = t + cmulc(U.m[1][a], h.v[s][1]);
+            t = t + cmulc(U.m[2][a], h.v[s][2]);
+            w.v[s][a] = t;
+        }
+}
+
+// ----------------------------------------------------------------------------- storage policies
+//
+// A policy P gives the arithmetic type P::R and how spinors, links and clover blocks are stored.
+//   PrecD: FP64 everything, full 3x3 links (9 double2 planes per direction), clover 36 double2.
+//   PrecS: FP32 spinors (6 float4 planes), two-row links (3 float4 planes), clover 18 float4.
+
+struct PrecD {
+    using R = double;
+    using SElem = double2;
+    static constexpr int SPLANES = 12;
+    static constexpr int UPLANES = 9;   // per direction
+    static constexpr int CPLANES = 36;  // per site, both chiralities
+    using UElem = double2;
+    using CElem = double2;
+
+    __device__ static __forceinline__ void load_spinor(const SElem *__restrict__ f, long stride, long s, Spinor<R> &p)
+    {
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            double2 v = __ldg(f + k * stride + s);
+            p.v[k / 3][k % 3] = {v.x, v.y};
+        }
+    }
+    __device__ static __forceinline__ void store_spinor(SElem *__restrict__ f, long stride, long s, const Spinor<R> &p)
+    {
+#pragma unroll
+        for (int k = 0; k < 12; k++) f[k * stride + s] = make_double2(p.v[k / 3][k % 3].re, p.v[k / 3][k % 3].im);
+    }
+    __device__ static __forceinline__ void load_link(const UElem *__restrict__ U, long V, int mu, long s, Link<R> &L)
+    {
+        const UElem *b = U + (long)mu * 9 * V + s;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            double2 v = __ldg(b + k * V);
+            L.m[k / 3][k % 3] = {v.x, v.y};
+        }
+    }
+    // reals 0..35 of chirality block ch
+    __device__ static __forceinline__ void load_clover(const CElem *__restrict__ Cl, long V, long s, int ch, R *c)
+    {
+        const CElem *b = Cl + (long)ch * 18 * V + s;
+#pragma unroll
+        for (int k = 0; k < 18; k++) {
+            double2 v = __ldg(b + k * V);
+            c[2 * k] = v.x;
+            c[2 * k + 1] = v.y;
+        }
+    }
+};
+
+struct PrecS {
+    using R = float;
+    using SElem = float4;
+    static constexpr int SPLANES = 6;
+    static constexpr int UPLANES = 3;
+    static constexpr int CPLANES = 18;
+    using UElem = float4;
+    using CElem = float4;
+
+    __device__ static __forceinline__ void load_spinor(const SElem *__restrict__ f, long stride, long s, Spinor<R> &p)
+    {
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            float4 v = __ldg(f + k * stride + s);
+            p.v[(2 * k) / 3][(2 * k) % 3] = {v.x, v.y};
+            p.v[(2 * k + 1) / 3][(2 * k + 1) % 3] = {v.z, v.w};
+        }
+    }
+    __device__ static __forceinline__ void store_spinor(SElem *__restrict__ f, long stride, long s, const Spinor<R> &p)
+    {
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            cpx<R> a = p.v[(2 * k) / 3][(2 * k) % 3], b = p.v[(2 * k + 1) / 3][(2 * k + 1) % 3];
+            f[k * stride + s] = make_float4(a.re, a.im, b.re, b.im);
+        }
+    }
+    // two stored rows; row 2 = conj(row0 x row1) (U in SU(3))
+    __device__ static __forceinline__ void load_link(const UElem *__restrict__ U, long V, int mu, long s, Link<R> &L)
+    {
+        const UElem *b = U + (long)mu * 3 * V + s;
+        float4 a0 = __ldg(b), a1 = __ldg(b + V), a2 = __ldg(b + 2 * V);
+        L.m[0][0] = {a0.x, a0.y};
+        L.m[0][1] = {a0.z, a0.w};
+        L.m[0][2] = {a1.x, a1.y};
+        L.m[1][0] = {a1.z, a1.w};
+        L.m[1][1] = {a2.x, a2.y};
+        L.m[1][2] = {a2.z, a2.w};
+        reconstruct_row2(L);
+    }
+    __device__ static __forceinline__ void reconstruct_row2(Link<R> &L)
+    {
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            int i = (c + 1) % 3, j = (c + 2) % 3;
+            cpx<R> t = cmul(L.m[0][i], L.m[1][j]) - cmul(L.m[0][j], L.m[1][i]);
+            L.m[2][c] = {t.re, -t.im};
+        }
+    }
+    __device__ static __forceinline__ void load_clover(const CElem *__restrict__ Cl, long V, long s, int ch, R *c)
+    {
+        const CElem *b = Cl + (long)ch * 9 * V + s;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            float4 v = __ldg(b + k * V);
+            c[4 * k] = v.x;
+            c[4 * k + 1] = v.y;
+            c[4 * k + 2] = v.z;
+            c[4 * k + 3] = v.w;
+        }
+    }
+};
+
+// Hermitian 6x6 block stored as 36 reals: d[0..5] the real diagonal, then the 15 entries above
+// the diagonal, row by row, as (re, im).  Index of (i, j), i < j, in that list:
+__host__ __device__ constexpr int herm_off(int i, int j) { return i * 5 - (i * (i - 1)) / 2 + (j - i - 1); }
+
+// out = (diag + H) v for a Hermitian 6x6 H in packed form
+template <typename R>
+__device__ __forceinline__ void herm6_mul(const R *c, R diag, const cpx<R> *v, cpx<R> *out)
+{
+#pragma unroll
+    for (int i = 0; i < 6; i++) out[i] = (diag + c[i]) * v[i];
+#pragma unroll
+    for (int i = 0; i < 6; i++)
+#pragma unroll
+        for (int j = i + 1; j < 6; j++) {
+            int o = 6 + 2 * herm_off(i, j);
+            cpx<R> hij = {c[o], c[o + 1]};
+            out[i] = out[i] + cmul(hij, v[j]);
+            out[j] = out[j] + cmulc(hij, v[i]);
+        }
+}
+
+// ----------------------------------------------------------------------------- host helpers
+
+#define DDRW_CUDA_CHECK(call)                                                                         \
+    do {                                                                                              \
+        cudaError_t err__ = (call);                                                                   \
+        if (err__ != cudaSuccess) return ::ddrw::set_cuda_error(ctx, err__, #call, __FILE__, __LINE__); \
+    } while (0)
+
+}  // namespace ddrw
