@@ -143,6 +143,14 @@ ddrw_status ddrw_noise(ddrw_ctx *ctx, uint64_t seed, uint64_t hit_offset, int nh
 ddrw_status ddrw_estimate(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64_t hit_offset, const double *eta,
                           double *exponents, double *logW, double *rel_var, double *delta, ddrw_solve_info *info);
 
+/* The estimate for several target masses in one batched call (the mass sweep of a reweighting
+ * study): right-hand side k * nhit + j carries m2[k] and noise vector j (the same noise vectors for
+ * every mass), all in one multi-right-hand-side pass.  exponents[nmass * nhit], logW[nmass] and
+ * rel_var[nmass] as in ddrw_estimate (each optional).  1 <= nmass <= 8; m1 from ddrw_set_params. */
+ddrw_status ddrw_estimate_masses(ddrw_ctx *ctx, int nmass, const double *m2, int nhit, uint64_t seed,
+                                 uint64_t hit_offset, double *exponents, double *logW, double *rel_var,
+                                 ddrw_solve_info *info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,8 @@ _STATUS = {0: "DDRW_OK", 1: "DDRW_EINVAL", 2: "DDRW_ENOMEM", 3: "DDRW_ECUDA", 4:
 #: every entry point declared in include/ddrw.h
 EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", "ddrw_volume", "ddrw_load_gauge",
            "ddrw_set_params", "ddrw_set_solver", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
-           "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate"]
+           "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
+           "ddrw_estimate_masses"]
 
 
 class DDRWError(RuntimeError):
@@ -78,6 +79,8 @@ def load(path: str | None = None):
         "ddrw_noise": (st, [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, dp]),
         "ddrw_estimate": (st, [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp, dp, dp, dp,
                                ctypes.POINTER(SolveInfo)]),
+        "ddrw_estimate_masses": (st, [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp,
+                                      dp, ctypes.POINTER(SolveInfo)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -199,3 +202,16 @@ class Context:
                                   _ptr(e), _ptr(lw), _ptr(rv), _ptr(delta), ctypes.byref(info))
         self._check(st, "ddrw_estimate")
         return e, float(lw[0]), float(rv[0]), info.as_dict()
+
+    def estimate_masses(self, m2s, nhit, seed=2, hit_offset=0):
+        """Batched estimate for several target masses: (exponents [nmass, nhit], logW [nmass],
+        rel_var [nmass], solve info)."""
+        m = np.ascontiguousarray(m2s, dtype=np.float64)
+        e = np.zeros((len(m), nhit), dtype=np.float64)
+        lw = np.zeros(len(m), dtype=np.float64)
+        rv = np.zeros(len(m), dtype=np.float64)
+        info = SolveInfo()
+        st = self.L.ddrw_estimate_masses(self._h, len(m), _ptr(m), int(nhit), ctypes.c_uint64(seed),
+                                         ctypes.c_uint64(hit_offset), _ptr(e), _ptr(lw), _ptr(rv), ctypes.byref(info))
+        self._check(st, "ddrw_estimate_masses")
+        return e, lw, rv, info.as_dict()

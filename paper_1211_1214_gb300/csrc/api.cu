@@ -414,7 +414,7 @@ ddrw_status ddrw_apply_block(ddrw_ctx *ctx, int rows, int cols, double m, const 
     c.out = fout;
     c.rstride = 12 * ctx->V;
     c.nrhs = nrhs;
-    c.mass = m;
+    c.masses[0] = m;
     c.alpha = 1.0;
     c.beta = -0.5;
     c.par0 = 0;

@@ -1,0 +1,207 @@
+// blocksolve.cu -- the persistent block solver (K6): x = D_cc(m)^-1 b for every block of one colour
+// c in one launch (D_bb and D_ww are block-diagonal, Eq. 1, so the blocks are independent).
+//
+// One CTA owns one (block, right-hand side) pair and runs the whole Krylov solve inside the kernel:
+// in-block even-odd preconditioning S = A_ee - 1/4 H_eo A_oo^-1 H_oe (hops inside the block only),
+// BiCGStab on S with CTA-wide reductions (warp shuffles + shared memory, FP64 above the thread),
+// then x_o = A_oo^-1 (b_o + 1/2 H_oe x_e).  The block's sites of one parity are contiguous in the
+// block-major layout, so every pass is a coalesced sweep over the block.
+//
+// The host driver wraps the kernel in FP64 defect correction: r = b - D_cc x in FP64, the kernel
+// (FP64 or FP32) solves D_cc e = r to a relative tolerance per block, x += e, until
+// ||b - D_cc x|| <= tol ||b|| for every right-hand side (norms over the colour).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "blocksolve.cuh"
+
+namespace ddrw {
+
+template <class P, int BL> void launch_block_kernel(ddrw_ctx *ctx, const BlkArgs<P> &a, int nrhs);
+
+// ----------------------------------------------------------------------------- host side
+
+template <class P>
+static void launch_block(ddrw_ctx *ctx, const BlkArgs<P> &a, int nrhs)
+{
+    switch (ctx->l) {
+    case 2: launch_block_kernel<P, 2>(ctx, a, nrhs); break;
+    case 4: launch_block_kernel<P, 4>(ctx, a, nrhs); break;
+    case 6: launch_block_kernel<P, 6>(ctx, a, nrhs); break;
+    default: launch_block_kernel<P, 8>(ctx, a, nrhs); break;
+    }
+}
+
+// colour ranges: sites of colour c and parity p are [p vh + c n_c, p vh + (c + 1) n_c)
+static VecRange colour_range(const ddrw_ctx *ctx, int colour, int parity, int nrhs, long rs)
+{
+    long vbh = (long)ctx->l * ctx->l * ctx->l * ctx->l / 2;
+    long nc = (long)ctx->nblk_c * vbh;
+    return VecRange{ctx->V, parity * ctx->vh + colour * nc, nc, rs, nrhs};
+}
+
+template <class P>
+static void fill_args(ddrw_ctx *ctx, BlkArgs<P> &a, const MassSet &ms, int colour)
+{
+    using R = typename P::R;
+    int nm = ms.n < 1 ? 1 : ms.n;
+    for (int k = 0; k < MAXM; k++) {
+        int kk = k < nm ? k : nm - 1;
+        a.mass4[k] = R(4.0 + ms.m[kk]);
+        if constexpr (sizeof(R) == 8) a.Ainv[k] = (const typename P::CElem *)ms.inv[kk]->A64;
+        else a.Ainv[k] = (const typename P::CElem *)ms.inv[kk]->A32;
+    }
+    if constexpr (sizeof(R) == 8) {
+        a.U = (const typename P::UElem *)ctx->U64;
+        a.Cl = (const typename P::CElem *)ctx->C64;
+    } else {
+        a.U = (const typename P::UElem *)ctx->U32;
+        a.Cl = (const typename P::CElem *)ctx->C32;
+    }
+    a.blk0 = colour == DDRW_BLACK ? 0 : ctx->nblk_c;
+}
+
+// norms over a colour (both parities) of nrhs FP64 fields -> host
+static ddrw_status colour_norms(ddrw_ctx *ctx, int colour, const double2 *f, int nrhs, std::vector<double> &out)
+{
+    double *d;
+    ddrw_status st = workspace(ctx, "blk_norms", sizeof(double) * 2 * nrhs, (void **)&d);
+    if (st) return st;
+    long rs = 12 * ctx->V;
+    for (int p = 0; p < 2; p++) {
+        st = Blas<PrecD>::norm2(ctx, colour_range(ctx, colour, p, nrhs, rs), f, d + p * nrhs);
+        if (st) return st;
+    }
+    std::vector<double> h(2 * nrhs);
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(h.data(), d, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    out.resize(nrhs);
+    for (int r = 0; r < nrhs; r++) out[r] = h[r] + h[nrhs + r];
+    return DDRW_OK;
+}
+
+// x = D_cc(ms)^-1 b on the sites of colour c (FP64 fields, full-field layout, nrhs rhs).
+// Sites of the other colour in x are left untouched.
+ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const double2 *b, double2 *x, int nrhs,
+                          double tol, int maxiter, bool mixed, SolveStats *stats)
+{
+    const long V = ctx->V, rs64 = 12 * V, rs32 = 6 * V;
+    const size_t f64 = sizeof(double2) * rs64 * nrhs, f32 = sizeof(float4) * rs32 * nrhs;
+    ddrw_status st;
+    std::vector<double> bb, rr;
+    if ((st = colour_norms(ctx, colour, b, nrhs, bb))) return st;
+    int *stat;
+    if ((st = workspace(ctx, "blk_stat", sizeof(int) * 2, (void **)&stat))) return st;
+    double2 *res64, *e64 = nullptr;
+    if ((st = workspace(ctx, "blk_res64", f64, (void **)&res64))) return st;
+
+    // inner workspaces
+    void *w[6];
+    const char *names64[6] = {"blk_r", "blk_rh", "blk_p", "blk_v", "blk_t", "blk_tmp"};
+    const char *names32[6] = {"blk32_r", "blk32_rh", "blk32_p", "blk32_v", "blk32_t", "blk32_tmp"};
+    for (int k = 0; k < 6; k++)
+        if ((st = workspace(ctx, mixed ? names32[k] : names64[k], mixed ? f32 : f64, &w[k]))) return st;
+    float4 *b32 = nullptr, *e32 = nullptr;
+    double *scale_d = nullptr;
+    if (mixed) {
+        if ((st = workspace(ctx, "blk32_b", f32, (void **)&b32))) return st;
+        if ((st = workspace(ctx, "blk32_e", f32, (void **)&e32))) return st;
+        if ((st = workspace(ctx, "blk_scale", sizeof(double) * 2 * nrhs, (void **)&scale_d))) return st;
+    } else {
+        if ((st = workspace(ctx, "blk_e64", f64, (void **)&e64))) return st;
+    }
+    // tolerance of one inner solve: the target itself in FP64, 1e-5 per cycle in FP32
+    const double tol_inner = mixed ? std::max(tol, 1e-5) : tol * 0.5;
+    const double2 *rhs = b;  // first cycle: r = b, x = 0
+    bool first = true;
+    int cycles = 0;
+    std::vector<double> scale(nrhs), unscale(nrhs);
+    for (; cycles < 50; cycles++) {
+        DDRW_CUDA_CHECK(cudaMemsetAsync(stat, 0, sizeof(int) * 2, ctx->stream));
+        if (mixed) {
+            const std::vector<double> &nr = first ? bb : rr;
+            for (int r = 0; r < nrhs; r++) {
+                double n = std::sqrt(nr[r]);
+                scale[r] = n > 0 ? 1.0 / n : 0.0;
+                unscale[r] = n;
+            }
+            DDRW_CUDA_CHECK(cudaMemcpyAsync(scale_d, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+            DDRW_CUDA_CHECK(cudaMemcpyAsync(scale_d + nrhs, unscale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice,
+                                            ctx->stream));
+            for (int p = 0; p < 2; p++) to32(ctx, colour_range(ctx, colour, p, nrhs, rs64), rs32, rhs, b32, scale_d);
+            BlkArgs<PrecS> a;
+            a.b = b32;
+            a.x = e32;
+            a.r = (float4 *)w[0]; a.rh = (float4 *)w[1]; a.p = (float4 *)w[2];
+            a.v = (float4 *)w[3]; a.t = (float4 *)w[4]; a.tmp = (float4 *)w[5];
+            a.rstride = rs32;
+            a.rpm = (nrhs + std::max(ms.n, 1) - 1) / std::max(ms.n, 1);
+            fill_args(ctx, a, ms, colour);
+            a.tol2 = tol_inner * tol_inner;
+            a.maxiter = maxiter;
+            a.stat = stat;
+            launch_block(ctx, a, nrhs);
+            if (first) zero_colour64(ctx, x, colour, nrhs);
+            for (int p = 0; p < 2; p++) add32(ctx, colour_range(ctx, colour, p, nrhs, rs64), rs32, e32, x, scale_d + nrhs);
+        } else {
+            BlkArgs<PrecD> a;
+            a.b = rhs;
+            a.x = first ? x : e64;
+            a.r = (double2 *)w[0]; a.rh = (double2 *)w[1]; a.p = (double2 *)w[2];
+            a.v = (double2 *)w[3]; a.t = (double2 *)w[4]; a.tmp = (double2 *)w[5];
+            a.rstride = rs64;
+            a.rpm = (nrhs + std::max(ms.n, 1) - 1) / std::max(ms.n, 1);
+            fill_args(ctx, a, ms, colour);
+            a.tol2 = tol_inner * tol_inner;
+            a.maxiter = maxiter;
+            a.stat = stat;
+            launch_block(ctx, a, nrhs);
+            if (!first)
+                for (int p = 0; p < 2; p++)
+                    Blas<PrecD>::axpby(ctx, colour_range(ctx, colour, p, nrhs, rs64), 1.0, e64, 1.0, x);
+        }
+        int hstat[2];
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(hstat, stat, sizeof(hstat), cudaMemcpyDeviceToHost, ctx->stream));
+        // true residual res = b - D_cc x in FP64
+        DslashCall c;
+        c.in = x;
+        c.x = x;
+        c.out = res64;
+        c.rstride = rs64;
+        c.nrhs = nrhs;
+        c.nmass = ms.n;
+        for (int k = 0; k < ms.n; k++) {
+            c.masses[k] = ms.m[k];
+            c.Ainv[k] = ms.inv[k]->A64;
+        }
+        c.alpha = -1.0;
+        c.beta = 0.5;
+        c.diag = 1;
+        c.hopsel = 1;
+        c.par0 = 0;
+        c.npar = 2;
+        c.blk0 = colour == DDRW_BLACK ? 0 : ctx->nblk_c;
+        c.nblk = ctx->nblk_c;
+        dslash64(ctx, c);
+        if (stats) stats->fp64_dslash_half += 1;
+        for (int p = 0; p < 2; p++) Blas<PrecD>::axpby(ctx, colour_range(ctx, colour, p, nrhs, rs64), 1.0, b, 1.0, res64);
+        if ((st = colour_norms(ctx, colour, res64, nrhs, rr))) return st;
+        if (stats) {
+            stats->block_iters_max = std::max(stats->block_iters_max, hstat[0]);
+            stats->block_cycles += 1;
+        }
+        double worst = 0;
+        for (int r = 0; r < nrhs; r++)
+            if (bb[r] > 0) worst = std::max(worst, std::sqrt(rr[r] / bb[r]));
+        if (stats) stats->block_rel_residual = std::max(stats->block_rel_residual, worst);
+        if (!(worst == worst)) return set_error(ctx, DDRW_ENUMERIC, "NaN in a block solve");
+        if (worst <= tol) return DDRW_OK;
+        rhs = res64;
+        first = false;
+        if (!mixed && hstat[1] > 0 && cycles >= 3) break;
+    }
+    return set_error(ctx, DDRW_ENOCONV, "block solve did not reach its tolerance");
+}
+
+}  // namespace ddrw

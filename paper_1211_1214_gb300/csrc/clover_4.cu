@@ -1,0 +1,6 @@
+// one instantiation of the clover-term kernel (see clover.cuh)
+#include "clover.cuh"
+
+namespace ddrw {
+template void clover_launch<4>(ddrw_ctx *ctx);
+}

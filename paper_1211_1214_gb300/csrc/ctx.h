@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <deque>
 #include <map>
 #include <string>
 #include <vector>
@@ -22,6 +23,25 @@ struct MassInv {
     double m;
     double2 *A64 = nullptr;  // [2][18][V]
     float4 *A32 = nullptr;   // [2][9][V]
+};
+
+// A set of masses, one per right-hand-side slot (rhs r uses slot r / ceil(nrhs / n)).
+struct MassSet {
+    int n = 1;
+    double m[MAXM] = {0.0};
+    MassInv *inv[MAXM] = {nullptr};
+};
+
+// Work counters of a solve, summed over its phases.
+struct SolveStats {
+    int block_iters_max = 0;     // largest in-kernel iteration count of any block solve
+    int block_cycles = 0;        // block defect-correction cycles
+    double block_rel_residual = 0;
+    int fp64_dslash_half = 0;    // FP64 stencil sweeps over half the lattice (one colour)
+    int outer_iters = 0;         // outer Krylov iterations, summed over cycles
+    int outer_cycles = 0;        // outer defect-correction cycles
+    int fp64_dslash_full = 0;    // FP64 full-lattice operator applications
+    double outer_rel_residual = 0;
 };
 
 }  // namespace ddrw
@@ -54,7 +74,7 @@ struct ddrw_ctx {
     float4 *U32 = nullptr;   // [4][3][V] two-row
     double2 *C64 = nullptr;  // [2][18][V]
     float4 *C32 = nullptr;   // [2][9][V]
-    std::vector<ddrw::MassInv> inv;
+    std::deque<ddrw::MassInv> inv;  // deque: MassInv addresses stay valid as entries are added
 
     // workspaces by name (grow-only)
     std::map<std::string, ddrw::DevBuf> ws;
@@ -107,13 +127,23 @@ struct DslashCall {
     void *out = nullptr;
     long rstride = 0;  // elements between right-hand sides
     int nrhs = 1;
-    double mass = 0.0;
-    const void *Ainv = nullptr;
+    int nmass = 1;                      // mass slots: rhs r uses slot r / ceil(nrhs / nmass)
+    double masses[MAXM] = {0.0};
+    const void *Ainv[MAXM] = {nullptr};  // A(m)^-1 of each slot, in the policy's precision
     double alpha = 0.0, beta = 0.0;
     int diag = 0, post = 0, hopsel = 0;
     int par0 = 0, npar = 2, blk0 = 0, nblk = 0;
 };
 void dslash64(ddrw_ctx *ctx, const DslashCall &c);
 void dslash32(ddrw_ctx *ctx, const DslashCall &c);
+
+// x = D_cc(ms)^-1 b on the sites of colour c (persistent block solver + FP64 defect correction)
+ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const double2 *b, double2 *x, int nrhs,
+                          double tol, int maxiter, bool mixed, SolveStats *stats);
+// x = D(ms)^-1 b on the full lattice (even-odd BiCGStab + FP64 defect correction)
+ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, double2 *x, int nrhs, double tol,
+                         int maxiter, ddrw_prec prec, SolveStats *stats);
+// mass set from a list of masses (builds the inverses on first use)
+ddrw_status make_massset(ddrw_ctx *ctx, int n, const double *m, MassSet *ms);
 
 }  // namespace ddrw

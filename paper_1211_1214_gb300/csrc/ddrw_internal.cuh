@@ -29,6 +29,8 @@
 
 namespace ddrw {
 
+constexpr int MAXM = 8;  // mass slots per launch (right-hand sides grouped by mass)
+
 // ----------------------------------------------------------------------------- geometry
 
 struct GeomDev {
@@ -251,6 +253,14 @@ struct PrecD {
             p.v[k / 3][k % 3] = {v.x, v.y};
         }
     }
+    __device__ static __forceinline__ void load_spinor_rw(const SElem *f, long stride, long s, Spinor<R> &p)
+    {
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            double2 v = f[k * stride + s];
+            p.v[k / 3][k % 3] = {v.x, v.y};
+        }
+    }
     __device__ static __forceinline__ void store_spinor(SElem *__restrict__ f, long stride, long s, const Spinor<R> &p)
     {
 #pragma unroll
@@ -292,6 +302,15 @@ struct PrecS {
 #pragma unroll
         for (int k = 0; k < 6; k++) {
             float4 v = __ldg(f + k * stride + s);
+            p.v[(2 * k) / 3][(2 * k) % 3] = {v.x, v.y};
+            p.v[(2 * k + 1) / 3][(2 * k + 1) % 3] = {v.z, v.w};
+        }
+    }
+    __device__ static __forceinline__ void load_spinor_rw(const SElem *f, long stride, long s, Spinor<R> &p)
+    {
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            float4 v = f[k * stride + s];
             p.v[(2 * k) / 3][(2 * k) % 3] = {v.x, v.y};
             p.v[(2 * k + 1) / 3][(2 * k + 1) % 3] = {v.z, v.w};
         }

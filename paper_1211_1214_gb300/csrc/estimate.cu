@@ -1,0 +1,504 @@
+// estimate.cu -- the stochastic estimate of 1/det(Mh^dag Mh) (Eq. 3; Eq. 8 with N = 1) for the
+// Schur complement A(m) = P Dhat(m) P (Sec. 1), and the entry points built on it:
+//
+//   noise (K3)   eta_k = sqrt(-ln u1) exp(2 pi i u2), u from Philox4x32-10 (counter (k, hit, 0, 0))
+//   r (K9)       r = (A(m1) - A(m2)) eta = dm P D_bb(m1)^-1 [D_bw a12 + D_bb(m2)^-1 D_bw a2],
+//                u = D_wb eta, a2 = D_ww(m2)^-1 u, a12 = D_ww(m1)^-1 a2      (resolvent form)
+//   delta        delta = A(m2)^-1 r = r - P x_b,  D(m2) x = (0_b ; D_wb r)     (Dhat^-1 = 1 - P Dcal_bw D_wb)
+//   e (K10)      e = ||delta||^2 + 2 Re <eta, delta>  (= ||Mh eta||^2 - ||eta||^2 without cancellation)
+//
+// Right-hand sides: nmass target masses x nhit noise vectors, slot-major (rhs = k * nhit + j uses
+// m2[k] and eta_j).  All fields are FP64; the solves run in the context's precision.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "blas.cuh"
+#include "ctx.h"
+
+namespace ddrw {
+
+// ----------------------------------------------------------------------------- Philox4x32-10
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; round++) {
+        if (round) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+// eta for packed component k of hit h -> internal field (and optionally the packed output)
+__global__ void k_noise(long V, long nP, const int *__restrict__ idx, uint32_t k0, uint32_t k1, uint64_t hit0,
+                        int nhit, int nrep, double2 *field, double *packed)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 12 * nP) return;
+    int h = blockIdx.y;
+    uint32_t c[4] = {(uint32_t)k, (uint32_t)(hit0 + (uint64_t)h), 0u, 0u};
+    philox4x32_10(c, k0, k1);
+    double u1 = ((double)c[0] + 1.0) * (1.0 / 4294967296.0);
+    double u2 = (double)c[1] * (1.0 / 4294967296.0);
+    double rho = sqrt(-log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    double2 z = make_double2(rho * cs, rho * sn);
+    long j = k / 12;
+    int comp = (int)(k - j * 12);
+    long s = idx[j];
+    if (field)
+        for (int rep = 0; rep < nrep; rep++) field[((long)(rep * nhit + h) * 12 + comp) * V + s] = z;
+    if (packed) {
+        packed[((long)h * nP * 12 + k) * 2] = z.x;
+        packed[((long)h * nP * 12 + k) * 2 + 1] = z.y;
+    }
+}
+
+// replicate rhs j of a nhit-field into slots: f[k * nhit + j] = f[j], k = 1 .. nrep-1
+__global__ void k_replicate(long n, long nhit, int nrep, double2 *f)
+{
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * nhit) return;
+    for (int k = 1; k < nrep; k++) f[(long)k * n * nhit + i] = f[i];
+}
+
+// r <- dm[slot] * P r on black sites (zero off supp P); also zero every white site
+template <int BL>
+__global__ void k_project_P(GeomDev g, double2 *r, int rpm, const double *dm, long rs)
+{
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.V) return;
+    long s = i;
+    Site<BL> st;
+    decode_site<BL>(s, g, st);
+    double f = 0.0;
+    if (st.blk < g.nblk_c) {
+        bool face = false;
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) face |= (st.c[mu] == 0 || st.c[mu] == BL - 1);
+        if (face) f = dm[blockIdx.y / rpm];
+    }
+    double2 *o = r + (long)blockIdx.y * rs + s;
+    for (int k = 0; k < 12; k++) {
+        double2 v = o[(long)k * g.V];
+        o[(long)k * g.V] = make_double2(f * v.x, f * v.y);
+    }
+}
+
+// delta = P (r - x) on supp P, zero elsewhere
+template <int BL>
+__global__ void k_delta(GeomDev g, const double2 *r, const double2 *x, double2 *d, long rs)
+{
+    long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    Site<BL> st;
+    decode_site<BL>(s, g, st);
+    bool in = false;
+    if (st.blk < g.nblk_c)
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) in |= (st.c[mu] == 0 || st.c[mu] == BL - 1);
+    long o = (long)blockIdx.y * rs + s;
+    for (int k = 0; k < 12; k++) {
+        double2 a = r[o + (long)k * g.V], b = x[o + (long)k * g.V];
+        d[o + (long)k * g.V] = in ? make_double2(a.x - b.x, a.y - b.y) : make_double2(0.0, 0.0);
+    }
+}
+
+#define DISPATCH_BL(ctx, KERNEL, GRID, BLOCK, ...)                                                        \
+    switch ((ctx)->l) {                                                                                   \
+    case 2: KERNEL<2><<<GRID, BLOCK, 0, (ctx)->stream>>>(__VA_ARGS__); break;                             \
+    case 4: KERNEL<4><<<GRID, BLOCK, 0, (ctx)->stream>>>(__VA_ARGS__); break;                             \
+    case 6: KERNEL<6><<<GRID, BLOCK, 0, (ctx)->stream>>>(__VA_ARGS__); break;                             \
+    default: KERNEL<8><<<GRID, BLOCK, 0, (ctx)->stream>>>(__VA_ARGS__); break;                            \
+    }
+
+static void noise_launch(ddrw_ctx *ctx, uint64_t seed, uint64_t hit0, int nhit, int nrep, double2 *field, double *packed)
+{
+    dim3 grid((unsigned)((12 * ctx->nP + 255) / 256), (unsigned)nhit);
+    k_noise<<<grid, 256, 0, ctx->stream>>>(ctx->V, ctx->nP, ctx->d_suppP, (uint32_t)(seed & 0xffffffffu),
+                                           (uint32_t)(seed >> 32), hit0, nhit, nrep, field, packed);
+}
+
+// hop between blocks: out (colour rows) = -1/2 H_{rows <- other colour} in ; other rows untouched
+static void hop_between(ddrw_ctx *ctx, int rows, const double2 *in, double2 *out, int nrhs)
+{
+    DslashCall c;
+    c.in = in;
+    c.out = out;
+    c.rstride = 12 * ctx->V;
+    c.nrhs = nrhs;
+    c.beta = -0.5;
+    c.hopsel = 2;
+    c.par0 = 0;
+    c.npar = 2;
+    c.blk0 = rows == DDRW_BLACK ? 0 : ctx->nblk_c;
+    c.nblk = ctx->nblk_c;
+    dslash64(ctx, c);
+}
+
+static double elapsed(std::chrono::steady_clock::time_point t0)
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+static void fill_info(ddrw_solve_info *info, const SolveStats &s, double secs)
+{
+    if (!info) return;
+    info->iters_outer = s.outer_iters;
+    info->cycles = s.outer_cycles;
+    info->fp64_dslash_calls = s.fp64_dslash_full;
+    info->block_iters_max = s.block_iters_max;
+    info->true_rel_residual = s.outer_rel_residual;
+    info->seconds = secs;
+}
+
+// r = (A(m1) - A(m2[slot])) eta for nrhs = nmass * nhit fields (eta: FP64 full fields, zero off
+// supp P).  Work fields f[0..2] (FP64, nrhs each).  Result in r.
+static ddrw_status apply_dA_fields(ddrw_ctx *ctx, const MassSet &m2s, const MassSet &m1s, const double2 *eta,
+                                   double2 *r, double2 *const *f, int nrhs, SolveStats *stats)
+{
+    const bool mixed = ctx->prec != DDRW_FP64;
+    const size_t fb = sizeof(double2) * 12 * ctx->V * nrhs;
+    double2 *u = f[0], *a2 = f[1], *a12 = r, *c2 = f[2];
+    ddrw_status st;
+    DDRW_CUDA_CHECK(cudaMemsetAsync(u, 0, fb, ctx->stream));
+    hop_between(ctx, DDRW_WHITE, eta, u, nrhs);  // u = D_wb eta
+    if ((st = block_solve64(ctx, DDRW_WHITE, m2s, u, a2, nrhs, ctx->tol_block, ctx->maxiter, mixed, stats))) return st;
+    if ((st = block_solve64(ctx, DDRW_WHITE, m1s, a2, a12, nrhs, ctx->tol_block, ctx->maxiter, mixed, stats))) return st;
+    // c = D_bw a12 (into u, black rows), c2 = D_bw a2
+    DDRW_CUDA_CHECK(cudaMemsetAsync(u, 0, fb, ctx->stream));
+    DDRW_CUDA_CHECK(cudaMemsetAsync(c2, 0, fb, ctx->stream));
+    hop_between(ctx, DDRW_BLACK, a12, u, nrhs);
+    hop_between(ctx, DDRW_BLACK, a2, c2, nrhs);
+    // t = D_bb(m2)^-1 c2 (into a2); w = c + t (into u)
+    if ((st = block_solve64(ctx, DDRW_BLACK, m2s, c2, a2, nrhs, ctx->tol_block, ctx->maxiter, mixed, stats))) return st;
+    Blas<PrecD>::axpby(ctx, VecRange{ctx->V, 0, ctx->V, 12 * ctx->V, nrhs}, 1.0, a2, 1.0, u);
+    // r = dm P D_bb(m1)^-1 w
+    DDRW_CUDA_CHECK(cudaMemsetAsync(r, 0, fb, ctx->stream));
+    if ((st = block_solve64(ctx, DDRW_BLACK, m1s, u, r, nrhs, ctx->tol_block, ctx->maxiter, mixed, stats))) return st;
+    double *dm;
+    if ((st = workspace(ctx, "est_dm", sizeof(double) * MAXM, (void **)&dm))) return st;
+    double hdm[MAXM];
+    for (int k = 0; k < MAXM; k++) hdm[k] = k < m2s.n ? m1s.m[0] - m2s.m[k] : 0.0;
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(dm, hdm, sizeof(hdm), cudaMemcpyHostToDevice, ctx->stream));
+    GeomDev g = geom_dev(ctx);
+    int rpm = (nrhs + m2s.n - 1) / m2s.n;
+    dim3 grid((unsigned)((ctx->V + 127) / 128), (unsigned)nrhs);
+    DISPATCH_BL(ctx, k_project_P, grid, 128, g, r, rpm, dm, 12 * ctx->V);
+    return DDRW_OK;
+}
+
+// delta = A(m)^-1 b for FP64 fields b supported on supp P; work fields f[0], f[1]
+static ddrw_status solve_schur_fields(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, double2 *delta,
+                                      double2 *const *f, int nrhs, SolveStats *stats)
+{
+    const size_t fb = sizeof(double2) * 12 * ctx->V * nrhs;
+    double2 *src = f[0], *x = f[1];
+    DDRW_CUDA_CHECK(cudaMemsetAsync(src, 0, fb, ctx->stream));
+    hop_between(ctx, DDRW_WHITE, b, src, nrhs);  // (0_b ; D_wb b)
+    ddrw_status st = full_solve64(ctx, ms, src, x, nrhs, ctx->tol_outer, ctx->maxiter, ctx->prec, stats);
+    if (st && st != DDRW_ENOCONV) return st;
+    GeomDev g = geom_dev(ctx);
+    dim3 grid((unsigned)((ctx->V + 127) / 128), (unsigned)nrhs);
+    DISPATCH_BL(ctx, k_delta, grid, 128, g, b, x, delta, 12 * ctx->V);
+    return st;
+}
+
+static ddrw_status fields(ddrw_ctx *ctx, const char *prefix, int n, int nrhs, double2 **out)
+{
+    for (int k = 0; k < n; k++) {
+        char nm[32];
+        snprintf(nm, sizeof nm, "%s%d", prefix, k);
+        ddrw_status st = workspace(ctx, nm, sizeof(double2) * 12 * ctx->V * nrhs, (void **)&out[k]);
+        if (st) return st;
+    }
+    return DDRW_OK;
+}
+
+// The estimate for nmass target masses: exponents[k * nhit + j], logW[k], rel_var[k].
+ddrw_status estimate_multi(ddrw_ctx *ctx, int nmass, const double *m2, int nhit, uint64_t seed, uint64_t hit0,
+                           const double *eta_user, double *exponents, double *logW, double *rel_var, double *delta_user,
+                           ddrw_solve_info *info)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
+    if (nhit <= 0 || nmass <= 0 || nmass > MAXM) return set_error(ctx, DDRW_EINVAL, "bad nhit or number of masses");
+    const int nrhs = nmass * nhit;
+    MassSet m2s, m1s;
+    ddrw_status st;
+    if ((st = make_massset(ctx, nmass, m2, &m2s))) return st;
+    if ((st = make_massset(ctx, 1, &ctx->m1, &m1s))) return st;
+    double2 *F[5];
+    if ((st = fields(ctx, "est_f", 5, nrhs, F))) return st;
+    double2 *eta = F[0], *r = F[1], *delta = F[2];
+    double2 *work[3] = {F[3], F[4], F[2]};
+    const size_t pbytes = sizeof(double) * 24 * ctx->nP;
+    // eta for every slot
+    if (eta_user) {
+        const void *d;
+        if ((st = stage_in(ctx, eta_user, pbytes * nhit, "stage_eta", &d))) return st;
+        unpack_P64(ctx, (const double *)d, eta, nhit);
+        long n = 12 * ctx->V;
+        if (nmass > 1) k_replicate<<<(unsigned)((n * nhit + 255) / 256), 256, 0, ctx->stream>>>(n, nhit, nmass, eta);
+    } else {
+        DDRW_CUDA_CHECK(cudaMemsetAsync(eta, 0, sizeof(double2) * 12 * ctx->V * nrhs, ctx->stream));
+        noise_launch(ctx, seed, hit0, nhit, nmass, eta, nullptr);
+    }
+    SolveStats stats;
+    ddrw_status conv = DDRW_OK;
+    if ((st = apply_dA_fields(ctx, m2s, m1s, eta, r, work, nrhs, &stats))) return st;
+    double2 *w2[2] = {F[3], F[4]};
+    st = solve_schur_fields(ctx, m2s, r, delta, w2, nrhs, &stats);
+    if (st == DDRW_ENOCONV) conv = st;
+    else if (st) return st;
+    // e = ||delta||^2 + 2 Re <eta, delta> over the black sites
+    double *red;
+    if ((st = workspace(ctx, "est_red", sizeof(double) * 4 * nrhs, (void **)&red))) return st;
+    long vbh = (long)ctx->l * ctx->l * ctx->l * ctx->l / 2, nc = (long)ctx->nblk_c * vbh;
+    for (int p = 0; p < 2; p++)
+        if ((st = Blas<PrecD>::norm_dot(ctx, VecRange{ctx->V, p * ctx->vh, nc, 12 * ctx->V, nrhs}, delta, eta,
+                                        red + 2 * p * nrhs)))
+            return st;
+    std::vector<double> h(4 * nrhs);
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(h.data(), red, sizeof(double) * 4 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    if (delta_user) {
+        void *dd;
+        bool host;
+        if ((st = stage_out(ctx, delta_user, pbytes * nrhs, "stage_delta", &dd, &host))) return st;
+        pack_P64(ctx, delta, (double *)dd, nrhs);
+        if ((st = finish_out(ctx, delta_user, dd, pbytes * nrhs, host))) return st;
+    }
+    if ((st = sync(ctx))) return st;
+    bool bad = false;
+    for (int k = 0; k < nmass; k++) {
+        std::vector<double> e(nhit);
+        for (int j = 0; j < nhit; j++) {
+            int rr = k * nhit + j;
+            double nn = h[2 * rr] + h[2 * nrhs + 2 * rr], dr = h[2 * rr + 1] + h[2 * nrhs + 2 * rr + 1];
+            e[j] = nn + 2.0 * dr;
+            if (!(e[j] == e[j])) bad = true;
+            if (exponents) exponents[rr] = e[j];
+        }
+        // log W = log((1/N) sum exp(-e_j)) by log-sum-exp; rel_var = var(exp(-e)) / W^2
+        double mx = -e[0];
+        for (int j = 1; j < nhit; j++) mx = std::max(mx, -e[j]);
+        double s = 0, s2 = 0;
+        for (int j = 0; j < nhit; j++) {
+            double w = std::exp(-e[j] - mx);
+            s += w;
+            s2 += w * w;
+        }
+        double mean = s / nhit;
+        if (logW) logW[k] = mx + std::log(mean);
+        if (rel_var) rel_var[k] = nhit > 1 ? (s2 / nhit - mean * mean) * nhit / (nhit - 1) / (mean * mean) : 0.0;
+    }
+    fill_info(info, stats, elapsed(t0));
+    if (bad) return set_error(ctx, DDRW_ENUMERIC, "NaN exponent");
+    return conv;
+}
+
+}  // namespace ddrw
+
+using namespace ddrw;
+
+extern "C" {
+
+ddrw_status ddrw_noise(ddrw_ctx *ctx, uint64_t seed, uint64_t hit_offset, int nhit, double *eta)
+{
+    if (!ctx || !eta || nhit <= 0) return set_error(ctx, DDRW_EINVAL, "bad argument");
+    cudaSetDevice(ctx->device);
+    size_t bytes = sizeof(double) * 24 * ctx->nP * nhit;
+    void *d;
+    bool host;
+    ddrw_status st;
+    if ((st = stage_out(ctx, eta, bytes, "stage_noise", &d, &host))) return st;
+    noise_launch(ctx, seed, hit_offset, nhit, 1, nullptr, (double *)d);
+    if ((st = finish_out(ctx, eta, d, bytes, host))) return st;
+    return sync(ctx);
+}
+
+ddrw_status ddrw_estimate(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64_t hit_offset, const double *eta,
+                          double *exponents, double *logW, double *rel_var, double *delta, ddrw_solve_info *info)
+{
+    if (!ctx) return DDRW_EINVAL;
+    cudaSetDevice(ctx->device);
+    return estimate_multi(ctx, 1, &ctx->m2, nhit, seed, hit_offset, eta, exponents, logW, rel_var, delta, info);
+}
+
+ddrw_status ddrw_estimate_masses(ddrw_ctx *ctx, int nmass, const double *m2, int nhit, uint64_t seed,
+                                 uint64_t hit_offset, double *exponents, double *logW, double *rel_var,
+                                 ddrw_solve_info *info)
+{
+    if (!ctx || !m2) return set_error(ctx, DDRW_EINVAL, "bad argument");
+    cudaSetDevice(ctx->device);
+    return estimate_multi(ctx, nmass, m2, nhit, seed, hit_offset, nullptr, exponents, logW, rel_var, nullptr, info);
+}
+
+ddrw_status ddrw_apply_dA(ddrw_ctx *ctx, const double *eta, double *r, int nrhs, ddrw_solve_info *info)
+{
+    if (!ctx || !eta || !r || nrhs <= 0) return set_error(ctx, DDRW_EINVAL, "bad argument");
+    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
+    cudaSetDevice(ctx->device);
+    auto t0 = std::chrono::steady_clock::now();
+    MassSet m2s, m1s;
+    ddrw_status st;
+    if ((st = make_massset(ctx, 1, &ctx->m2, &m2s))) return st;
+    if ((st = make_massset(ctx, 1, &ctx->m1, &m1s))) return st;
+    double2 *F[5];
+    if ((st = fields(ctx, "est_f", 5, nrhs, F))) return st;
+    size_t pbytes = sizeof(double) * 24 * ctx->nP * nrhs;
+    const void *din;
+    void *dout;
+    bool host;
+    if ((st = stage_in(ctx, eta, pbytes, "stage_in", &din))) return st;
+    if ((st = stage_out(ctx, r, pbytes, "stage_out", &dout, &host))) return st;
+    unpack_P64(ctx, (const double *)din, F[0], nrhs);
+    SolveStats stats;
+    double2 *work[3] = {F[2], F[3], F[4]};
+    if ((st = apply_dA_fields(ctx, m2s, m1s, F[0], F[1], work, nrhs, &stats))) return st;
+    pack_P64(ctx, F[1], (double *)dout, nrhs);
+    if ((st = finish_out(ctx, r, dout, pbytes, host))) return st;
+    st = sync(ctx);
+    fill_info(info, stats, elapsed(t0));
+    return st;
+}
+
+ddrw_status ddrw_solve_schur(ddrw_ctx *ctx, double m, const double *b, double *x, int nrhs, ddrw_solve_info *info)
+{
+    if (!ctx || !b || !x || nrhs <= 0) return set_error(ctx, DDRW_EINVAL, "bad argument");
+    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
+    cudaSetDevice(ctx->device);
+    auto t0 = std::chrono::steady_clock::now();
+    MassSet ms;
+    ddrw_status st;
+    if ((st = make_massset(ctx, 1, &m, &ms))) return st;
+    double2 *F[4];
+    if ((st = fields(ctx, "sch_f", 4, nrhs, F))) return st;
+    size_t pbytes = sizeof(double) * 24 * ctx->nP * nrhs;
+    const void *din;
+    void *dout;
+    bool host;
+    if ((st = stage_in(ctx, b, pbytes, "stage_in", &din))) return st;
+    if ((st = stage_out(ctx, x, pbytes, "stage_out", &dout, &host))) return st;
+    unpack_P64(ctx, (const double *)din, F[0], nrhs);
+    SolveStats stats;
+    double2 *work[2] = {F[2], F[3]};
+    ddrw_status conv = solve_schur_fields(ctx, ms, F[0], F[1], work, nrhs, &stats);
+    if (conv && conv != DDRW_ENOCONV) return conv;
+    pack_P64(ctx, F[1], (double *)dout, nrhs);
+    if ((st = finish_out(ctx, x, dout, pbytes, host))) return st;
+    if ((st = sync(ctx))) return st;
+    fill_info(info, stats, elapsed(t0));
+    return conv;
+}
+
+ddrw_status ddrw_apply_schur(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs)
+{
+    if (!ctx || !in || !out || nrhs <= 0) return set_error(ctx, DDRW_EINVAL, "bad argument");
+    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
+    cudaSetDevice(ctx->device);
+    MassSet ms;
+    ddrw_status st;
+    if ((st = make_massset(ctx, 1, &m, &ms))) return st;
+    double2 *F[4];
+    if ((st = fields(ctx, "sch_f", 4, nrhs, F))) return st;
+    size_t pbytes = sizeof(double) * 24 * ctx->nP * nrhs, fb = sizeof(double2) * 12 * ctx->V * nrhs;
+    const void *din;
+    void *dout;
+    bool host;
+    if ((st = stage_in(ctx, in, pbytes, "stage_in", &din))) return st;
+    if ((st = stage_out(ctx, out, pbytes, "stage_out", &dout, &host))) return st;
+    const bool mixed = ctx->prec != DDRW_FP64;
+    unpack_P64(ctx, (const double *)din, F[0], nrhs);
+    // A v = v - P D_bb^-1 D_bw D_ww^-1 D_wb v
+    DDRW_CUDA_CHECK(cudaMemsetAsync(F[1], 0, fb, ctx->stream));
+    hop_between(ctx, DDRW_WHITE, F[0], F[1], nrhs);
+    if ((st = block_solve64(ctx, DDRW_WHITE, ms, F[1], F[2], nrhs, ctx->tol_block, ctx->maxiter, mixed, nullptr))) return st;
+    DDRW_CUDA_CHECK(cudaMemsetAsync(F[1], 0, fb, ctx->stream));
+    hop_between(ctx, DDRW_BLACK, F[2], F[1], nrhs);
+    if ((st = block_solve64(ctx, DDRW_BLACK, ms, F[1], F[3], nrhs, ctx->tol_block, ctx->maxiter, mixed, nullptr))) return st;
+    GeomDev g = geom_dev(ctx);
+    dim3 grid((unsigned)((ctx->V + 127) / 128), (unsigned)nrhs);
+    DISPATCH_BL(ctx, k_delta, grid, 128, g, F[0], F[3], F[1], 12 * ctx->V);
+    pack_P64(ctx, F[1], (double *)dout, nrhs);
+    if ((st = finish_out(ctx, out, dout, pbytes, host))) return st;
+    return sync(ctx);
+}
+
+ddrw_status ddrw_solve_block(ddrw_ctx *ctx, int colour, double m, const double *b, double *x, int nrhs,
+                             ddrw_solve_info *info)
+{
+    if (!ctx || !b || !x || nrhs <= 0 || (colour != DDRW_BLACK && colour != DDRW_WHITE))
+        return set_error(ctx, DDRW_EINVAL, "bad argument");
+    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
+    cudaSetDevice(ctx->device);
+    auto t0 = std::chrono::steady_clock::now();
+    MassSet ms;
+    ddrw_status st;
+    if ((st = make_massset(ctx, 1, &m, &ms))) return st;
+    double2 *F[2];
+    if ((st = fields(ctx, "api_s", 2, nrhs, F))) return st;
+    size_t ub = sizeof(double) * 24 * ctx->V * nrhs;
+    const void *din;
+    void *dout;
+    bool host;
+    if ((st = stage_in(ctx, b, ub, "stage_in", &din))) return st;
+    if ((st = stage_out(ctx, x, ub, "stage_out", &dout, &host))) return st;
+    pack_spinor64(ctx, (const double *)din, F[0], nrhs);
+    DDRW_CUDA_CHECK(cudaMemsetAsync(F[1], 0, sizeof(double2) * 12 * ctx->V * nrhs, ctx->stream));
+    SolveStats stats;
+    st = block_solve64(ctx, colour, ms, F[0], F[1], nrhs, ctx->tol_block, ctx->maxiter, ctx->prec != DDRW_FP64, &stats);
+    if (st && st != DDRW_ENOCONV) return st;
+    ddrw_status conv = st;
+    unpack_spinor64(ctx, F[1], (double *)dout, nrhs);
+    if ((st = finish_out(ctx, x, dout, ub, host))) return st;
+    if ((st = sync(ctx))) return st;
+    if (info) {
+        fill_info(info, stats, elapsed(t0));
+        info->true_rel_residual = stats.block_rel_residual;
+        info->cycles = stats.block_cycles;
+    }
+    return conv;
+}
+
+ddrw_status ddrw_solve_D(ddrw_ctx *ctx, double m, const double *b, double *x, int nrhs, ddrw_solve_info *info)
+{
+    if (!ctx || !b || !x || nrhs <= 0) return set_error(ctx, DDRW_EINVAL, "bad argument");
+    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
+    cudaSetDevice(ctx->device);
+    auto t0 = std::chrono::steady_clock::now();
+    MassSet ms;
+    ddrw_status st;
+    if ((st = make_massset(ctx, 1, &m, &ms))) return st;
+    double2 *F[2];
+    if ((st = fields(ctx, "api_s", 2, nrhs, F))) return st;
+    size_t ub = sizeof(double) * 24 * ctx->V * nrhs;
+    const void *din;
+    void *dout;
+    bool host;
+    if ((st = stage_in(ctx, b, ub, "stage_in", &din))) return st;
+    if ((st = stage_out(ctx, x, ub, "stage_out", &dout, &host))) return st;
+    pack_spinor64(ctx, (const double *)din, F[0], nrhs);
+    SolveStats stats;
+    st = full_solve64(ctx, ms, F[0], F[1], nrhs, ctx->tol_outer, ctx->maxiter, ctx->prec, &stats);
+    if (st && st != DDRW_ENOCONV) return st;
+    ddrw_status conv = st;
+    unpack_spinor64(ctx, F[1], (double *)dout, nrhs);
+    if ((st = finish_out(ctx, x, dout, ub, host))) return st;
+    if ((st = sync(ctx))) return st;
+    fill_info(info, stats, elapsed(t0));
+    return conv;
+}
+
+}  // extern "C"

@@ -1,0 +1,277 @@
+// solver.cu -- the full-lattice Krylov solver (K8): x = D(m)^-1 b, used for the inverse of the
+// Schur complement through Dhat^-1 = 1 - P Dcal_bw D_wb (Sec. 1: one Dirac inversion per estimate).
+//
+//   even-odd reduction:  Mhat = A_ee - 1/4 H_eo A_oo^-1 H_oe,  btil_e = b_e + 1/2 H_eo A_oo^-1 b_o,
+//                        x_o = A_oo^-1 (b_o + 1/2 H_oe x_e)
+//   Krylov method:       BiCGStab on Mhat x_e = btil_e, all right-hand sides in lockstep with their
+//                        own scalars (device resident); a right-hand side that has converged stops
+//                        updating while the others continue.
+//   precision:           FP64 defect correction around the inner solve:
+//                        r = b - D x (FP64 stencil), inner solve D e = r / ||r|| in FP64 (FP64 path)
+//                        or FP32 (mixed path), x += ||r|| e, until ||b - D x|| <= tol ||b||.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "blas.cuh"
+#include "ctx.h"
+
+namespace ddrw {
+
+ddrw_status make_massset(ddrw_ctx *ctx, int n, const double *m, MassSet *ms)
+{
+    if (n < 1 || n > MAXM) return set_error(ctx, DDRW_EINVAL, "1 to 8 masses per call");
+    ms->n = n;
+    for (int k = 0; k < n; k++) {
+        ms->m[k] = m[k];
+        ddrw_status st = mass_inverse(ctx, m[k], &ms->inv[k]);
+        if (st) return st;
+    }
+    return DDRW_OK;
+}
+
+namespace {
+
+template <class P> struct EoSpace {
+    using E = typename P::SElem;
+    E *r, *rh, *p, *v, *t, *tmp;
+};
+
+template <class P> void stencil(ddrw_ctx *ctx, const DslashCall &c)
+{
+    if constexpr (sizeof(typename P::R) == 8) dslash64(ctx, c);
+    else dslash32(ctx, c);
+}
+
+template <class P> DslashCall base_call(const ddrw_ctx *ctx, const MassSet &ms, int nrhs, long rs)
+{
+    DslashCall c;
+    c.rstride = rs;
+    c.nrhs = nrhs;
+    c.nmass = ms.n;
+    for (int k = 0; k < ms.n; k++) {
+        c.masses[k] = ms.m[k];
+        if constexpr (sizeof(typename P::R) == 8) c.Ainv[k] = ms.inv[k]->A64;
+        else c.Ainv[k] = ms.inv[k]->A32;
+    }
+    c.blk0 = 0;
+    c.nblk = ctx->nblk;
+    c.npar = 1;
+    return c;
+}
+
+// out_e = Mhat in_e  (tmp on odd sites)
+template <class P>
+void apply_mhat(ddrw_ctx *ctx, const MassSet &ms, int nrhs, long rs, const typename P::SElem *in,
+                typename P::SElem *tmp, typename P::SElem *out)
+{
+    DslashCall c = base_call<P>(ctx, ms, nrhs, rs);
+    c.in = in;
+    c.out = tmp;
+    c.beta = 1.0;
+    c.post = 1;
+    c.par0 = 1;
+    stencil<P>(ctx, c);
+    DslashCall d = base_call<P>(ctx, ms, nrhs, rs);
+    d.in = tmp;
+    d.x = in;
+    d.out = out;
+    d.alpha = 1.0;
+    d.beta = -0.25;
+    d.diag = 1;
+    d.par0 = 0;
+    stencil<P>(ctx, d);
+}
+
+// Inner even-odd BiCGStab in policy P: solve D x = b (full fields) to relative tolerance tol
+// against ||b|| (bb: host ||b||^2 per rhs).  Adds iterations to *iters.
+template <class P>
+ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SElem *b, typename P::SElem *x, int nrhs,
+                        const std::vector<double> &bb, double tol, int maxiter, int *iters)
+{
+    using E = typename P::SElem;
+    const long rs = (long)P::SPLANES * ctx->V;
+    const size_t fb = sizeof(E) * rs * nrhs;
+    const char *names[6] = {"eo_r", "eo_rh", "eo_p", "eo_v", "eo_t", "eo_tmp"};
+    void *w[6];
+    ddrw_status st;
+    for (int k = 0; k < 6; k++) {
+        char nm[32];
+        snprintf(nm, sizeof nm, "%s%d", names[k], (int)sizeof(typename P::R));
+        if ((st = workspace(ctx, nm, fb, &w[k]))) return st;
+    }
+    E *r = (E *)w[0], *rh = (E *)w[1], *p = (E *)w[2], *v = (E *)w[3], *t = (E *)w[4], *tmp = (E *)w[5];
+    KScal *sc;
+    if ((st = workspace(ctx, "eo_kscal", sizeof(KScal) * nrhs, (void **)&sc))) return st;
+
+    // btil_e = b_e + 1/2 H_eo A_oo^-1 b_o  (into r)
+    DslashCall c = base_call<P>(ctx, ms, nrhs, rs);
+    c.x = b;
+    c.out = tmp;
+    c.alpha = 1.0;
+    c.diag = 2;
+    c.post = 1;
+    c.par0 = 1;
+    stencil<P>(ctx, c);
+    DslashCall d = base_call<P>(ctx, ms, nrhs, rs);
+    d.in = tmp;
+    d.x = b;
+    d.out = r;
+    d.alpha = 1.0;
+    d.beta = 0.5;
+    d.diag = 2;
+    d.par0 = 0;
+    stencil<P>(ctx, d);
+
+    std::vector<KScal> h(nrhs);
+    for (int k = 0; k < nrhs; k++) {
+        h[k] = KScal{};
+        h[k].thresh = tol * tol * bb[k];
+        h[k].maxiter = maxiter;
+    }
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(sc, h.data(), sizeof(KScal) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+    VecRange ev{ctx->V, 0, ctx->vh, rs, nrhs};
+    if ((st = Blas<P>::bicg_init(ctx, ev, r, rh, p, x, sc))) return st;
+
+    KScal *hs = (KScal *)ctx->h_pinned;
+    const int check = sizeof(typename P::R) == 8 ? 1 : 4;
+    int it = 0;
+    for (;;) {
+        for (int k = 0; k < check; k++) {
+            apply_mhat<P>(ctx, ms, nrhs, rs, p, tmp, v);
+            if ((st = Blas<P>::bicg_alpha(ctx, ev, rh, v, sc))) return st;
+            Blas<P>::bicg_s(ctx, ev, r, v, sc);
+            apply_mhat<P>(ctx, ms, nrhs, rs, r, tmp, t);
+            if ((st = Blas<P>::bicg_omega(ctx, ev, t, r, sc))) return st;
+            if ((st = Blas<P>::bicg_xr(ctx, ev, x, p, r, t, rh, sc))) return st;
+            Blas<P>::bicg_p(ctx, ev, p, r, v, sc);
+            it++;
+        }
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, sc, sizeof(KScal) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+        DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        int active = 0;
+        for (int k = 0; k < nrhs; k++) active += hs[k].active;
+        if (!active || it >= maxiter) break;
+    }
+    int itmax = 0;
+    for (int k = 0; k < nrhs; k++) itmax = std::max(itmax, hs[k].iters);
+    *iters += itmax;
+    // x_o = A_oo^-1 (b_o + 1/2 H_oe x_e)
+    DslashCall e = base_call<P>(ctx, ms, nrhs, rs);
+    e.in = x;
+    e.x = b;
+    e.out = x;
+    e.alpha = 1.0;
+    e.beta = 0.5;
+    e.diag = 2;
+    e.post = 1;
+    e.par0 = 1;
+    stencil<P>(ctx, e);
+    return DDRW_OK;
+}
+
+ddrw_status full_norms(ddrw_ctx *ctx, const double2 *f, int nrhs, std::vector<double> &out)
+{
+    double *d;
+    ddrw_status st = workspace(ctx, "full_norms", sizeof(double) * nrhs, (void **)&d);
+    if (st) return st;
+    VecRange all{ctx->V, 0, ctx->V, 12 * ctx->V, nrhs};
+    if ((st = Blas<PrecD>::norm2(ctx, all, f, d))) return st;
+    out.resize(nrhs);
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(out.data(), d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    return DDRW_OK;
+}
+
+}  // namespace
+
+ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, double2 *x, int nrhs, double tol,
+                         int maxiter, ddrw_prec prec, SolveStats *stats)
+{
+    const long V = ctx->V, rs64 = 12 * V, rs32 = 6 * V;
+    const size_t f64 = sizeof(double2) * rs64 * nrhs, f32 = sizeof(float4) * rs32 * nrhs;
+    const bool mixed = prec != DDRW_FP64;
+    ddrw_status st;
+    std::vector<double> bb, rr;
+    if ((st = full_norms(ctx, b, nrhs, bb))) return st;
+    double2 *res, *e64 = nullptr;
+    float4 *b32 = nullptr, *e32 = nullptr;
+    double *scale_d = nullptr;
+    if ((st = workspace(ctx, "full_res", f64, (void **)&res))) return st;
+    if (mixed) {
+        if ((st = workspace(ctx, "full_b32", f32, (void **)&b32))) return st;
+        if ((st = workspace(ctx, "full_e32", f32, (void **)&e32))) return st;
+        if ((st = workspace(ctx, "full_scale", sizeof(double) * 2 * nrhs, (void **)&scale_d))) return st;
+    } else if ((st = workspace(ctx, "full_e64", f64, (void **)&e64))) {
+        return st;
+    }
+    const double tol_inner = mixed ? std::max(tol, 1e-6) : tol * 0.5;
+    const double2 *rhs = b;
+    bool first = true;
+    std::vector<double> scale(nrhs), unscale(nrhs), ones(nrhs, 1.0);
+    int iters = 0, cycles = 0;
+    for (; cycles < 40; cycles++) {
+        const std::vector<double> &nr = first ? bb : rr;
+        if (mixed) {
+            for (int r = 0; r < nrhs; r++) {
+                double n = std::sqrt(nr[r]);
+                scale[r] = n > 0 ? 1.0 / n : 0.0;
+                unscale[r] = n;
+            }
+            DDRW_CUDA_CHECK(cudaMemcpyAsync(scale_d, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+            DDRW_CUDA_CHECK(cudaMemcpyAsync(scale_d + nrhs, unscale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice,
+                                            ctx->stream));
+            VecRange all{V, 0, V, rs64, nrhs};
+            to32(ctx, all, rs32, rhs, b32, scale_d);
+            std::vector<double> unit(nrhs);
+            for (int r = 0; r < nrhs; r++) unit[r] = nr[r] > 0 ? 1.0 : 0.0;
+            if ((st = eo_bicgstab<PrecS>(ctx, ms, b32, e32, nrhs, unit, tol_inner, maxiter, &iters))) return st;
+            if (first) DDRW_CUDA_CHECK(cudaMemsetAsync(x, 0, f64, ctx->stream));
+            add32(ctx, all, rs32, e32, x, scale_d + nrhs);
+        } else {
+            double2 *target = first ? x : e64;
+            if ((st = eo_bicgstab<PrecD>(ctx, ms, rhs, target, nrhs, nr, tol_inner, maxiter, &iters))) return st;
+            if (!first) Blas<PrecD>::axpby(ctx, VecRange{V, 0, V, rs64, nrhs}, 1.0, e64, 1.0, x);
+        }
+        // res = b - D x in FP64
+        DslashCall c;
+        c.in = x;
+        c.x = x;
+        c.out = res;
+        c.rstride = rs64;
+        c.nrhs = nrhs;
+        c.nmass = ms.n;
+        for (int k = 0; k < ms.n; k++) {
+            c.masses[k] = ms.m[k];
+            c.Ainv[k] = ms.inv[k]->A64;
+        }
+        c.alpha = -1.0;
+        c.beta = 0.5;
+        c.diag = 1;
+        c.blk0 = 0;
+        c.nblk = ctx->nblk;
+        c.par0 = 0;
+        c.npar = 2;
+        dslash64(ctx, c);
+        if (stats) stats->fp64_dslash_full += 1;
+        Blas<PrecD>::axpby(ctx, VecRange{V, 0, V, rs64, nrhs}, 1.0, b, 1.0, res);
+        if ((st = full_norms(ctx, res, nrhs, rr))) return st;
+        double worst = 0;
+        for (int r = 0; r < nrhs; r++)
+            if (bb[r] > 0) worst = std::max(worst, std::sqrt(rr[r] / bb[r]));
+        if (stats) {
+            stats->outer_cycles = cycles + 1;
+            stats->outer_rel_residual = worst;
+        }
+        if (!(worst == worst)) return set_error(ctx, DDRW_ENUMERIC, "NaN in the outer solve");
+        if (worst <= tol) break;
+        if (iters >= maxiter * 4) break;
+        rhs = res;
+        first = false;
+    }
+    if (stats) stats->outer_iters += iters;
+    if (stats && stats->outer_rel_residual > tol) return set_error(ctx, DDRW_ENOCONV, "outer solve did not converge");
+    return DDRW_OK;
+}
+
+}  // namespace ddrw

@@ -1,0 +1,178 @@
+"""Parity of the solver and estimate path (K3, K6, K7, K8, K9, K10) with the CPU oracle.
+
+Bars: block solves to the block tolerance, the full solve to the outer tolerance (true FP64
+residual), r and delta to 1e-10 relative, exponents e_j and log W to 1e-8 relative
+(|d| <= 1e-8 max(|x|, 1)), noise to 1e-15 (same Philox integers, libm vs CUDA transcendental
+rounding).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import core as oc
+from paper_1211_1214_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # name, dims, l, eps, csw, m1, m2, nhit
+    ("c1_4x4x4x4_l2", (4, 4, 4, 4), 2, 0.3, 1.0, 0.20, 0.19, 8),
+    ("8x8x8x8_l4", (8, 8, 8, 8), 4, 0.25, 1.5, 0.10, 0.09, 2),
+    ("12x12x12x12_l6", (12, 12, 12, 12), 6, 0.2, 1.9, 0.10, 0.08, 1),
+]
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def close(a, b, tol=1e-8):
+    return abs(a - b) <= tol * max(abs(b), 1.0)
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: c[0])
+def case(request):
+    name, dims, l, eps, csw, m1, m2, nhit = request.param
+    U = synth.gauge_field(dims, eps, seed=1)
+    ctx = binding.Context(dims, (l,) * 4)
+    ctx.load_gauge(torch.from_numpy(U).cuda())
+    ctx.set_params(csw, m1, m2)
+    ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+    lat = oc.Lattice(dims, (l,) * 4, U, csw)
+    yield dict(ctx=ctx, lat=lat, dims=dims, m1=m1, m2=m2, nhit=nhit, l=l)
+    ctx.close()
+
+
+def test_noise_matches_oracle_philox(case):
+    ctx = case["ctx"]
+    eta = torch.zeros((3, ctx.nP, 4, 3), dtype=torch.complex128, device="cuda")
+    ctx.noise(2, 5, 3, eta)
+    want = oc.noise_packed(2, 5, 3, ctx.nP * 12).reshape(3, ctx.nP, 4, 3)
+    assert np.max(np.abs(eta.cpu().numpy() - want)) < 1e-14
+    # P has the size the oracle's projector has
+    assert ctx.nP == len(case["lat"].suppP_sites())
+
+
+@pytest.mark.parametrize("colour", [0, 1])
+def test_block_solve(case, colour):
+    ctx, lat, dims = case["ctx"], case["lat"], case["dims"]
+    b = synth.spinor_field(dims, seed=31, nrhs=2)
+    x = np.zeros_like(b)
+    info = ctx.solve_block(colour, case["m2"], b, x, nrhs=2)
+    col = lat.colour()
+    for r in range(2):
+        bc = b[r].copy()
+        bc[col != colour] = 0
+        res = bc - lat.apply(case["m2"], x[r], rows=colour, cols=colour)
+        assert np.linalg.norm(res) / np.linalg.norm(bc) < 2e-13
+        assert np.max(np.abs(x[r][col != colour])) == 0.0
+    assert info["block_iters_max"] > 0
+
+
+def test_full_solve(case):
+    ctx, lat, dims = case["ctx"], case["lat"], case["dims"]
+    b = synth.spinor_field(dims, seed=32)
+    x = np.zeros_like(b)
+    info = ctx.solve_D(case["m2"], b, x)
+    res = np.linalg.norm(b - lat.apply(case["m2"], x)) / np.linalg.norm(b)
+    assert res <= 1e-10
+    assert info["true_rel_residual"] <= 1e-10
+
+
+def oracle_schur(lat, m, v_full):
+    """A(m) v = v - P D_bb^-1 D_bw D_ww^-1 D_wb v from the oracle's operator and CGNR."""
+    u = lat.apply(m, v_full, rows=oc.WHITE, cols=oc.BLACK)
+    a, _, _ = lat.solve(m, u, sel=oc.WHITE, tol=1e-13)
+    c = lat.apply(m, a, rows=oc.BLACK, cols=oc.WHITE)
+    y, _, _ = lat.solve(m, c, sel=oc.BLACK, tol=1e-13)
+    P = lat.suppP().astype(bool)
+    out = v_full - y
+    out[~P] = 0
+    return out
+
+
+def test_apply_schur(case):
+    ctx, lat = case["ctx"], case["lat"]
+    v = synth.complex_gaussian((1, ctx.nP, 4, 3), seed=33)
+    out = np.zeros_like(v)
+    ctx.apply_schur(case["m2"], v, out)
+    want = lat.pack(oracle_schur(lat, case["m2"], lat.unpack(v[0].reshape(-1))))
+    assert rel(out[0].reshape(-1), want) < 1e-11
+
+
+def test_dA_and_delta_and_exponent(case):
+    """r = (A(m1) - A(m2)) eta, delta = A(m2)^-1 r and e_j against the oracle's own chain."""
+    ctx, lat = case["ctx"], case["lat"]
+    nhit = case["nhit"]
+    eta = oc.noise_packed(2, 0, nhit, ctx.nP * 12)
+    eta_t = torch.from_numpy(eta.reshape(nhit, ctx.nP, 4, 3)).cuda()
+    r = torch.zeros_like(eta_t)
+    ctx.apply_dA(eta_t, r, nrhs=nhit)
+    delta = torch.zeros_like(eta_t)
+    e, logw, relvar, info = ctx.estimate(nhit, eta=eta_t, delta=delta)
+    r_h, d_h = r.cpu().numpy().reshape(nhit, -1), delta.cpu().numpy().reshape(nhit, -1)
+    e_orc = []
+    for j in range(nhit):
+        res = lat.exponent(case["m1"], case["m2"], lat.unpack(eta[j]))
+        assert rel(r_h[j], lat.pack(res["r"])) < 1e-10
+        assert rel(d_h[j], lat.pack(res["delta"])) < 1e-8
+        assert close(e[j], res["e"]), (j, e[j], res["e"])
+        e_orc.append(res["e"])
+    assert close(logw, oc.log_w(e_orc))
+    assert info["true_rel_residual"] <= 1e-10
+
+
+def test_estimate_with_own_noise_equals_estimate_with_passed_noise(case):
+    ctx = case["ctx"]
+    nhit = 2
+    eta = torch.zeros((nhit, ctx.nP, 4, 3), dtype=torch.complex128, device="cuda")
+    ctx.noise(7, 3, nhit, eta)
+    e1, lw1, _, _ = ctx.estimate(nhit, seed=7, hit_offset=3)
+    e2, lw2, _, _ = ctx.estimate(nhit, eta=eta)
+    assert np.allclose(e1, e2, rtol=1e-12, atol=1e-14)
+
+
+def test_zero_mass_shift():
+    dims, l = (4, 4, 4, 8), 2
+    U = synth.gauge_field(dims, 0.3, seed=2)
+    ctx = binding.Context(dims, (l,) * 4)
+    ctx.load_gauge(U)
+    ctx.set_params(1.0, 0.15, 0.15)
+    e, lw, _, _ = ctx.estimate(2)
+    assert np.all(e == 0.0) and lw == 0.0
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [binding.MIXED_FP32])
+def test_mixed_precision_estimate_matches_fp64(case, prec):
+    ctx = case["ctx"]
+    nhit = min(case["nhit"], 4)
+    e64, lw64, _, _ = ctx.estimate(nhit, seed=2)
+    ctx.set_solver(prec, tol_outer=1e-10, tol_block=1e-12)
+    try:
+        e, lw, _, info = ctx.estimate(nhit, seed=2)
+    finally:
+        ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+    for j in range(nhit):
+        assert close(e[j], e64[j]), (j, e[j], e64[j])
+    assert close(lw, lw64)
+    assert info["true_rel_residual"] <= 1e-10
+
+
+def test_batched_masses_match_single_mass_calls(case):
+    ctx = case["ctx"]
+    m1 = case["m1"]
+    m2s = [m1 - 0.002, m1 - 0.005, m1 - 0.01]
+    nhit = 2
+    E, LW, RV, _ = ctx.estimate_masses(m2s, nhit, seed=4)
+    for k, m2 in enumerate(m2s):
+        ctx.set_params(ctx_csw(case), m1, m2)
+        e, lw, _, _ = ctx.estimate(nhit, seed=4)
+        assert np.allclose(E[k], e, rtol=1e-9, atol=1e-12)
+        assert close(LW[k], lw, 1e-9)
+    ctx.set_params(ctx_csw(case), m1, case["m2"])
+
+
+def ctx_csw(case):
+    return case["lat"].csw
