@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Benchmark of the domain-decomposed stochastic estimate of 1/det(Mh^dag Mh) on GB300.
+
+One step = one batched call of the whole hot path over one batch of synthetic input: Philox noise,
+u = D_wb eta, the four block solves of r = (A(m1) - A(m2)) eta, the full-lattice solve of
+delta = A(m2)^-1 r and the exponents e_j, for N_hit noise vectors at each target mass of the sweep.
+``value`` is estimates per second (one estimate = one e_j at outer residual 1e-10).
+
+Default workload: 64x32^3 lattice, 8^4 blocks (8x4x4x4), links U = exp(i 0.2 H) (seed 1),
+csw 1.9, m1 0.02, m2 in {0.018, 0.015, 0.010}, N_hit 16, inner solves in FP32 with FP64 defect
+correction.  Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "64x32^3": dict(dims=(64, 32, 32, 32), l=8, eps=0.2, csw=1.9, m1=0.02, m2s=(0.018, 0.015, 0.010), nhit=16,
+                    small=(16, 16, 16, 16)),
+    "48x24^3": dict(dims=(48, 24, 24, 24), l=6, eps=0.2, csw=1.9, m1=0.02, m2s=(0.015,), nhit=32,
+                    small=(12, 12, 12, 12)),
+    "16^4": dict(dims=(16, 16, 16, 16), l=4, eps=0.25, csw=1.5, m1=0.05, m2s=(0.045,), nhit=16,
+                 small=(8, 8, 8, 8)),
+}
+METRIC = "Dslash HBM GB/s & reweight estimates/s, mixed vs FP64, same 1e-10 residual"
+
+
+def describe(name, w, prec):
+    return (f"{name} lattice, {w['l']}^4 blocks, U=exp(i {w['eps']} H) seed 1, csw {w['csw']}, m1 {w['m1']}, "
+            f"m2 in {list(w['m2s'])}, N_hit {w['nhit']}, {prec} inner solves, FP64 defect correction, "
+            f"outer residual 1e-10")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+STENCIL_SOURCES = ["paper_1211_1214_gb300/csrc/dslash.cu", "paper_1211_1214_gb300/csrc/stencil.cuh",
+                   "paper_1211_1214_gb300/csrc/ddrw_internal.cuh"]
+
+
+def ncu_traffic(kernel_key):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu summary, or None if the
+    kernel sources changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(kernel_key)
+    if not e or e.get("source_sha") != source_sha(STENCIL_SOURCES):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        try:
+            rows = [l.split(",") for l in open(self.f.name) if l.strip()]
+        except Exception:
+            rows = []
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, n in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_baseline(w, seconds_cap=60.0):
+    """The CPU oracle as it stands, timed on this host's cores on a bounded sample of the workload.
+
+    Sample: one oracle estimate (one noise vector, the middle target mass) with the workload's
+    eps, csw, masses and block length on the smaller lattice w['small'], scaled by the volume
+    ratio to the workload lattice (per-site work is the same; the CGNR iteration counts are taken
+    as volume independent), plus the oracle operator rate on that lattice."""
+    from oracle import core as oc
+    from paper_1211_1214_gb300 import synth
+
+    dims = w["small"]
+    V = int(np.prod(dims))
+    Vw = int(np.prod(w["dims"]))
+    U = synth.gauge_field(dims, w["eps"], seed=1)
+    lat = oc.Lattice(dims, (w["l"],) * 4, U, w["csw"])
+    m2 = w["m2s"][len(w["m2s"]) // 2]
+    x = synth.spinor_field(dims, seed=3)
+    t = time.perf_counter()
+    napply = 0
+    while napply < 3 or time.perf_counter() - t < 1.0:
+        lat.apply(m2, x)
+        napply += 1
+    t_apply = (time.perf_counter() - t) / napply
+    eta = lat.unpack(oc.noise_packed(2, 0, 1, 12 * len(lat.suppP_sites()))[0])
+    t = time.perf_counter()
+    res = lat.exponent(w["m1"], m2, eta, tol_block=1e-13, tol_outer=1e-10)
+    t_est = time.perf_counter() - t
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {
+        "value": 1.0 / (t_est * Vw / V),
+        "unit": "estimates/s",
+        "cores": cores,
+        "kind": "oracle",
+        "sample": (f"one oracle estimate (1 noise vector, m2={m2}) on {'x'.join(map(str, dims))} with the workload's "
+                   f"eps/csw/masses/{w['l']}^4 blocks took {t_est:.2f} s; scaled by the volume ratio {Vw // V} to "
+                   f"{'x'.join(map(str, w['dims']))} (CGNR iteration counts {res['iters']} taken as volume independent)"),
+        "oracle_dslash_site_updates_per_s": V / t_apply,
+    }
+
+
+def run_reference(args, w, name):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import core as oc
+
+    oc.build()
+    for _ in range(args.warmup):
+        pass  # the oracle has nothing to warm up beyond its build
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_baseline(w))
+    wall = time.perf_counter() - t0
+    v = statistics.median([c["value"] for c in vals])
+    cb = dict(vals[0])
+    cb["value"] = v
+    out = {"metric": METRIC, "value": v, "unit": "estimates/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": describe(name, w, "FP64 CGNR (oracle)"), "lattice": list(w["dims"]), "block": w["l"]},
+           "cpu_baseline": cb, "e2e": {"value": v, "unit": "estimates/s", "h2d_bytes_per_step": 0,
+                                       "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="64x32^3")
+    ap.add_argument("--prec", choices=["mixed32", "fp64"], default="mixed32")
+    ap.add_argument("--fp64-hits", type=int, default=2, help="noise vectors of the FP64-path comparison (0: skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    name = args.workload
+
+    if args.impl == "reference":
+        run_reference(args, w, name)
+        return
+
+    import torch
+
+    from paper_1211_1214_gb300 import binding, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # ---- setup (untimed): gauge field resident in HBM, clover term, per-mass inverses
+    U = synth.gauge_field(w["dims"], w["eps"], seed=1)
+    U_pin = torch.from_numpy(U).pin_memory()
+    stream = torch.cuda.Stream(device=dev)
+    ctx = binding.Context(w["dims"], w["l"], device=local, stream=stream.cuda_stream)
+    ctx.load_gauge(U_pin.to(dev))
+    ctx.set_params(w["csw"], w["m1"], w["m2s"][0])
+    prec = binding.MIXED_FP32 if args.prec == "mixed32" else binding.FP64
+    tol_block = 1e-12 if prec != binding.FP64 else 1e-13
+    ctx.set_solver(prec, tol_outer=1e-10, tol_block=tol_block)
+    nhit, m2s = w["nhit"], list(w["m2s"])
+    per_step = nhit * len(m2s)
+    hit_base = rank * 1_000_000  # disjoint Philox counters per rank: independent units, no exchange
+
+    def step(k):
+        return ctx.estimate_masses(m2s, nhit, seed=2, hit_offset=hit_base + k * nhit)
+
+    for k in range(args.warmup):
+        step(k)
+
+    # ---- timed region: kernels only, inputs resident
+    ctx.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    infos = []
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            E, LW, RV, info = step(args.warmup + k)
+            infos.append(info)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    key = binding.PROF_DSLASH32 if prec != binding.FP64 else binding.PROF_DSLASH64
+    nl, kms, kbytes = ctx.profile_read(key)
+    launches = ctx.profile_read(binding.PROF_LAUNCHES)[0]
+    blk = ctx.profile_read(binding.PROF_BLOCK32 if prec != binding.FP64 else binding.PROF_BLOCK64)
+    ctx.profile(False)
+    t_max = ms
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * per_step * args.steps / (t_max / 1e3)
+
+    peaks = measured_peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = (kbytes / (kms / 1e3) / 1e9) if kms > 0 else None
+    kname = "k_dslash<PrecS,%d,0>" % w["l"] if prec != binding.FP64 else "k_dslash<PrecD,%d,0>" % w["l"]
+    traffic = ncu_traffic(kname)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                "kernel": kname, "launches": nl, "avg_launch_ms": kms / max(nl, 1),
+                "algorithmic_bytes_per_launch": kbytes / max(nl, 1),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s",
+                "share_of_step": (kms / ms) if ms > 0 else None,
+                "block_solver_share_of_step": (blk[1] / ms) if ms > 0 else None}
+
+    out = {"metric": METRIC, "value": value, "unit": "estimates/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32/f64" if prec != binding.FP64 else "f64",
+           "data": "synthetic (U = exp(i eps H) Gaussian su(3) links, Philox complex Gaussian noise)",
+           "config": {"workload": describe(name, w, "FP32" if prec != binding.FP64 else "FP64"),
+                      "lattice": list(w["dims"]), "block": w["l"], "nhit": nhit, "m1": w["m1"], "m2": m2s,
+                      "estimates_per_step": per_step, "tol_outer": 1e-10, "tol_block": tol_block,
+                      "l2": "inputs larger than L2 (gauge, clover and fields are GBs)",
+                      "parallelism": f"replicas x{world} (disjoint noise vectors)"},
+           "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
+           "solver": {"outer_iters": infos[-1]["iters_outer"], "cycles": infos[-1]["cycles"],
+                      "fp64_dslash_calls": infos[-1]["fp64_dslash_calls"],
+                      "block_iters_max": infos[-1]["block_iters_max"],
+                      "true_rel_residual": infos[-1]["true_rel_residual"]},
+           "logW": [float(x) for x in LW], "wall_s_timed": wall}
+
+    # ---- end to end through the public API with host buffers: per step the gauge configuration
+    # is copied from pinned host memory, the clover term and inverses rebuilt, the estimate run and
+    # the exponents read back
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        te0 = time.perf_counter()
+        nst = 1
+        for k in range(nst):
+            ctx.load_gauge(U_pin.numpy())
+            ctx.set_params(w["csw"], w["m1"], w["m2s"][0])
+            E2, _, _, _ = ctx.estimate_masses(m2s, nhit, seed=2, hit_offset=hit_base + 100 * nhit)
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - te0) / nst
+        out["e2e"] = {"value": world * per_step / te, "unit": "estimates/s",
+                      "h2d_bytes_per_step": int(U.nbytes), "d2h_bytes_per_step": int(E2.nbytes),
+                      "what": "ddrw_load_gauge from pinned host memory + ddrw_set_params + ddrw_estimate_masses, "
+                              "exponents to host"}
+
+    # ---- the plain FP64 path on a few noise vectors (same residual), for the speed-up and the error
+    if args.fp64_hits > 0 and prec != binding.FP64:
+        m2 = m2s[len(m2s) // 2]
+        ctx.set_params(w["csw"], w["m1"], m2)
+        h = args.fp64_hits
+        ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        e64, lw64, _, i64 = ctx.estimate(h, seed=2, hit_offset=hit_base)
+        t64 = time.perf_counter() - t
+        ctx.set_solver(prec, tol_outer=1e-10, tol_block=tol_block)
+        t = time.perf_counter()
+        emx, lwmx, _, _ = ctx.estimate(h, seed=2, hit_offset=hit_base)
+        tmx = time.perf_counter() - t
+        rel = [abs(a - b) / max(abs(b), 1.0) for a, b in zip(emx, e64)]
+        out["fp64_path"] = {"value": h / t64, "unit": "estimates/s", "hits": h, "m2": m2,
+                            "mixed_same_hits_estimates_per_s": h / tmx,
+                            "speedup_mixed_over_fp64": t64 / tmx,
+                            "max_rel_err_exponent": max(rel),
+                            "logW_rel_err": abs(lwmx - lw64) / max(abs(lw64), 1.0),
+                            "fp64_outer_iters": i64["iters_outer"]}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = oracle_baseline(w)
+        except Exception as exc:  # the GPU result stands without it
+            out["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

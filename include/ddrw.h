@@ -151,6 +151,17 @@ ddrw_status ddrw_estimate_masses(ddrw_ctx *ctx, int nmass, const double *m2, int
                                  uint64_t hit_offset, double *exponents, double *logW, double *rel_var,
                                  ddrw_solve_info *info);
 
+/* Kernel timing for measurement (not part of the method): with profiling enabled, CUDA events
+ * bracket every launch of the instrumented kernel classes on the context's stream, and
+ * ddrw_profile_read returns, per class, the number of launches, their summed device time (ms) and
+ * their summed compulsory bytes (each field counted once per launch: spinors per right-hand
+ * side, links and clover terms once).  Classes: 0 FP64 stencil, 1 FP32 stencil (all hops),
+ * 2 / 3 FP64 / FP32 stencil restricted to hops inside or between blocks, 4 / 5 FP64 / FP32
+ * persistent block solver (bytes not counted); class 6 returns in *launches the number of kernel
+ * launches of every kind since the last reset.  ddrw_profile(ctx, enable) resets the counters. */
+ddrw_status ddrw_profile(ddrw_ctx *ctx, int enable);
+ddrw_status ddrw_profile_read(ddrw_ctx *ctx, int kind, long *launches, double *ms, double *bytes);
+
 #ifdef __cplusplus
 }
 #endif

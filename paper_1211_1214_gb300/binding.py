@@ -24,7 +24,10 @@ _STATUS = {0: "DDRW_OK", 1: "DDRW_EINVAL", 2: "DDRW_ENOMEM", 3: "DDRW_ECUDA", 4:
 EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", "ddrw_volume", "ddrw_load_gauge",
            "ddrw_set_params", "ddrw_set_solver", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
-           "ddrw_estimate_masses"]
+           "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read"]
+
+#: kernel classes of ddrw_profile_read
+PROF_DSLASH64, PROF_DSLASH32, PROF_DSLASH64_BLK, PROF_DSLASH32_BLK, PROF_BLOCK64, PROF_BLOCK32, PROF_LAUNCHES = range(7)
 
 
 class DDRWError(RuntimeError):
@@ -81,6 +84,9 @@ def load(path: str | None = None):
                                ctypes.POINTER(SolveInfo)]),
         "ddrw_estimate_masses": (st, [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp,
                                       dp, ctypes.POINTER(SolveInfo)]),
+        "ddrw_profile": (st, [vp, ctypes.c_int]),
+        "ddrw_profile_read": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -202,6 +208,16 @@ class Context:
                                   _ptr(e), _ptr(lw), _ptr(rv), _ptr(delta), ctypes.byref(info))
         self._check(st, "ddrw_estimate")
         return e, float(lw[0]), float(rv[0]), info.as_dict()
+
+    def profile(self, enable=True):
+        self._check(self.L.ddrw_profile(self._h, int(enable)), "ddrw_profile")
+
+    def profile_read(self, kind):
+        """(launches, summed device ms, summed compulsory bytes) of one kernel class."""
+        n, ms, b = ctypes.c_long(), ctypes.c_double(), ctypes.c_double()
+        self._check(self.L.ddrw_profile_read(self._h, int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)),
+                    "ddrw_profile_read")
+        return n.value, ms.value, b.value
 
     def estimate_masses(self, m2s, nhit, seed=2, hit_offset=0):
         """Batched estimate for several target masses: (exponents [nmass, nhit], logW [nmass],

@@ -173,7 +173,51 @@ void zero_colour64(ddrw_ctx *ctx, double2 *f, int colour, int nrhs)
     long n = (long)ctx->nblk_c * vbh;
     long lo = colour == DDRW_BLACK ? 0 : n;
     long tot = 2 * n * 12 * nrhs;
+    ++ctx->launches;
     k_zero_colour<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(f, ctx->V, ctx->vh, lo, n, nrhs);
+}
+
+static cudaEvent_t pool_event(ddrw_ctx *ctx)
+{
+    if (!ctx->prof_pool.empty()) {
+        cudaEvent_t e = ctx->prof_pool.back();
+        ctx->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+ProfScope::ProfScope(ddrw_ctx *c, int k, double b) : ctx(c), kind(k), bytes(b)
+{
+    if (!ctx->prof_on) return;
+    a = pool_event(ctx);
+    cudaEventRecord(a, ctx->stream);
+}
+
+ProfScope::~ProfScope()
+{
+    if (!a) return;
+    cudaEvent_t b = pool_event(ctx);
+    cudaEventRecord(b, ctx->stream);
+    ctx->prof_pending.push_back({a, b, kind, bytes});
+}
+
+static void prof_collect(ddrw_ctx *ctx)
+{
+    if (ctx->prof_pending.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &r : ctx->prof_pending) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        ctx->prof_count[r.kind] += 1;
+        ctx->prof_ms[r.kind] += ms;
+        ctx->prof_bytes[r.kind] += r.bytes;
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
 }
 
 }  // namespace ddrw
@@ -181,6 +225,36 @@ void zero_colour64(ddrw_ctx *ctx, double2 *f, int colour, int nrhs)
 using namespace ddrw;
 
 extern "C" {
+
+ddrw_status ddrw_profile(ddrw_ctx *ctx, int enable)
+{
+    if (!ctx) return DDRW_EINVAL;
+    prof_collect(ctx);
+    for (int k = 0; k < 16; k++) {
+        ctx->prof_count[k] = 0;
+        ctx->prof_ms[k] = 0;
+        ctx->prof_bytes[k] = 0;
+    }
+    ctx->prof_on = enable != 0;
+    ctx->launches = 0;
+    return DDRW_OK;
+}
+
+ddrw_status ddrw_profile_read(ddrw_ctx *ctx, int kind, long *launches, double *ms, double *bytes)
+{
+    if (!ctx || kind < 0 || kind > PROF_NKIND) return DDRW_EINVAL;
+    prof_collect(ctx);
+    if (kind == PROF_NKIND) {  // every kernel launch of the library
+        if (launches) *launches = ctx->launches;
+        if (ms) *ms = 0;
+        if (bytes) *bytes = 0;
+        return DDRW_OK;
+    }
+    if (launches) *launches = ctx->prof_count[kind];
+    if (ms) *ms = ctx->prof_ms[kind];
+    if (bytes) *bytes = ctx->prof_bytes[kind];
+    return DDRW_OK;
+}
 
 ddrw_status ddrw_create(ddrw_ctx **out, const int dims[4], const int block[4], int device, void *cuda_stream)
 {
@@ -309,6 +383,11 @@ void ddrw_destroy(ddrw_ctx *ctx)
     cudaFree(ctx->C32);
     free_inverses(ctx);
     for (auto &kv : ctx->ws) cudaFree(kv.second.p);
+    for (auto &r : ctx->prof_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;

@@ -299,6 +299,8 @@ void launch_block_kernel(ddrw_ctx *ctx, const BlkArgs<P> &a, int nrhs)
     dim3 grid((unsigned)ctx->nblk_c, (unsigned)nrhs);
     constexpr int VBH = BlockShape<BL>::VBH;
     constexpr int NT = VBH <= 32 ? 32 : (VBH <= 128 ? 128 : 256);
+    ProfScope ps(ctx, sizeof(typename P::R) == 8 ? PROF_BLOCK64 : PROF_BLOCK32, 0.0);
+    ++ctx->launches;
     k_block_solve<P, BL, NT><<<grid, NT, 0, ctx->stream>>>(g, a);
 }
 

@@ -128,6 +128,7 @@ void clover_launch(ddrw_ctx *ctx)
 {
     GeomDev g = geom_dev(ctx);
     dim3 grid((unsigned)((ctx->V + 63) / 64));
+    ++ctx->launches;
     k_clover<BL><<<grid, 64, 0, ctx->stream>>>(g, ctx->U64, ctx->csw, ctx->C64, ctx->C32);
 }
 

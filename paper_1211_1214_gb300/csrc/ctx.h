@@ -68,6 +68,7 @@ struct ddrw_ctx {
     ddrw_prec prec = DDRW_FP64;
     double tol_outer = 1e-10, tol_block = 1e-13;
     int maxiter = 20000;
+    int max_rhs = 0;  // right-hand sides per chunk of a batched estimate (0: from free memory)
 
     // resident fields
     double2 *U64 = nullptr;  // [4][9][V]
@@ -81,10 +82,44 @@ struct ddrw_ctx {
     double *h_pinned = nullptr;  // small pinned host buffer for scalars
     size_t h_pinned_bytes = 0;
 
+    // kernel timing (ddrw_profile): CUDA events around the instrumented launches
+    bool prof_on = false;
+    long launches = 0;  // kernel launches since creation or the last ddrw_profile call
+    struct ProfRec {
+        cudaEvent_t a, b;
+        int kind;
+        double bytes;
+    };
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    long prof_count[16] = {0};
+    double prof_ms[16] = {0}, prof_bytes[16] = {0};
+
     std::string err;
 };
 
 namespace ddrw {
+
+// kernel classes timed by ddrw_profile (see include/ddrw.h)
+enum {
+    PROF_DSLASH64 = 0,      // FP64 stencil, all hops
+    PROF_DSLASH32 = 1,      // FP32 stencil, all hops
+    PROF_DSLASH64_BLK = 2,  // FP64 stencil, hops inside / between blocks
+    PROF_DSLASH32_BLK = 3,
+    PROF_BLOCK64 = 4,       // persistent block solver, FP64
+    PROF_BLOCK32 = 5,       // persistent block solver, FP32
+    PROF_NKIND = 6
+};
+
+// Records CUDA events around the launches in its scope when profiling is on.
+struct ProfScope {
+    ddrw_ctx *ctx;
+    int kind;
+    double bytes;
+    cudaEvent_t a = nullptr;
+    ProfScope(ddrw_ctx *c, int k, double b);
+    ~ProfScope();
+};
 
 ddrw_status set_error(ddrw_ctx *ctx, ddrw_status st, const std::string &msg);
 ddrw_status set_cuda_error(ddrw_ctx *ctx, cudaError_t e, const char *what, const char *file, int line);

@@ -4,9 +4,9 @@
 //
 //   out(x) = POST( alpha * DIAG(x) + beta * sum_mu [ (1 - g_mu) U_mu(x) in(x+mu) + (1 + g_mu) U_mu(x-mu)^dag in(x-mu) ] )
 //
-// DIAG is A(m) x = (4 + m) x + C x (or x itself), POST an optional A(m)^-1.  Right-hand sides run
-// along gridDim.y and are grouped into mass slots (rhs / rpm), so one launch can carry several
-// masses.  The SU(3) x spin stencil is not a dense contraction, so it runs on the FP32/FP64
+// DIAG is A(m) x = (4 + m) x + C x (or x itself), POST an optional A(m)^-1.  Right-hand sides are
+// interleaved with the site tiles along gridDim.x (right-hand side fastest) and grouped into mass
+// slots (rhs / rpm), so one launch can carry several masses.  The SU(3) x spin stencil is not a dense contraction, so it runs on the FP32/FP64
 // ALUs, not on tensor cores.  Each hop projects the neighbour to a 2-spin half spinor before the
 // colour multiply (half the complex multiplies of a 4-spin product).
 #include "ctx.h"
@@ -24,7 +24,7 @@ template <class P> struct DsArgs {
     typename P::R alpha, beta;
     int diag, post;
     int par0, npar, blk0, nblk;
-    int rpm;
+    int nrhs, rpm;
     typename P::R mass4[MAXM];           // 4 + m per slot
     const typename P::CElem *Ainv[MAXM];  // A(m)^-1 per slot
 };
@@ -33,11 +33,15 @@ template <class P, int BL, int HOPSEL>
 __global__ void __launch_bounds__(128) k_dslash(GeomDev g, DsArgs<P> a)
 {
     using R = typename P::R;
+    // right-hand side fastest across CTAs: the nrhs CTAs of one site tile run together and share
+    // its links and clover term through L2
+    const int rhs = blockIdx.x % a.nrhs;
+    const long tile = blockIdx.x / a.nrhs;
     const long nper = (long)a.nblk * BlockShape<BL>::VBH;
-    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long i = tile * blockDim.x + threadIdx.x;
     if (i >= nper * a.npar) return;
-    const long roff = (long)blockIdx.y * a.rstride;
-    const int slot = blockIdx.y / a.rpm;
+    const long roff = (long)rhs * a.rstride;
+    const int slot = rhs / a.rpm;
     const int pp = (int)(i / nper);
     const long s = (long)(a.par0 + pp) * g.vh + (long)a.blk0 * BlockShape<BL>::VBH + (i - pp * nper);
     Site<BL> st;
@@ -77,6 +81,7 @@ static void launch_bl(ddrw_ctx *ctx, const DslashCall &c)
     a.blk0 = c.blk0;
     a.nblk = c.nblk;
     int nm = c.nmass < 1 ? 1 : c.nmass;
+    a.nrhs = c.nrhs;
     a.rpm = (c.nrhs + nm - 1) / nm;
     for (int k = 0; k < MAXM; k++) {
         int kk = k < nm ? k : nm - 1;
@@ -93,7 +98,19 @@ static void launch_bl(ddrw_ctx *ctx, const DslashCall &c)
     GeomDev g = geom_dev(ctx);
     long n = (long)c.npar * c.nblk * BlockShape<BL>::VBH;
     if (n == 0 || c.nrhs == 0) return;
-    dim3 grid((unsigned)((n + 127) / 128), (unsigned)c.nrhs);
+    dim3 grid((unsigned)(((n + 127) / 128) * c.nrhs));
+    // compulsory bytes of this launch: per output site the R input, output and diagonal-input
+    // spinors, the links of its hops (8 per site when the output is one parity, since the backward
+    // links are stored at the other parity; 4 per site for both parities), clover terms once
+    const double S = sizeof(typename P::SElem) * P::SPLANES, Lk = sizeof(typename P::UElem) * P::UPLANES,
+                 Cb = sizeof(typename P::CElem) * P::CPLANES;
+    double per = S * c.nrhs * ((c.beta != 0.0) + 1 + (c.diag != 0));
+    if (c.beta != 0.0) per += (c.npar == 1 ? 8.0 : 4.0) * Lk;
+    if (c.diag == 1) per += Cb;
+    if (c.post) per += Cb;
+    int kind = (sizeof(R) == 8 ? PROF_DSLASH64 : PROF_DSLASH32) + (c.hopsel != 0 ? 2 : 0);
+    ProfScope ps(ctx, kind, per * (double)n);
+    ++ctx->launches;
     switch (c.hopsel) {
     case 0: k_dslash<P, BL, 0><<<grid, 128, 0, ctx->stream>>>(g, a); break;
     case 1: k_dslash<P, BL, 1><<<grid, 128, 0, ctx->stream>>>(g, a); break;

@@ -116,6 +116,7 @@ __global__ void k_delta(GeomDev g, const double2 *r, const double2 *x, double2 *
 }
 
 #define DISPATCH_BL(ctx, KERNEL, GRID, BLOCK, ...)                                                        \
+    ++(ctx)->launches;                                                                                    \
     switch ((ctx)->l) {                                                                                   \
     case 2: KERNEL<2><<<GRID, BLOCK, 0, (ctx)->stream>>>(__VA_ARGS__); break;                             \
     case 4: KERNEL<4><<<GRID, BLOCK, 0, (ctx)->stream>>>(__VA_ARGS__); break;                             \
@@ -126,6 +127,7 @@ __global__ void k_delta(GeomDev g, const double2 *r, const double2 *x, double2 *
 static void noise_launch(ddrw_ctx *ctx, uint64_t seed, uint64_t hit0, int nhit, int nrep, double2 *field, double *packed)
 {
     dim3 grid((unsigned)((12 * ctx->nP + 255) / 256), (unsigned)nhit);
+    ++ctx->launches;
     k_noise<<<grid, 256, 0, ctx->stream>>>(ctx->V, ctx->nP, ctx->d_suppP, (uint32_t)(seed & 0xffffffffu),
                                            (uint32_t)(seed >> 32), hit0, nhit, nrep, field, packed);
 }
@@ -226,14 +228,12 @@ static ddrw_status fields(ddrw_ctx *ctx, const char *prefix, int n, int nrhs, do
     return DDRW_OK;
 }
 
-// The estimate for nmass target masses: exponents[k * nhit + j], logW[k], rel_var[k].
-ddrw_status estimate_multi(ddrw_ctx *ctx, int nmass, const double *m2, int nhit, uint64_t seed, uint64_t hit0,
-                           const double *eta_user, double *exponents, double *logW, double *rel_var, double *delta_user,
-                           ddrw_solve_info *info)
+// One chunk of the estimate: nmass target masses x nhit noise vectors as nrhs = nmass * nhit
+// right-hand sides; writes the FP64 exponents e[k * nhit + j].  eta_user (packed, nhit vectors)
+// or the Philox noise of hits hit0 .. hit0 + nhit - 1.
+static ddrw_status estimate_chunk(ddrw_ctx *ctx, int nmass, const double *m2, int nhit, uint64_t seed, uint64_t hit0,
+                                  const double *eta_user, double *exponents, double *delta_user, SolveStats &stats)
 {
-    auto t0 = std::chrono::steady_clock::now();
-    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
-    if (nhit <= 0 || nmass <= 0 || nmass > MAXM) return set_error(ctx, DDRW_EINVAL, "bad nhit or number of masses");
     const int nrhs = nmass * nhit;
     MassSet m2s, m1s;
     ddrw_status st;
@@ -250,12 +250,12 @@ ddrw_status estimate_multi(ddrw_ctx *ctx, int nmass, const double *m2, int nhit,
         if ((st = stage_in(ctx, eta_user, pbytes * nhit, "stage_eta", &d))) return st;
         unpack_P64(ctx, (const double *)d, eta, nhit);
         long n = 12 * ctx->V;
+        ++ctx->launches;
         if (nmass > 1) k_replicate<<<(unsigned)((n * nhit + 255) / 256), 256, 0, ctx->stream>>>(n, nhit, nmass, eta);
     } else {
         DDRW_CUDA_CHECK(cudaMemsetAsync(eta, 0, sizeof(double2) * 12 * ctx->V * nrhs, ctx->stream));
         noise_launch(ctx, seed, hit0, nhit, nmass, eta, nullptr);
     }
-    SolveStats stats;
     ddrw_status conv = DDRW_OK;
     if ((st = apply_dA_fields(ctx, m2s, m1s, eta, r, work, nrhs, &stats))) return st;
     double2 *w2[2] = {F[3], F[4]};
@@ -280,13 +280,69 @@ ddrw_status estimate_multi(ddrw_ctx *ctx, int nmass, const double *m2, int nhit,
         if ((st = finish_out(ctx, delta_user, dd, pbytes * nrhs, host))) return st;
     }
     if ((st = sync(ctx))) return st;
+    for (int rr = 0; rr < nrhs; rr++) {
+        double nn = h[2 * rr] + h[2 * nrhs + 2 * rr], dr = h[2 * rr + 1] + h[2 * nrhs + 2 * rr + 1];
+        exponents[rr] = nn + 2.0 * dr;
+    }
+    return conv;
+}
+
+// right-hand sides that fit the free device memory (about 3 KB per site and right-hand side of
+// FP64/FP32 fields in the estimate, the block solves and the outer solve), at most 64
+static int rhs_budget(ddrw_ctx *ctx)
+{
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    size_t have = fr;
+    for (auto &kv : ctx->ws) have += kv.second.bytes;  // workspaces are reused
+    double per = 4096.0 * (double)ctx->V;
+    int n = (int)((double)have * 0.85 / per);
+    return std::max(1, std::min(n, 64));
+}
+
+// The estimate for nmass target masses: exponents[k * nhit + j], logW[k], rel_var[k].  The
+// masses and hits are processed in chunks of right-hand sides that fit the device memory.
+ddrw_status estimate_multi(ddrw_ctx *ctx, int nmass, const double *m2, int nhit, uint64_t seed, uint64_t hit0,
+                           const double *eta_user, double *exponents, double *logW, double *rel_var, double *delta_user,
+                           ddrw_solve_info *info)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
+    if (nhit <= 0 || nmass <= 0 || nmass > MAXM) return set_error(ctx, DDRW_EINVAL, "bad nhit or number of masses");
+    const int budget = ctx->max_rhs > 0 ? ctx->max_rhs : rhs_budget(ctx);
+    std::vector<double> eall((size_t)nmass * nhit);
+    SolveStats stats;
+    ddrw_status conv = DDRW_OK, st;
+    if (eta_user != nullptr || delta_user != nullptr) {
+        // the caller's vectors go through in one chunk
+        if (nmass * nhit > budget)
+            return set_error(ctx, DDRW_ENOMEM, "caller-supplied noise or delta for more right-hand sides than fit");
+        st = estimate_chunk(ctx, nmass, m2, nhit, seed, hit0, eta_user, eall.data(), delta_user, stats);
+        if (st == DDRW_ENOCONV) conv = st;
+        else if (st) return st;
+    } else {
+        // whole masses per chunk while nhit fits, else one mass and as many hits as fit
+        const int mper = std::max(1, std::min(nmass, budget / nhit));
+        const int hper = mper == 1 ? std::min(nhit, budget) : nhit;
+        for (int k0 = 0; k0 < nmass; k0 += mper) {
+            const int km = std::min(mper, nmass - k0);
+            for (int j0 = 0; j0 < nhit; j0 += hper) {
+                const int jn = std::min(hper, nhit - j0);
+                std::vector<double> ec((size_t)km * jn);
+                st = estimate_chunk(ctx, km, m2 + k0, jn, seed, hit0 + j0, nullptr, ec.data(), nullptr, stats);
+                if (st == DDRW_ENOCONV) conv = st;
+                else if (st) return st;
+                for (int k = 0; k < km; k++)
+                    for (int j = 0; j < jn; j++) eall[(size_t)(k0 + k) * nhit + j0 + j] = ec[(size_t)k * jn + j];
+            }
+        }
+    }
     bool bad = false;
     for (int k = 0; k < nmass; k++) {
         std::vector<double> e(nhit);
         for (int j = 0; j < nhit; j++) {
             int rr = k * nhit + j;
-            double nn = h[2 * rr] + h[2 * nrhs + 2 * rr], dr = h[2 * rr + 1] + h[2 * nrhs + 2 * rr + 1];
-            e[j] = nn + 2.0 * dr;
+            e[j] = eall[rr];
             if (!(e[j] == e[j])) bad = true;
             if (exponents) exponents[rr] = e[j];
         }

@@ -153,6 +153,7 @@ __global__ void k_unpack_P(long V, long nP, const int *__restrict__ idx, const d
 // ----------------------------------------------------------------------------- launchers
 
 #define DISPATCH_BL(ctx, KERNEL, GRID, BLOCK, ...)                                                        \
+    ++(ctx)->launches;                                                                                    \
     switch ((ctx)->l) {                                                                                   \
     case 2: KERNEL<2><<<GRID, BLOCK, 0, (ctx)->stream>>>(__VA_ARGS__); break;                             \
     case 4: KERNEL<4><<<GRID, BLOCK, 0, (ctx)->stream>>>(__VA_ARGS__); break;                             \
@@ -180,6 +181,7 @@ void build_clover(ddrw_ctx *ctx)
 void build_inverse(ddrw_ctx *ctx, double m, MassInv &mi)
 {
     dim3 grid((unsigned)((ctx->V + 63) / 64));
+    ++ctx->launches;
     k_inverse<<<grid, 64, 0, ctx->stream>>>(ctx->V, ctx->C64, m, mi.A64, mi.A32);
 }
 
@@ -201,6 +203,7 @@ void pack_P64(ddrw_ctx *ctx, const double2 *f, double *packed, int nrhs)
 {
     if (ctx->nP == 0) return;
     dim3 grid((unsigned)((ctx->nP + 127) / 128), (unsigned)nrhs);
+    ++ctx->launches;
     k_pack_P<<<grid, 128, 0, ctx->stream>>>(ctx->V, ctx->nP, ctx->d_suppP, f, packed);
 }
 
@@ -209,6 +212,7 @@ void unpack_P64(ddrw_ctx *ctx, const double *packed, double2 *f, int nrhs)
     cudaMemsetAsync(f, 0, sizeof(double2) * 12 * (size_t)ctx->V * nrhs, ctx->stream);
     if (ctx->nP == 0) return;
     dim3 grid((unsigned)((ctx->nP + 127) / 128), (unsigned)nrhs);
+    ++ctx->launches;
     k_unpack_P<<<grid, 128, 0, ctx->stream>>>(ctx->V, ctx->nP, ctx->d_suppP, packed, f);
 }
 

@@ -58,6 +58,37 @@ def _expm_batch(A: np.ndarray) -> np.ndarray:
     return out
 
 
+def _expm_i_traceless_hermitian(Q: np.ndarray) -> np.ndarray:
+    """exp(iQ) for a batch of traceless Hermitian 3x3 Q, from the spectral decomposition.
+
+    The eigenvalues solve l^3 - c1 l - c0 = 0 with c1 = tr(Q^2)/2 and c0 = det Q (trigonometric
+    solution of the cubic); exp(iQ) = sum_j e^{i l_j} (Q - l_k)(Q - l_m) / ((l_j - l_k)(l_j - l_m)).
+    Matrices with nearly degenerate eigenvalues fall back to the Taylor series.
+    """
+    Q2 = Q @ Q
+    c1 = 0.5 * np.real(np.einsum("nii->n", Q2))
+    a, b, c = Q[:, 0], Q[:, 1], Q[:, 2]
+    c0 = np.real(a[:, 0] * (b[:, 1] * c[:, 2] - b[:, 2] * c[:, 1]) - a[:, 1] * (b[:, 0] * c[:, 2] - b[:, 2] * c[:, 0])
+                 + a[:, 2] * (b[:, 0] * c[:, 1] - b[:, 1] * c[:, 0]))
+    c1s = np.maximum(c1, 1e-300)
+    arg = np.clip(0.5 * c0 * (3.0 / c1s) ** 1.5, -1.0, 1.0)
+    phi = np.arccos(arg) / 3.0
+    rad = 2.0 * np.sqrt(c1s / 3.0)
+    lam = np.stack([rad * np.cos(phi - 2.0 * np.pi * k / 3.0) for k in range(3)], axis=-1)
+    l0, l1, l2 = lam[:, 0], lam[:, 1], lam[:, 2]
+    d = np.stack([(l0 - l1) * (l0 - l2), (l1 - l0) * (l1 - l2), (l2 - l0) * (l2 - l1)], axis=-1)
+    e = np.exp(1j * lam)
+    w = e / np.where(np.abs(d) > 0, d, 1.0)
+    A = w.sum(-1)
+    B = (w * lam).sum(-1)
+    C = w[:, 0] * l1 * l2 + w[:, 1] * l0 * l2 + w[:, 2] * l0 * l1
+    out = A[:, None, None] * Q2 + B[:, None, None] * Q + C[:, None, None] * np.eye(3)
+    bad = np.abs(d).min(axis=-1) < 1e-6 * np.maximum(c1, 1e-30)
+    if np.any(bad):
+        out[bad] = _expm_batch(1j * Q[bad])
+    return out
+
+
 def _project_su3(U: np.ndarray) -> np.ndarray:
     """Gram-Schmidt on rows 0 and 1, row 2 = conj(row0 x row1): unitary with det exactly 1."""
     r0 = U[..., 0, :]
@@ -69,22 +100,31 @@ def _project_su3(U: np.ndarray) -> np.ndarray:
     return np.stack([r0, r1, r2], axis=-2)
 
 
-def gauge_field(dims, eps: float, seed: int, chunk: int = 1 << 18) -> np.ndarray:
+def gauge_field(dims, eps: float, seed: int, chunk: int = 1 << 16) -> np.ndarray:
     """SU(3) links U = exp(i eps H), H = sum_a w_a lambda_a/2, w_a ~ N(0,1); shape (V, 4, 3, 3).
 
     All 8*4*V normals are drawn from one ``numpy.random.default_rng(seed)`` stream in the order
-    (site, mu, a), so the field does not depend on ``chunk``.
+    (site, mu, a), so the field depends on neither ``chunk`` nor the number of threads that
+    exponentiate the chunks.
     """
+    import concurrent.futures as cf
+    import os
+
     dims = tuple(int(d) for d in dims)
     V = int(np.prod(dims))
     rng = np.random.default_rng(seed)
     omega = rng.standard_normal((V * 4, 8))
-    lam_half = gell_mann() / 2.0
+    lam_half = (gell_mann() / 2.0).reshape(8, 9)
     U = np.empty((V * 4, 3, 3), dtype=np.complex128)
-    for lo in range(0, V * 4, chunk):
+
+    def work(lo):
         hi = min(V * 4, lo + chunk)
-        H = np.einsum("na,aij->nij", omega[lo:hi], lam_half)
-        U[lo:hi] = _project_su3(_expm_batch(1j * eps * H))
+        w = omega[lo:hi] * eps
+        H = (w @ lam_half.real + 1j * (w @ lam_half.imag)).reshape(-1, 3, 3)
+        U[lo:hi] = _project_su3(_expm_i_traceless_hermitian(H))
+
+    with cf.ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+        list(ex.map(work, range(0, V * 4, chunk)))
     return U.reshape(V, 4, 3, 3)
 
 
@@ -108,4 +148,4 @@ def gauge_transform(dims, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     omega = rng.standard_normal((V, 8))
     H = np.einsum("na,aij->nij", omega, gell_mann() / 2.0)
-    return _project_su3(_expm_batch(1j * 1.0 * H))
+    return _project_su3(_expm_i_traceless_hermitian(H))
