@@ -35,6 +35,9 @@ WORKLOADS = {
                     small=(12, 12, 12, 12)),
     "16^4": dict(dims=(16, 16, 16, 16), l=4, eps=0.25, csw=1.5, m1=0.05, m2s=(0.045,), nhit=16,
                  small=(8, 8, 8, 8)),
+    # the 64x32^3 physics on a lattice small enough for ncu captures (a few GB on the device)
+    "32x16^3": dict(dims=(32, 16, 16, 16), l=8, eps=0.2, csw=1.9, m1=0.02, m2s=(0.015,), nhit=16,
+                    small=(16, 16, 16, 16)),
 }
 METRIC = "Dslash HBM GB/s & reweight estimates/s, mixed vs FP64, same 1e-10 residual"
 

@@ -13,32 +13,6 @@ namespace ddrw {
 
 // ----------------------------------------------------------------------------- element access
 
-template <class E> struct El;
-template <> struct El<double2> {
-    using R = double;
-    static constexpr int NC = 1;
-    __device__ static __forceinline__ void ld(const double2 *p, cpx<R> *c)
-    {
-        double2 v = *p;
-        c[0] = {v.x, v.y};
-    }
-    __device__ static __forceinline__ void st(double2 *p, const cpx<R> *c) { *p = make_double2(c[0].re, c[0].im); }
-};
-template <> struct El<float4> {
-    using R = float;
-    static constexpr int NC = 2;
-    __device__ static __forceinline__ void ld(const float4 *p, cpx<R> *c)
-    {
-        float4 v = *p;
-        c[0] = {v.x, v.y};
-        c[1] = {v.z, v.w};
-    }
-    __device__ static __forceinline__ void st(float4 *p, const cpx<R> *c)
-    {
-        *p = make_float4(c[0].re, c[0].im, c[1].re, c[1].im);
-    }
-};
-
 template <class P> struct VecArgs {
     long V, off, n, rs;  // plane stride, first site, sites, rhs stride (elements)
 };

@@ -6,6 +6,33 @@
 
 namespace ddrw {
 
+// One 16-byte field element as complex numbers in its arithmetic type (double2: 1, float4: 2).
+template <class E> struct El;
+template <> struct El<double2> {
+    using R = double;
+    static constexpr int NC = 1;
+    __device__ static __forceinline__ void ld(const double2 *p, cpx<R> *c)
+    {
+        double2 v = *p;
+        c[0] = {v.x, v.y};
+    }
+    __device__ static __forceinline__ void st(double2 *p, const cpx<R> *c) { *p = make_double2(c[0].re, c[0].im); }
+};
+template <> struct El<float4> {
+    using R = float;
+    static constexpr int NC = 2;
+    __device__ static __forceinline__ void ld(const float4 *p, cpx<R> *c)
+    {
+        float4 v = *p;
+        c[0] = {v.x, v.y};
+        c[1] = {v.z, v.w};
+    }
+    __device__ static __forceinline__ void st(float4 *p, const cpx<R> *c)
+    {
+        *p = make_float4(c[0].re, c[0].im, c[1].re, c[1].im);
+    }
+};
+
 // Krylov scalars of one right-hand side, resident on the device.
 struct KScal {
     double2 rho, alpha, omega, beta;

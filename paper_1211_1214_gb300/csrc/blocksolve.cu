@@ -111,8 +111,8 @@ ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const do
     } else {
         if ((st = workspace(ctx, "blk_e64", f64, (void **)&e64))) return st;
     }
-    // tolerance of one inner solve: the target itself in FP64, 1e-5 per cycle in FP32
-    const double tol_inner = mixed ? std::max(tol, 1e-5) : tol * 0.5;
+    // tolerance of one inner solve: the target itself in FP64, 1e-6 per cycle in FP32
+    const double tol_inner = mixed ? std::max(tol, 1e-6) : tol * 0.5;
     const double2 *rhs = b;  // first cycle: r = b, x = 0
     bool first = true;
     int cycles = 0;

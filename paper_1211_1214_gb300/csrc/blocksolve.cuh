@@ -74,55 +74,128 @@ __device__ __forceinline__ R sp_norm2(const Spinor<R> &a)
     return s;
 }
 
+// Per-site pieces of the block operator, kept out of line so that every phase of the kernel
+// reuses one register allocation (the fully unrolled stencil is large).
+
+// odd site s:  out(s) = A_oo^-1 ( y(s) + coef * H_intra in (s) )    (y may be null, coef 0 skips the hop)
+template <class P, int BL>
+__device__ __noinline__ void site_odd(const GeomDev &g, long s, const typename P::SElem *in,
+                                      const typename P::SElem *y, typename P::R coef,
+                                      const typename P::UElem *__restrict__ U,
+                                      const typename P::CElem *__restrict__ Ainv, typename P::SElem *out)
+{
+    using R = typename P::R;
+    Spinor<R> acc;
+    zero(acc);
+    if (coef != R(0)) {
+        Site<BL> st;
+        decode_site<BL>(s, g, st);
+        hop_sum<P, BL, 1, false>(g, st, s, in, U, acc);
+        scale(acc, coef);
+    }
+    if (y) {
+        Spinor<R> q;
+        P::load_spinor_rw(y, g.V, s, q);
+        axpy(acc, R(1), q);
+    }
+    clover_apply<P>(Ainv, g.V, s, R(0), acc);
+    P::store_spinor(out, g.V, s, acc);
+}
+
+template <typename R> struct Dot3 {
+    R a, b, c;
+};
+
+// even site s:  out(s) = D(x)(s) + coef * H_intra tmp (s), D = A(m) (diag) or 1, and the partial
+// inner products of the phase: mode 1 -> conj(w) out; mode 2 -> conj(out) x and |out|^2.
+template <class P, int BL>
+__device__ __noinline__ Dot3<typename P::R> site_even(const GeomDev &g, long s, const typename P::SElem *tmp,
+                                                      const typename P::SElem *x, typename P::R coef, bool diag,
+                                                      typename P::R mass4, const typename P::UElem *__restrict__ U,
+                                                      const typename P::CElem *__restrict__ Cl,
+                                                      const typename P::SElem *w, int mode, typename P::SElem *out)
+{
+    using R = typename P::R;
+    Spinor<R> acc, q;
+    zero(acc);
+    Site<BL> st;
+    decode_site<BL>(s, g, st);
+    hop_sum<P, BL, 1, false>(g, st, s, tmp, U, acc);
+    scale(acc, coef);
+    P::load_spinor_rw(x, g.V, s, q);
+    Dot3<R> d{R(0), R(0), R(0)};
+    if (diag) {
+        Spinor<R> dq = q;
+        clover_apply<P>(Cl, g.V, s, mass4, dq);
+        axpy(acc, R(1), dq);
+    } else {
+        axpy(acc, R(1), q);
+    }
+    P::store_spinor(out, g.V, s, acc);
+    if (mode == 1) {
+        P::load_spinor_rw(w, g.V, s, q);
+        sp_norm_dot(q, acc, d.a, d.b);
+    } else if (mode == 2) {
+        sp_norm_dot(acc, q, d.a, d.b);
+        d.c = sp_norm2(acc);
+    }
+    return d;
+}
+
 template <class P, int BL, int NT>
 __global__ void __launch_bounds__(NT) k_block_solve(GeomDev g, BlkArgs<P> a)
 {
     using R = typename P::R;
+    using E = typename P::SElem;
+    using L = El<E>;
     constexpr int VBH = BlockShape<BL>::VBH;
+    constexpr int NP = P::SPLANES;
     __shared__ double sm[NT / 32][3];
-    const int blk = a.blk0 + blockIdx.x;
-    const long ro = (long)blockIdx.y * a.rstride;
-    const int slot = blockIdx.y / a.rpm;
+    // right-hand side fastest: the CTAs of one block run together and share its links in L2
+    const int rhs = blockIdx.x;
+    const int blk = a.blk0 + blockIdx.y;
+    const long ro = (long)rhs * a.rstride;
+    const int slot = rhs / a.rpm;
     const R mass4 = a.mass4[slot];
     const typename P::CElem *Ainv = a.Ainv[slot];
     const long e0 = (long)blk * VBH, o0 = g.vh + (long)blk * VBH;
-    const typename P::SElem *b = a.b + ro;
-    typename P::SElem *x = a.x + ro, *r = a.r + ro, *rh = a.rh + ro, *p = a.p + ro, *v = a.v + ro, *t = a.t + ro,
-                      *tmp = a.tmp + ro;
+    const long V = g.V;
+    const E *b = a.b + ro;
+    E *x = a.x + ro, *r = a.r + ro, *rh = a.rh + ro, *p = a.p + ro, *v = a.v + ro, *t = a.t + ro, *tmp = a.tmp + ro;
 
-    // ||b||^2 over the block, tmp_o = A_oo^-1 b_o
+    // ||b||^2 over the block; tmp_o = A_oo^-1 b_o
     R bbl = 0;
-    for (int h = threadIdx.x; h < VBH; h += NT) {
-        Spinor<R> q;
-        P::load_spinor_rw(b, g.V, e0 + h, q);
-        bbl += sp_norm2(q);
-        P::load_spinor_rw(b, g.V, o0 + h, q);
-        bbl += sp_norm2(q);
-        clover_apply<P>(Ainv, g.V, o0 + h, R(0), q);
-        P::store_spinor(tmp, g.V, o0 + h, q);
-    }
+    for (int h = threadIdx.x; h < VBH; h += NT)
+        for (int k = 0; k < NP; k++) {
+            cpx<R> c[L::NC], d[L::NC];
+            L::ld(b + k * V + e0 + h, c);
+            L::ld(b + k * V + o0 + h, d);
+#pragma unroll
+            for (int q = 0; q < L::NC; q++)
+                bbl += c[q].re * c[q].re + c[q].im * c[q].im + d[q].re * d[q].re + d[q].im * d[q].im;
+        }
+    for (int h = threadIdx.x; h < VBH; h += NT) site_odd<P, BL>(g, o0 + h, nullptr, b, R(0), a.U, Ainv, tmp);
     double red[3] = {(double)bbl, 0, 0};
     cta_sum<3, NT>(red, sm);
     const double bb = red[0];
     // r = b_e + 1/2 H_eo tmp_o ; rh = p = r ; x_e = 0
+    for (int h = threadIdx.x; h < VBH; h += NT)
+        site_even<P, BL>(g, e0 + h, tmp, b, R(0.5), false, mass4, a.U, a.Cl, nullptr, 0, r);
     R rl = 0;
-    for (int h = threadIdx.x; h < VBH; h += NT) {
-        long s = e0 + h;
-        Site<BL> st;
-        decode_site<BL>(s, g, st);
-        Spinor<R> acc, q, z;
-        zero(acc);
-        zero(z);
-        hop_sum<P, BL, 1, false>(g, st, s, tmp, a.U, acc);
-        P::load_spinor_rw(b, g.V, s, q);
-        scale(acc, R(0.5));
-        axpy(acc, R(1), q);
-        P::store_spinor(r, g.V, s, acc);
-        P::store_spinor(rh, g.V, s, acc);
-        P::store_spinor(p, g.V, s, acc);
-        P::store_spinor(x, g.V, s, z);
-        rl += sp_norm2(acc);
-    }
+    for (int h = threadIdx.x; h < VBH; h += NT)
+        for (int k = 0; k < NP; k++) {
+            long ad = k * V + e0 + h;
+            cpx<R> c[L::NC], z[L::NC];
+            L::ld(r + ad, c);
+#pragma unroll
+            for (int q = 0; q < L::NC; q++) {
+                rl += c[q].re * c[q].re + c[q].im * c[q].im;
+                z[q] = {R(0), R(0)};
+            }
+            L::st(rh + ad, c);
+            L::st(p + ad, c);
+            L::st(x + ad, z);
+        }
     red[0] = (double)rl;
     cta_sum<3, NT>(red, sm);
     double rr = red[0];
@@ -131,33 +204,14 @@ __global__ void __launch_bounds__(NT) k_block_solve(GeomDev g, BlkArgs<P> a)
     int it = 0;
     bool ok = rr <= thresh;
     while (!ok && it < a.maxiter) {
-        // v = S p
-        for (int h = threadIdx.x; h < VBH; h += NT) {
-            long s = o0 + h;
-            Site<BL> st;
-            decode_site<BL>(s, g, st);
-            Spinor<R> acc;
-            zero(acc);
-            hop_sum<P, BL, 1, false>(g, st, s, p, a.U, acc);
-            clover_apply<P>(Ainv, g.V, s, R(0), acc);
-            P::store_spinor(tmp, g.V, s, acc);
-        }
+        // v = S p  and  (rh, v)
+        for (int h = threadIdx.x; h < VBH; h += NT) site_odd<P, BL>(g, o0 + h, p, nullptr, R(1), a.U, Ainv, tmp);
         __syncthreads();
         R are = 0, aim = 0;
         for (int h = threadIdx.x; h < VBH; h += NT) {
-            long s = e0 + h;
-            Site<BL> st;
-            decode_site<BL>(s, g, st);
-            Spinor<R> acc, q;
-            zero(acc);
-            hop_sum<P, BL, 1, false>(g, st, s, tmp, a.U, acc);
-            scale(acc, R(-0.25));
-            P::load_spinor_rw(p, g.V, s, q);
-            clover_apply<P>(a.Cl, g.V, s, mass4, q);
-            axpy(acc, R(1), q);
-            P::store_spinor(v, g.V, s, acc);
-            P::load_spinor_rw(rh, g.V, s, q);
-            sp_norm_dot(q, acc, are, aim);
+            Dot3<R> d = site_even<P, BL>(g, e0 + h, tmp, p, R(-0.25), true, mass4, a.U, a.Cl, rh, 1, v);
+            are += d.a;
+            aim += d.b;
         }
         red[0] = (double)are;
         red[1] = (double)aim;
@@ -167,46 +221,26 @@ __global__ void __launch_bounds__(NT) k_block_solve(GeomDev g, BlkArgs<P> a)
         double2 alpha = make_double2((rho.x * red[0] + rho.y * red[1]) / den, (rho.y * red[0] - rho.x * red[1]) / den);
         const cpx<R> al = {R(alpha.x), R(alpha.y)};
         // s = r - alpha v (in r)
-        for (int h = threadIdx.x; h < VBH; h += NT) {
-            long s = e0 + h;
-            Spinor<R> q, w;
-            P::load_spinor_rw(r, g.V, s, q);
-            P::load_spinor_rw(v, g.V, s, w);
+        for (int h = threadIdx.x; h < VBH; h += NT)
+            for (int k = 0; k < NP; k++) {
+                long ad = k * V + e0 + h;
+                cpx<R> c[L::NC], d[L::NC];
+                L::ld(r + ad, c);
+                L::ld(v + ad, d);
 #pragma unroll
-            for (int sp = 0; sp < 4; sp++)
-#pragma unroll
-                for (int c = 0; c < 3; c++) q.v[sp][c] = q.v[sp][c] - cmul(al, w.v[sp][c]);
-            P::store_spinor(r, g.V, s, q);
-        }
+                for (int q = 0; q < L::NC; q++) c[q] = c[q] - cmul(al, d[q]);
+                L::st(r + ad, c);
+            }
         __syncthreads();
-        // t = S s
-        for (int h = threadIdx.x; h < VBH; h += NT) {
-            long s = o0 + h;
-            Site<BL> st;
-            decode_site<BL>(s, g, st);
-            Spinor<R> acc;
-            zero(acc);
-            hop_sum<P, BL, 1, false>(g, st, s, r, a.U, acc);
-            clover_apply<P>(Ainv, g.V, s, R(0), acc);
-            P::store_spinor(tmp, g.V, s, acc);
-        }
+        // t = S s  and  (t, s), (t, t)
+        for (int h = threadIdx.x; h < VBH; h += NT) site_odd<P, BL>(g, o0 + h, r, nullptr, R(1), a.U, Ainv, tmp);
         __syncthreads();
         R tsr = 0, tsi = 0, tt = 0;
         for (int h = threadIdx.x; h < VBH; h += NT) {
-            long s = e0 + h;
-            Site<BL> st;
-            decode_site<BL>(s, g, st);
-            Spinor<R> acc, q;
-            zero(acc);
-            hop_sum<P, BL, 1, false>(g, st, s, tmp, a.U, acc);
-            scale(acc, R(-0.25));
-            P::load_spinor_rw(r, g.V, s, q);
-            Spinor<R> d = q;
-            clover_apply<P>(a.Cl, g.V, s, mass4, d);
-            axpy(acc, R(1), d);
-            P::store_spinor(t, g.V, s, acc);
-            sp_norm_dot(acc, q, tsr, tsi);
-            tt += sp_norm2(acc);
+            Dot3<R> d = site_even<P, BL>(g, e0 + h, tmp, r, R(-0.25), true, mass4, a.U, a.Cl, nullptr, 2, t);
+            tsr += d.a;
+            tsi += d.b;
+            tt += d.c;
         }
         red[0] = (double)tsr;
         red[1] = (double)tsi;
@@ -217,26 +251,27 @@ __global__ void __launch_bounds__(NT) k_block_solve(GeomDev g, BlkArgs<P> a)
         const cpx<R> om = {R(omega.x), R(omega.y)};
         // x += alpha p + omega s ; r = s - omega t ; rho' = (rh, r) ; rr = (r, r)
         R hre = 0, him = 0, rrl = 0;
-        for (int h = threadIdx.x; h < VBH; h += NT) {
-            long s = e0 + h;
-            Spinor<R> xv, pv, sv, tv, hv;
-            P::load_spinor_rw(x, g.V, s, xv);
-            P::load_spinor_rw(p, g.V, s, pv);
-            P::load_spinor_rw(r, g.V, s, sv);
-            P::load_spinor_rw(t, g.V, s, tv);
-            P::load_spinor_rw(rh, g.V, s, hv);
+        for (int h = threadIdx.x; h < VBH; h += NT)
+            for (int k = 0; k < NP; k++) {
+                long ad = k * V + e0 + h;
+                cpx<R> xv[L::NC], pv[L::NC], sv[L::NC], tv[L::NC], hv[L::NC];
+                L::ld(x + ad, xv);
+                L::ld(p + ad, pv);
+                L::ld(r + ad, sv);
+                L::ld(t + ad, tv);
+                L::ld(rh + ad, hv);
 #pragma unroll
-            for (int sp = 0; sp < 4; sp++)
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    xv.v[sp][c] = xv.v[sp][c] + cmul(al, pv.v[sp][c]) + cmul(om, sv.v[sp][c]);
-                    sv.v[sp][c] = sv.v[sp][c] - cmul(om, tv.v[sp][c]);
+                for (int q = 0; q < L::NC; q++) {
+                    xv[q] = xv[q] + cmul(al, pv[q]) + cmul(om, sv[q]);
+                    sv[q] = sv[q] - cmul(om, tv[q]);
+                    cpx<R> z = cmulc(hv[q], sv[q]);
+                    hre += z.re;
+                    him += z.im;
+                    rrl += sv[q].re * sv[q].re + sv[q].im * sv[q].im;
                 }
-            P::store_spinor(x, g.V, s, xv);
-            P::store_spinor(r, g.V, s, sv);
-            sp_norm_dot(hv, sv, hre, him);
-            rrl += sp_norm2(sv);
-        }
+                L::st(x + ad, xv);
+                L::st(r + ad, sv);
+            }
         red[0] = (double)hre;
         red[1] = (double)him;
         red[2] = (double)rrl;
@@ -256,36 +291,22 @@ __global__ void __launch_bounds__(NT) k_block_solve(GeomDev g, BlkArgs<P> a)
         const cpx<R> be = {R(q1.x * q2.x - q1.y * q2.y), R(q1.x * q2.y + q1.y * q2.x)};
         rho = rn;
         // p = r + beta (p - omega v)
-        for (int h = threadIdx.x; h < VBH; h += NT) {
-            long s = e0 + h;
-            Spinor<R> pv, rv, vv;
-            P::load_spinor_rw(p, g.V, s, pv);
-            P::load_spinor_rw(r, g.V, s, rv);
-            P::load_spinor_rw(v, g.V, s, vv);
+        for (int h = threadIdx.x; h < VBH; h += NT)
+            for (int k = 0; k < NP; k++) {
+                long ad = k * V + e0 + h;
+                cpx<R> pv[L::NC], rv[L::NC], vv[L::NC];
+                L::ld(p + ad, pv);
+                L::ld(r + ad, rv);
+                L::ld(v + ad, vv);
 #pragma unroll
-            for (int sp = 0; sp < 4; sp++)
-#pragma unroll
-                for (int c = 0; c < 3; c++)
-                    pv.v[sp][c] = rv.v[sp][c] + cmul(be, pv.v[sp][c] - cmul(om, vv.v[sp][c]));
-            P::store_spinor(p, g.V, s, pv);
-        }
+                for (int q = 0; q < L::NC; q++) pv[q] = rv[q] + cmul(be, pv[q] - cmul(om, vv[q]));
+                L::st(p + ad, pv);
+            }
         __syncthreads();
     }
     __syncthreads();
     // x_o = A_oo^-1 (b_o + 1/2 H_oe x_e)
-    for (int h = threadIdx.x; h < VBH; h += NT) {
-        long s = o0 + h;
-        Site<BL> st;
-        decode_site<BL>(s, g, st);
-        Spinor<R> acc, q;
-        zero(acc);
-        hop_sum<P, BL, 1, false>(g, st, s, x, a.U, acc);
-        scale(acc, R(0.5));
-        P::load_spinor_rw(b, g.V, s, q);
-        axpy(acc, R(1), q);
-        clover_apply<P>(Ainv, g.V, s, R(0), acc);
-        P::store_spinor(x, g.V, s, acc);
-    }
+    for (int h = threadIdx.x; h < VBH; h += NT) site_odd<P, BL>(g, o0 + h, x, b, R(0.5), a.U, Ainv, x);
     if (threadIdx.x == 0) {
         atomicMax(a.stat, it);
         if (!ok) atomicAdd(a.stat + 1, 1);
@@ -296,7 +317,7 @@ template <class P, int BL>
 void launch_block_kernel(ddrw_ctx *ctx, const BlkArgs<P> &a, int nrhs)
 {
     GeomDev g = geom_dev(ctx);
-    dim3 grid((unsigned)ctx->nblk_c, (unsigned)nrhs);
+    dim3 grid((unsigned)nrhs, (unsigned)ctx->nblk_c);
     constexpr int VBH = BlockShape<BL>::VBH;
     constexpr int NT = VBH <= 32 ? 32 : (VBH <= 128 ? 128 : 256);
     ProfScope ps(ctx, sizeof(typename P::R) == 8 ? PROF_BLOCK64 : PROF_BLOCK32, 0.0);
