@@ -151,6 +151,26 @@ ddrw_status ddrw_estimate_masses(ddrw_ctx *ctx, int nmass, const double *m2, int
                                  uint64_t hit_offset, double *exponents, double *logW, double *rel_var,
                                  ddrw_solve_info *info);
 
+/* ddrw_solve_block for callers that cannot allocate device memory.  The paper has no counterpart:
+ * this is an integration aid.  Some callers may not call cudaMalloc -- code running while a
+ * framework's memory pool is frozen or a graph is being built, or a host application that owns
+ * every device allocation -- and ddrw_solve_block grows its workspace with cudaMalloc.  This call
+ * allocates nothing: its scratch (about 40 MB: ten FP64 fields of up to 20736 sites plus reduction
+ * slots) is one fixed array in device memory that every GPU using the library holds until the
+ * process exits.
+ *   - One right-hand side, FP64 (whatever ddrw_set_solver chose), tolerance tol_block, same
+ *     result as ddrw_solve_block: x = D_cc(m)^-1 b on colour c, x zero on the other colour.
+ *   - Lattices of at most 20736 sites (12^4); larger ones return DDRW_EINVAL with a message.
+ *   - b and x must be device pointers (boundary layout); host pointers return DDRW_EINVAL.
+ *   - m must be m1 or m2 of the last ddrw_set_params (their inverses already exist).
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ *     that first call before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; calls that overlap on the
+ *     GPU (other streams or contexts on the same device) race on it, so serialise them.
+ *   - With kernel timing (ddrw_profile) on, the timing events are created on first use. */
+ddrw_status ddrw_solve_block_noalloc(ddrw_ctx *ctx, int colour, double m, const double *b, double *x,
+                                     ddrw_solve_info *info);
+
 /* Kernel timing for measurement (not part of the method): with profiling enabled, CUDA events
  * bracket every launch of the instrumented kernel classes on the context's stream, and
  * ddrw_profile_read returns, per class, the number of launches, their summed device time (ms) and

@@ -24,7 +24,7 @@ _STATUS = {0: "DDRW_OK", 1: "DDRW_EINVAL", 2: "DDRW_ENOMEM", 3: "DDRW_ECUDA", 4:
 EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", "ddrw_volume", "ddrw_load_gauge",
            "ddrw_set_params", "ddrw_set_solver", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
-           "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read"]
+           "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc"]
 
 #: kernel classes of ddrw_profile_read
 PROF_DSLASH64, PROF_DSLASH32, PROF_DSLASH64_BLK, PROF_DSLASH32_BLK, PROF_BLOCK64, PROF_BLOCK32, PROF_LAUNCHES = range(7)
@@ -85,6 +85,7 @@ def load(path: str | None = None):
         "ddrw_estimate_masses": (st, [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp,
                                       dp, ctypes.POINTER(SolveInfo)]),
         "ddrw_profile": (st, [vp, ctypes.c_int]),
+        "ddrw_solve_block_noalloc": (st, [vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.POINTER(SolveInfo)]),
         "ddrw_profile_read": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]),
     }
@@ -172,6 +173,13 @@ class Context:
         info = SolveInfo()
         st = self.L.ddrw_solve_block(self._h, int(colour), float(m), _ptr(b), _ptr(x), int(nrhs), ctypes.byref(info))
         self._check(st, "ddrw_solve_block")
+        return info.as_dict()
+
+    def solve_block_noalloc(self, colour, m, b, x):
+        """ddrw_solve_block without device allocation (one right-hand side, device pointers)."""
+        info = SolveInfo()
+        st = self.L.ddrw_solve_block_noalloc(self._h, int(colour), float(m), _ptr(b), _ptr(x), ctypes.byref(info))
+        self._check(st, "ddrw_solve_block_noalloc")
         return info.as_dict()
 
     def solve_D(self, m, b, x, nrhs=1):
