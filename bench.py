@@ -62,7 +62,7 @@ def source_sha(files):
     return h.hexdigest()[:16]
 
 
-STENCIL_SOURCES = ["paper_1211_1214_gb300/csrc/dslash.cu", "paper_1211_1214_gb300/csrc/stencil.cuh",
+STENCIL_SOURCES = ["paper_1211_1214_gb300/csrc/dslash.cuh", "paper_1211_1214_gb300/csrc/stencil.cuh",
                    "paper_1211_1214_gb300/csrc/ddrw_internal.cuh"]
 
 
@@ -310,7 +310,8 @@ def main():
                       "fp64_dslash_calls": infos[-1]["fp64_dslash_calls"],
                       "block_iters_max": infos[-1]["block_iters_max"],
                       "true_rel_residual": infos[-1]["true_rel_residual"]},
-           "logW": [float(x) for x in LW], "wall_s_timed": wall}
+           "logW": [float(x) for x in LW], "wall_s_timed": wall,
+           "autotune": ctx.autotune_report().strip().splitlines()}
 
     # ---- end to end through the public API with host buffers: per step the gauge configuration
     # is copied from pinned host memory, the clover term and inverses rebuilt, the estimate run and

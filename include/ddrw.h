@@ -171,6 +171,13 @@ ddrw_status ddrw_estimate_masses(ddrw_ctx *ctx, int nmass, const double *m2, int
 ddrw_status ddrw_solve_block_noalloc(ddrw_ctx *ctx, int colour, double m, const double *b, double *x,
                                      ddrw_solve_info *info);
 
+/* Autotuner of the stencil launches: on the first launch of each shape (precision, block length,
+ * parities, right-hand sides, diagonal/post modes) it times right-hand sides per thread {1,2,4}
+ * and CTA sizes {64,128,256} with CUDA events and keeps the fastest.  enable = 0 uses a fixed
+ * choice; either call clears the tuned table.  The report lists the tuned shapes, one per line. */
+ddrw_status ddrw_autotune(ddrw_ctx *ctx, int enable);
+ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
+
 /* Kernel timing for measurement (not part of the method): with profiling enabled, CUDA events
  * bracket every launch of the instrumented kernel classes on the context's stream, and
  * ddrw_profile_read returns, per class, the number of launches, their summed device time (ms) and

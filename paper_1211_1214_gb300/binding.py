@@ -24,7 +24,8 @@ _STATUS = {0: "DDRW_OK", 1: "DDRW_EINVAL", 2: "DDRW_ENOMEM", 3: "DDRW_ECUDA", 4:
 EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", "ddrw_volume", "ddrw_load_gauge",
            "ddrw_set_params", "ddrw_set_solver", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
-           "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc"]
+           "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
+           "ddrw_autotune", "ddrw_autotune_report"]
 
 #: kernel classes of ddrw_profile_read
 PROF_DSLASH64, PROF_DSLASH32, PROF_DSLASH64_BLK, PROF_DSLASH32_BLK, PROF_BLOCK64, PROF_BLOCK32, PROF_LAUNCHES = range(7)
@@ -85,6 +86,8 @@ def load(path: str | None = None):
         "ddrw_estimate_masses": (st, [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp,
                                       dp, ctypes.POINTER(SolveInfo)]),
         "ddrw_profile": (st, [vp, ctypes.c_int]),
+        "ddrw_autotune": (st, [vp, ctypes.c_int]),
+        "ddrw_autotune_report": (st, [vp, ctypes.c_char_p, ctypes.c_long]),
         "ddrw_solve_block_noalloc": (st, [vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.POINTER(SolveInfo)]),
         "ddrw_profile_read": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]),
@@ -216,6 +219,14 @@ class Context:
                                   _ptr(e), _ptr(lw), _ptr(rv), _ptr(delta), ctypes.byref(info))
         self._check(st, "ddrw_estimate")
         return e, float(lw[0]), float(rv[0]), info.as_dict()
+
+    def autotune(self, enable=True):
+        self._check(self.L.ddrw_autotune(self._h, int(enable)), "ddrw_autotune")
+
+    def autotune_report(self):
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(self.L.ddrw_autotune_report(self._h, buf, len(buf)), "ddrw_autotune_report")
+        return buf.value.decode()
 
     def profile(self, enable=True):
         self._check(self.L.ddrw_profile(self._h, int(enable)), "ddrw_profile")

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
+#include <cstring>
 #include <deque>
 #include <map>
 #include <string>
@@ -23,6 +25,12 @@ struct MassInv {
     double m;
     double2 *A64 = nullptr;  // [2][18][V]
     float4 *A32 = nullptr;   // [2][9][V]
+};
+
+// a tuned stencil launch configuration
+struct TuneEntry {
+    int nr, nt;
+    float ms;
 };
 
 // A set of masses, one per right-hand-side slot (rhs r uses slot r / ceil(nrhs / n)).
@@ -81,6 +89,10 @@ struct ddrw_ctx {
     std::map<std::string, ddrw::DevBuf> ws;
     double *h_pinned = nullptr;  // small pinned host buffer for scalars
     size_t h_pinned_bytes = 0;
+
+    // stencil autotuner (dslash_tune.cu)
+    bool autotune = true;
+    std::map<std::array<int, 8>, ddrw::TuneEntry> tune;
 
     // kernel timing (ddrw_profile): CUDA events around the instrumented launches
     bool prof_on = false;

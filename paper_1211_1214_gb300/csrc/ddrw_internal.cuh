@@ -266,6 +266,15 @@ struct PrecD {
 #pragma unroll
         for (int k = 0; k < 12; k++) f[k * stride + s] = make_double2(p.v[k / 3][k % 3].re, p.v[k / 3][k % 3].im);
     }
+    // the 6 components of chirality ch (spins 2ch, 2ch+1): planes 6ch .. 6ch+5
+    __device__ static __forceinline__ void load_chiral(const SElem *__restrict__ f, long stride, long s, int ch, cpx<R> *v)
+    {
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            double2 e = __ldg(f + (6 * ch + k) * stride + s);
+            v[k] = {e.x, e.y};
+        }
+    }
     __device__ static __forceinline__ void load_link(const UElem *__restrict__ U, long V, int mu, long s, Link<R> &L)
     {
         const UElem *b = U + (long)mu * 9 * V + s;
@@ -321,6 +330,16 @@ struct PrecS {
         for (int k = 0; k < 6; k++) {
             cpx<R> a = p.v[(2 * k) / 3][(2 * k) % 3], b = p.v[(2 * k + 1) / 3][(2 * k + 1) % 3];
             f[k * stride + s] = make_float4(a.re, a.im, b.re, b.im);
+        }
+    }
+    // the 6 components of chirality ch (spins 2ch, 2ch+1): planes 3ch .. 3ch+2
+    __device__ static __forceinline__ void load_chiral(const SElem *__restrict__ f, long stride, long s, int ch, cpx<R> *v)
+    {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            float4 e = __ldg(f + (3 * ch + k) * stride + s);
+            v[2 * k] = {e.x, e.y};
+            v[2 * k + 1] = {e.z, e.w};
         }
     }
     // two stored rows; row 2 = conj(row0 x row1) (U in SU(3))

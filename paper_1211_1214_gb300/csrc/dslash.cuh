@@ -1,0 +1,221 @@
+// dslash.cuh -- the fused hopping + clover stencil of the Wilson-clover operator (K4) and its
+// block-restricted forms (K5): D_bb / D_ww keep the hops inside a block, D_bw / D_wb the hops
+// between blocks (Eq. 1).  One kernel template serves every form:
+//
+//   out(x) = POST( alpha * DIAG(x) + beta * sum_mu [ (1 - g_mu) U_mu(x) in(x+mu) + (1 + g_mu) U_mu(x-mu)^dag in(x-mu) ] )
+//
+// DIAG is A(m) x = (4 + m) x + C x (or x itself), POST an optional A(m)^-1.  A thread owns one
+// site and NR right-hand sides: each link and clover block is loaded (and two-row links
+// reconstructed) once for the NR.  Groups of NR right-hand sides are interleaved with the site
+// tiles along gridDim.x (group fastest), so the groups of one tile run together and share the
+// tile's links and clover terms through L2.  Right-hand sides carry mass slots (rhs / rpm), so one
+// launch can hold several masses.  The SU(3) x spin stencil is not a dense contraction, so it
+// runs on the FP32/FP64 ALUs, not on tensor cores.  Each hop projects the neighbour to a 2-spin
+// half spinor before the colour multiply (half the complex multiplies of a 4-spin product).
+//
+// The launcher autotunes NR and the CTA size per launch shape on first use (dslash_tune.cu);
+// every launch of this kernel is idempotent (its output sites are never among its inputs), so the
+// tuning runs are harmless.
+#pragma once
+
+#include "ctx.h"
+#include "stencil.cuh"
+
+namespace ddrw {
+
+template <class P> struct DsArgs {
+    typename P::SElem *out;
+    const typename P::SElem *in;
+    const typename P::SElem *x;
+    long rstride;
+    const typename P::UElem *U;
+    const typename P::CElem *Cl;
+    typename P::R alpha, beta;
+    int diag, post;
+    int par0, npar, blk0, nblk;
+    int nrhs, rpm;
+    typename P::R mass4[MAXM];           // 4 + m per slot
+    const typename P::CElem *Ainv[MAXM];  // A(m)^-1 per slot
+};
+
+template <class P, int BL, int HOPSEL, int NR>
+__global__ void __launch_bounds__(256) k_dslash(GeomDev g, DsArgs<P> a)
+{
+    using R = typename P::R;
+    const int ngrp = a.nrhs / NR;
+    const int grp = blockIdx.x % ngrp;
+    const long tile = blockIdx.x / ngrp;
+    const long nper = (long)a.nblk * BlockShape<BL>::VBH;
+    const long i = tile * blockDim.x + threadIdx.x;
+    if (i >= nper * a.npar) return;
+    const int r0 = grp * NR;
+    const long roff = (long)r0 * a.rstride;
+    const int pp = (int)(i / nper);
+    const long s = (long)(a.par0 + pp) * g.vh + (long)a.blk0 * BlockShape<BL>::VBH + (i - pp * nper);
+    Site<BL> st;
+    decode_site<BL>(s, g, st);
+
+    Spinor<R> acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) zero(acc[r]);
+    if (a.beta != R(0)) {
+        const typename P::SElem *in = a.in + roff;
+        hop_dir_multi<P, BL, HOPSEL, 0, NR>(g, st, s, in, a.rstride, a.U, acc);
+        hop_dir_multi<P, BL, HOPSEL, 1, NR>(g, st, s, in, a.rstride, a.U, acc);
+        hop_dir_multi<P, BL, HOPSEL, 2, NR>(g, st, s, in, a.rstride, a.U, acc);
+        hop_dir_multi<P, BL, HOPSEL, 3, NR>(g, st, s, in, a.rstride, a.U, acc);
+#pragma unroll
+        for (int r = 0; r < NR; r++) scale(acc[r], a.beta);
+    }
+    if (a.diag) {
+        const typename P::SElem *x = a.x + roff;
+#pragma unroll
+        for (int ch = 0; ch < 2; ch++) {
+            R c[36];
+            if (a.diag == 1) P::load_clover(a.Cl, g.V, s, ch, c);
+#pragma unroll
+            for (int r = 0; r < NR; r++) {
+                cpx<R> v6[6], o6[6];
+                P::load_chiral(x + r * a.rstride, g.V, s, ch, v6);
+                if (a.diag == 1) herm6_mul<R>(c, a.mass4[(r0 + r) / a.rpm], v6, o6);
+                else
+#pragma unroll
+                    for (int k = 0; k < 6; k++) o6[k] = v6[k];
+#pragma unroll
+                for (int k = 0; k < 6; k++)
+                    acc[r].v[2 * ch + k / 3][k % 3] = acc[r].v[2 * ch + k / 3][k % 3] + a.alpha * o6[k];
+            }
+        }
+    }
+    if (a.post) {
+        // a group of NR right-hand sides never straddles two mass slots (launcher's rule)
+        const typename P::CElem *Ai = a.Ainv[r0 / a.rpm];
+#pragma unroll
+        for (int ch = 0; ch < 2; ch++) {
+            R c[36];
+            P::load_clover(Ai, g.V, s, ch, c);
+#pragma unroll
+            for (int r = 0; r < NR; r++) {
+                cpx<R> v6[6], o6[6];
+#pragma unroll
+                for (int k = 0; k < 6; k++) v6[k] = acc[r].v[2 * ch + k / 3][k % 3];
+                herm6_mul<R>(c, R(0), v6, o6);
+#pragma unroll
+                for (int k = 0; k < 6; k++) acc[r].v[2 * ch + k / 3][k % 3] = o6[k];
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; r++) P::store_spinor(a.out + roff + r * a.rstride, g.V, s, acc[r]);
+}
+
+// launch configuration of one stencil launch
+struct DsConfig {
+    int nr = 1;    // right-hand sides per thread
+    int nt = 128;  // threads per CTA
+};
+
+template <class P, int BL>
+DsArgs<P> make_args(ddrw_ctx *ctx, const DslashCall &c)
+{
+    using R = typename P::R;
+    DsArgs<P> a;
+    a.out = (typename P::SElem *)c.out;
+    a.in = (const typename P::SElem *)c.in;
+    a.x = (const typename P::SElem *)c.x;
+    a.rstride = c.rstride;
+    a.alpha = R(c.alpha);
+    a.beta = R(c.beta);
+    a.diag = c.diag;
+    a.post = c.post;
+    a.par0 = c.par0;
+    a.npar = c.npar;
+    a.blk0 = c.blk0;
+    a.nblk = c.nblk;
+    int nm = c.nmass < 1 ? 1 : c.nmass;
+    a.nrhs = c.nrhs;
+    a.rpm = (c.nrhs + nm - 1) / nm;
+    for (int k = 0; k < MAXM; k++) {
+        int kk = k < nm ? k : nm - 1;
+        a.mass4[k] = R(4.0 + c.masses[kk]);
+        a.Ainv[k] = (const typename P::CElem *)c.Ainv[kk];
+    }
+    if constexpr (sizeof(R) == 8) {
+        a.U = (const typename P::UElem *)ctx->U64;
+        a.Cl = (const typename P::CElem *)ctx->C64;
+    } else {
+        a.U = (const typename P::UElem *)ctx->U32;
+        a.Cl = (const typename P::CElem *)ctx->C32;
+    }
+    return a;
+}
+
+template <class P, int BL>
+void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig cfg)
+{
+    GeomDev g = geom_dev(ctx);
+    long n = (long)c.npar * c.nblk * BlockShape<BL>::VBH;
+    unsigned grid = (unsigned)(((n + cfg.nt - 1) / cfg.nt) * (c.nrhs / cfg.nr));
+    ++ctx->launches;
+    if (c.hopsel == 0) {
+        switch (cfg.nr) {
+        case 4: k_dslash<P, BL, 0, 4><<<grid, cfg.nt, 0, ctx->stream>>>(g, a); break;
+        case 2: k_dslash<P, BL, 0, 2><<<grid, cfg.nt, 0, ctx->stream>>>(g, a); break;
+        default: k_dslash<P, BL, 0, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a); break;
+        }
+    } else if (c.hopsel == 1) {
+        k_dslash<P, BL, 1, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
+    } else {
+        k_dslash<P, BL, 2, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
+    }
+}
+
+// compulsory bytes of a launch: per output site the R input, output and diagonal-input spinors,
+// the links of its hops (8 per site when the output is one parity, since the backward links are
+// stored at the other parity; 4 per site for both parities), clover terms once
+template <class P>
+double compulsory_bytes(const DslashCall &c, long n)
+{
+    const double S = sizeof(typename P::SElem) * P::SPLANES, Lk = sizeof(typename P::UElem) * P::UPLANES,
+                 Cb = sizeof(typename P::CElem) * P::CPLANES;
+    double per = S * c.nrhs * ((c.beta != 0.0) + 1 + (c.diag != 0));
+    if (c.beta != 0.0) per += (c.npar == 1 ? 8.0 : 4.0) * Lk;
+    if (c.diag == 1) per += Cb;
+    if (c.post) per += Cb;
+    return per * (double)n;
+}
+
+DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
+                      void (*run)(ddrw_ctx *, const DslashCall &, DsConfig));
+
+template <class P, int BL>
+void run_cfg(ddrw_ctx *ctx, const DslashCall &c, DsConfig cfg)
+{
+    launch_cfg<P, BL>(ctx, c, make_args<P, BL>(ctx, c), cfg);
+}
+
+template <class P, int BL>
+void launch_bl(ddrw_ctx *ctx, const DslashCall &c)
+{
+    using R = typename P::R;
+    long n = (long)c.npar * c.nblk * BlockShape<BL>::VBH;
+    if (n == 0 || c.nrhs == 0) return;
+    DsConfig cfg;
+    if (c.hopsel == 0) cfg = tuned_config(ctx, c, sizeof(R) == 8 ? 64 : 32, BL, &run_cfg<P, BL>);
+    int kind = (sizeof(R) == 8 ? PROF_DSLASH64 : PROF_DSLASH32) + (c.hopsel != 0 ? 2 : 0);
+    ProfScope ps(ctx, kind, compulsory_bytes<P>(c, n));
+    launch_cfg<P, BL>(ctx, c, make_args<P, BL>(ctx, c), cfg);
+}
+
+template <class P>
+void launch(ddrw_ctx *ctx, const DslashCall &c)
+{
+    switch (ctx->l) {
+    case 2: launch_bl<P, 2>(ctx, c); break;
+    case 4: launch_bl<P, 4>(ctx, c); break;
+    case 6: launch_bl<P, 6>(ctx, c); break;
+    default: launch_bl<P, 8>(ctx, c); break;
+    }
+}
+
+}  // namespace ddrw

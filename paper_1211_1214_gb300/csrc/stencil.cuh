@@ -73,6 +73,61 @@ __device__ __forceinline__ void hop_sum(const GeomDev &g, const Site<BL> &st, lo
     hop_dir<P, BL, HOPSEL, 3, RO>(g, st, s, in, U, acc);
 }
 
+// Hops of NR right-hand sides at once (fields rstride elements apart): the link of each hop is
+// loaded, and for two-row storage reconstructed, once for all NR.
+template <class P, int BL, int HOPSEL, int MU, int NR>
+__device__ __forceinline__ void hop_dir_multi(const GeomDev &g, const Site<BL> &st, long s,
+                                              const typename P::SElem *in, long rstride,
+                                              const typename P::UElem *__restrict__ U,
+                                              Spinor<typename P::R> (&acc)[NR])
+{
+    using R = typename P::R;
+    bool cross;
+    int ph;
+    {
+        long sf = neighbour<BL>(st, MU, +1, g, &cross, &ph);
+        if (HOPSEL == 0 || (HOPSEL == 1 && !cross) || (HOPSEL == 2 && cross)) {
+            Link<R> L;
+            P::load_link(U, g.V, MU, s, L);
+#pragma unroll
+            for (int r = 0; r < NR; r++) {
+                Spinor<R> p;
+                P::load_spinor(in + r * rstride, g.V, sf, p);
+                Half<R> h, w;
+                project<MU, -1>(p, h);
+                link_mul(L, h, w);
+                if (ph < 0)
+#pragma unroll
+                    for (int a = 0; a < 2; a++)
+#pragma unroll
+                        for (int c = 0; c < 3; c++) w.v[a][c] = -w.v[a][c];
+                reconstruct_add<MU, -1>(acc[r], w);
+            }
+        }
+    }
+    {
+        long sb = neighbour<BL>(st, MU, -1, g, &cross, &ph);
+        if (HOPSEL == 0 || (HOPSEL == 1 && !cross) || (HOPSEL == 2 && cross)) {
+            Link<R> L;
+            P::load_link(U, g.V, MU, sb, L);
+#pragma unroll
+            for (int r = 0; r < NR; r++) {
+                Spinor<R> p;
+                P::load_spinor(in + r * rstride, g.V, sb, p);
+                Half<R> h, w;
+                project<MU, +1>(p, h);
+                link_dag_mul(L, h, w);
+                if (ph < 0)
+#pragma unroll
+                    for (int a = 0; a < 2; a++)
+#pragma unroll
+                        for (int c = 0; c < 3; c++) w.v[a][c] = -w.v[a][c];
+                reconstruct_add<MU, +1>(acc[r], w);
+            }
+        }
+    }
+}
+
 // v <- (diag + H_ch) v on both chirality blocks, H from a packed clover-format array
 template <class P>
 __device__ __forceinline__ void clover_apply(const typename P::CElem *__restrict__ Cl, long V, long s,
