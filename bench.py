@@ -239,7 +239,7 @@ def main():
     ctx.load_gauge(U_pin.to(dev))
     ctx.set_params(w["csw"], w["m1"], w["m2s"][0])
     prec = binding.MIXED_FP32 if args.prec == "mixed32" else binding.FP64
-    tol_block = 1e-12 if prec != binding.FP64 else 1e-13
+    tol_block = 1e-10 if prec != binding.FP64 else 1e-13
     ctx.set_solver(prec, tol_outer=1e-10, tol_block=tol_block)
     nhit, m2s = w["nhit"], list(w["m2s"])
     per_step = nhit * len(m2s)

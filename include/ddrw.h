@@ -59,7 +59,7 @@ typedef enum {
 typedef enum {
     DDRW_FP64 = 0,       /* every kernel in FP64 */
     DDRW_MIXED_FP32 = 1, /* inner solves in FP32 storage and arithmetic, FP64 defect correction */
-    DDRW_MIXED_FP16 = 2  /* inner solves in FP16 storage, FP32 arithmetic, FP64 defect correction */
+    DDRW_MIXED_FP16 = 2  /* reserved: FP16 storage is not built; ddrw_set_solver rejects it (DDRW_EINVAL) */
 } ddrw_prec;
 
 typedef enum { DDRW_BLACK = 0, DDRW_WHITE = 1, DDRW_ALL = 2 } ddrw_colour;

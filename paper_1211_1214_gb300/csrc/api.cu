@@ -460,6 +460,7 @@ ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, dou
 {
     if (!ctx) return DDRW_EINVAL;
     if (prec < DDRW_FP64 || prec > DDRW_MIXED_FP16) return set_error(ctx, DDRW_EINVAL, "unknown precision");
+    if (prec == DDRW_MIXED_FP16) return set_error(ctx, DDRW_EINVAL, "FP16 storage is not built in this library");
     if (!(tol_outer > 0) || !(tol_block > 0) || maxiter <= 0) return set_error(ctx, DDRW_EINVAL, "bad tolerance");
     ctx->prec = prec;
     ctx->tol_outer = tol_outer;

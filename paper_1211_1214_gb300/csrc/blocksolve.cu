@@ -111,8 +111,9 @@ ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const do
     } else {
         if ((st = workspace(ctx, "blk_e64", f64, (void **)&e64))) return st;
     }
-    // tolerance of one inner solve: the target itself in FP64, 1e-6 per cycle in FP32
-    const double tol_inner = mixed ? std::max(tol, 1e-6) : tol * 0.5;
+    // tolerance of one inner solve: the target itself in FP64; in FP32 what is still missing to
+    // reach tol (margin 2, worst right-hand side), but no deeper than 1e-6
+    double tol_inner = mixed ? std::max(tol, 1e-6) : tol * 0.5;
     const double2 *rhs = b;  // first cycle: r = b, x = 0
     bool first = true;
     int cycles = 0;
@@ -121,6 +122,10 @@ ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const do
         DDRW_CUDA_CHECK(cudaMemsetAsync(stat, 0, sizeof(int) * 2, ctx->stream));
         if (mixed) {
             const std::vector<double> &nr = first ? bb : rr;
+            double need = 1.0;
+            for (int r = 0; r < nrhs; r++)
+                if (nr[r] > 0) need = std::min(need, 0.5 * tol * std::sqrt(bb[r] / nr[r]));
+            tol_inner = std::max(1e-6, std::min(need, 0.5));
             for (int r = 0; r < nrhs; r++) {
                 double n = std::sqrt(nr[r]);
                 scale[r] = n > 0 ? 1.0 / n : 0.0;

@@ -83,11 +83,11 @@ void apply_mhat(ddrw_ctx *ctx, const MassSet &ms, int nrhs, long rs, const typen
     stencil<P>(ctx, d);
 }
 
-// Inner even-odd BiCGStab in policy P: solve D x = b (full fields) to relative tolerance tol
-// against ||b|| (bb: host ||b||^2 per rhs).  Adds iterations to *iters.
+// Inner even-odd BiCGStab in policy P: solve D x = b (full fields) until the even-odd residual of
+// right-hand side r satisfies ||r||^2 <= thresh[r].  Adds iterations to *iters.
 template <class P>
 ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SElem *b, typename P::SElem *x, int nrhs,
-                        const std::vector<double> &bb, double tol, int maxiter, int *iters)
+                        const std::vector<double> &thresh, int maxiter, int *iters)
 {
     using E = typename P::SElem;
     const long rs = (long)P::SPLANES * ctx->V;
@@ -126,7 +126,7 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
     std::vector<KScal> h(nrhs);
     for (int k = 0; k < nrhs; k++) {
         h[k] = KScal{};
-        h[k].thresh = tol * tol * bb[k];
+        h[k].thresh = thresh[k];
         h[k].maxiter = maxiter;
     }
     DDRW_CUDA_CHECK(cudaMemcpyAsync(sc, h.data(), sizeof(KScal) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
@@ -205,7 +205,8 @@ ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, dou
     } else if ((st = workspace(ctx, "full_e64", f64, (void **)&e64))) {
         return st;
     }
-    const double tol_inner = mixed ? std::max(tol, 1e-6) : tol * 0.5;
+    // inner target per right-hand side and cycle: what is still missing to reach tol, with a
+    // margin of 2, but no deeper than an FP32 solve reliably goes (1e-6)
     const double2 *rhs = b;
     bool first = true;
     std::vector<double> scale(nrhs), unscale(nrhs), ones(nrhs, 1.0);
@@ -223,14 +224,20 @@ ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, dou
                                             ctx->stream));
             VecRange all{V, 0, V, rs64, nrhs};
             to32(ctx, all, rs32, rhs, b32, scale_d);
-            std::vector<double> unit(nrhs);
-            for (int r = 0; r < nrhs; r++) unit[r] = nr[r] > 0 ? 1.0 : 0.0;
-            if ((st = eo_bicgstab<PrecS>(ctx, ms, b32, e32, nrhs, unit, tol_inner, maxiter, &iters))) return st;
+            std::vector<double> th(nrhs);
+            for (int r = 0; r < nrhs; r++) {
+                double need = nr[r] > 0 ? 0.5 * tol * std::sqrt(bb[r] / nr[r]) : 1.0;
+                double ti = std::max(1e-6, std::min(need, 0.5));
+                th[r] = nr[r] > 0 ? ti * ti : 0.0;
+            }
+            if ((st = eo_bicgstab<PrecS>(ctx, ms, b32, e32, nrhs, th, maxiter, &iters))) return st;
             if (first) DDRW_CUDA_CHECK(cudaMemsetAsync(x, 0, f64, ctx->stream));
             add32(ctx, all, rs32, e32, x, scale_d + nrhs);
         } else {
             double2 *target = first ? x : e64;
-            if ((st = eo_bicgstab<PrecD>(ctx, ms, rhs, target, nrhs, nr, tol_inner, maxiter, &iters))) return st;
+            std::vector<double> th(nrhs);
+            for (int r = 0; r < nrhs; r++) th[r] = 0.25 * tol * tol * bb[r];
+            if ((st = eo_bicgstab<PrecD>(ctx, ms, rhs, target, nrhs, th, maxiter, &iters))) return st;
             if (!first) Blas<PrecD>::axpby(ctx, VecRange{V, 0, V, rs64, nrhs}, 1.0, e64, 1.0, x);
         }
         // res = b - D x in FP64
