@@ -151,6 +151,18 @@ ddrw_status ddrw_estimate_masses(ddrw_ctx *ctx, int nmass, const double *m2, int
                                  uint64_t hit_offset, double *exponents, double *logW, double *rel_var,
                                  ddrw_solve_info *info);
 
+/* The adjoint of the estimate: for each of nhit noise vectors (as in ddrw_estimate) the exponent
+ * e_j, its derivative with respect to every link and with respect to m2 (m1 fixed), by reverse
+ * mode through the Schur complement (recomputing the solutions, not storing Krylov iterates):
+ *   dU[x][mu][a] = sum_j w_j d e_j / dt,  U_mu(x) -> exp(i t lambda_a/2) U_mu(x)  (left multiplication,
+ *                  Gell-Mann matrices lambda_a, a = 1..8 stored 0..7; x lexicographic),
+ *   dm2[j]       = d e_j / d m2.
+ * weights w_j (null: all 1); eta packed or null (Philox noise of seed, hit_offset); exponents[nhit],
+ * dU[V][4][8] (host or device) and dm2[nhit] are each optional.  Solves run in the context's
+ * precision; the force kernels in FP64. */
+ddrw_status ddrw_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64_t hit_offset, const double *eta,
+                       const double *weights, double *exponents, double *dU, double *dm2, ddrw_solve_info *info);
+
 /* ddrw_solve_block for callers that cannot allocate device memory.  The paper has no counterpart:
  * this is an integration aid.  Some callers may not call cudaMalloc -- code running while a
  * framework's memory pool is frozen or a graph is being built, or a host application that owns

@@ -53,6 +53,9 @@ def lib():
         L.orc_exponent.restype = ctypes.c_int
         L.orc_exponent.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, dp, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_long, dp, dp, dp, ctypes.POINTER(ctypes.c_long)]
+        L.orc_force.restype = ctypes.c_int
+        L.orc_force.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, dp, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_long, dp, dp, dp]
         L.orc_gamma.argtypes = [ctypes.c_int, dp]
         u32p = ctypes.POINTER(ctypes.c_uint32)
         L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
@@ -176,6 +179,22 @@ class Lattice:
         if st != 0:
             raise RuntimeError("oracle solve did not converge")
         return {"e": e.value, "r": r, "delta": delta, "iters": list(iters)}
+
+
+def _force(self, m1, m2, eta, tol_block=1e-13, tol_outer=1e-13, maxiter=100000, links=True):
+    """Link derivatives dU[x, mu, a] = de/dt for U_mu(x) -> exp(i t lambda_a/2) U_mu(x) and de/dm2."""
+    eta = np.ascontiguousarray(eta, dtype=np.complex128).reshape(self.V, 4, 3)
+    e = ctypes.c_double(0)
+    dm2 = ctypes.c_double(0)
+    dU = np.zeros((self.V, 4, 8), dtype=np.float64) if links else None
+    st = lib().orc_force(self._h, float(m1), float(m2), _dp(eta), float(tol_block), float(tol_outer), int(maxiter),
+                         ctypes.byref(e), _dp(dU) if links else None, ctypes.byref(dm2))
+    if st != 0:
+        raise RuntimeError("oracle solve did not converge")
+    return e.value, dU, dm2.value
+
+
+Lattice.force = _force
 
 
 def log_w(exponents) -> float:

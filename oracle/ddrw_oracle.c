@@ -381,8 +381,18 @@ static cplx vdot(long n, const cplx *a, const cplx *b) /* sum conj(a) b */
  * number of operator applications of D (not counting D^dag), or -1 if the true relative residual
  * did not reach tol within maxiter iterations; *relres receives the final true relative residual.
  */
+static long cgnr_d(const orc_lat *g, double m, int dag, int sel, const cplx *b, cplx *x, double tol, long maxiter,
+                   double *relres);
+
 static long cgnr(const orc_lat *g, double m, int sel, const cplx *b, cplx *x, double tol, long maxiter,
                  double *relres)
+{
+    return cgnr_d(g, m, 0, sel, b, x, tol, maxiter, relres);
+}
+
+/* CGNR for A = D_{sel,sel} (dag = 0) or A = (D^dag)_{sel,sel} (dag = 1): CG on A^dag A x = A^dag b. */
+static long cgnr_d(const orc_lat *g, double m, int dag, int sel, const cplx *b, cplx *x, double tol, long maxiter,
+                   double *relres)
 {
     long n = g->V * NSC;
     cplx *r = (cplx *)malloc(sizeof(cplx) * n), *z = (cplx *)malloc(sizeof(cplx) * n);
@@ -398,15 +408,15 @@ static long cgnr(const orc_lat *g, double m, int sel, const cplx *b, cplx *x, do
     double res = 1.0;
     for (int restart = 0; restart < 50 && it < maxiter; restart++) {
         /* true residual r = b - A x */
-        apply_dirac(g, m, 0, sel, sel, x, w);
+        apply_dirac(g, m, dag, sel, sel, x, w);
         for (long i = 0; i < n; i++) r[i] = b[i] - w[i];
         res = sqrt(vnorm2(n, r) / bn2);
         if (res <= tol) break;
-        apply_dirac(g, m, 1, sel, sel, r, z);
+        apply_dirac(g, m, !dag, sel, sel, r, z);
         memcpy(pp, z, sizeof(cplx) * n);
         double zz = vnorm2(n, z);
         while (it < maxiter) {
-            apply_dirac(g, m, 0, sel, sel, pp, w);
+            apply_dirac(g, m, dag, sel, sel, pp, w);
             it++;
             double ww = vnorm2(n, w);
             if (ww == 0.0) break;
@@ -417,14 +427,14 @@ static long cgnr(const orc_lat *g, double m, int sel, const cplx *b, cplx *x, do
             }
             double rr = vnorm2(n, r);
             if (sqrt(rr / bn2) <= 0.5 * tol) break;
-            apply_dirac(g, m, 1, sel, sel, r, z);
+            apply_dirac(g, m, !dag, sel, sel, r, z);
             double zz_new = vnorm2(n, z);
             double beta = zz_new / zz;
             zz = zz_new;
             for (long i = 0; i < n; i++) pp[i] = z[i] + beta * pp[i];
         }
     }
-    apply_dirac(g, m, 0, sel, sel, x, w);
+    apply_dirac(g, m, dag, sel, sel, x, w);
     for (long i = 0; i < n; i++) r[i] = b[i] - w[i];
     res = sqrt(vnorm2(n, r) / bn2);
     if (relres) *relres = res;
@@ -553,4 +563,295 @@ void orc_noise(uint64_t seed, uint64_t hit0, int nhit, long n, double *eta)
             eta[2 * ((size_t)h * n + k)] = rho * cos(two_pi * u2);
             eta[2 * ((size_t)h * n + k) + 1] = rho * sin(two_pi * u2);
         }
+}
+
+/* ------------------------------------------------------------------ the adjoint (link and mass derivatives) */
+
+/*
+ * Derivative of one clover leaf product with respect to the link (lx, lmu) in direction
+ * dU = i T_a U (T_a = lambda_a / 2): product rule over the leaf's four factors; a factor that is
+ * the link becomes i T_a U, a factor that is its adjoint becomes -i U^dag T_a, the others stay.
+ */
+typedef struct {
+    long site;
+    int dir;
+    int dag;
+} factor;
+
+static const double LAMBDA8 = 0.57735026918962576451;
+
+static void gell_mann_half(int a, cplx *T)
+{
+    for (int k = 0; k < 9; k++) T[k] = 0;
+    switch (a) {
+    case 0: T[1] = T[3] = 0.5; break;
+    case 1: T[1] = -0.5 * I; T[3] = 0.5 * I; break;
+    case 2: T[0] = 0.5; T[4] = -0.5; break;
+    case 3: T[2] = T[6] = 0.5; break;
+    case 4: T[2] = -0.5 * I; T[6] = 0.5 * I; break;
+    case 5: T[5] = T[7] = 0.5; break;
+    case 6: T[5] = -0.5 * I; T[7] = 0.5 * I; break;
+    default: T[0] = T[4] = 0.5 * LAMBDA8; T[8] = -LAMBDA8; break;
+    }
+}
+
+static void factor_matrix(const orc_lat *g, factor f, long lx, int lmu, const cplx *T, int deriv, cplx *out)
+{
+    const cplx *u = link(g, f.site, f.dir);
+    if (!deriv) {
+        if (f.dag) m3_dag(u, out);
+        else memcpy(out, u, sizeof(cplx) * 9);
+        return;
+    }
+    (void)lx; (void)lmu;
+    cplx t[9];
+    if (!f.dag) { /* i T U */
+        m3_mul(T, u, t);
+        for (int k = 0; k < 9; k++) out[k] = I * t[k];
+    } else { /* -i U^dag T */
+        cplx ud[9];
+        m3_dag(u, ud);
+        m3_mul(ud, T, t);
+        for (int k = 0; k < 9; k++) out[k] = -I * t[k];
+    }
+}
+
+/* dQ_{mu nu}(y): derivative of the four-leaf sum at y with respect to link (lx, lmu), generator a */
+static int clover_leaves_deriv(const orc_lat *g, long y, int mu, int nu, long lx, int lmu, const cplx *T, cplx *dQ)
+{
+    long ypm = neighbour(g, y, mu, +1), ypn = neighbour(g, y, nu, +1);
+    long ymm = neighbour(g, y, mu, -1), ymn = neighbour(g, y, nu, -1);
+    long ymm_pn = neighbour(g, ymm, nu, +1), ymm_mn = neighbour(g, ymm, nu, -1);
+    long ymn_pm = neighbour(g, ymn, mu, +1);
+    factor leaves[4][4] = {
+        {{y, mu, 0}, {ypm, nu, 0}, {ypn, mu, 1}, {y, nu, 1}},
+        {{y, nu, 0}, {ymm_pn, mu, 1}, {ymm, nu, 1}, {ymm, mu, 0}},
+        {{ymm, mu, 1}, {ymm_mn, nu, 1}, {ymm_mn, mu, 0}, {ymn, nu, 0}},
+        {{ymn, nu, 1}, {ymn, mu, 0}, {ymn_pm, nu, 0}, {y, mu, 1}},
+    };
+    int any = 0;
+    for (int k = 0; k < 9; k++) dQ[k] = 0;
+    for (int l = 0; l < 4; l++)
+        for (int d = 0; d < 4; d++) {
+            if (leaves[l][d].site != lx || leaves[l][d].dir != lmu) continue;
+            any = 1;
+            cplx m[4][9], t1[9], t2[9], prod[9];
+            for (int f = 0; f < 4; f++) factor_matrix(g, leaves[l][f], lx, lmu, T, f == d, m[f]);
+            m3_mul(m[0], m[1], t1);
+            m3_mul(t1, m[2], t2);
+            m3_mul(t2, m[3], prod);
+            for (int k = 0; k < 9; k++) dQ[k] += prod[k];
+        }
+    return any;
+}
+
+/* out_k(y) = dC(y) in_k(y) on every site y whose clover term depends on link (lx, lmu), for k < nin;
+ * returns the number of those sites, listed in sites[] */
+static int apply_dclover(const orc_lat *g, long lx, int lmu, const cplx *T, int nin, cplx *const *in, cplx *const *out,
+                         long *sites)
+{
+    init_gamma();
+    cplx sigma[4][4][4][4];
+    for (int mu = 0; mu < 4; mu++)
+        for (int nu = 0; nu < 4; nu++)
+            for (int a = 0; a < 4; a++)
+                for (int b = 0; b < 4; b++) {
+                    cplx s = 0;
+                    for (int k = 0; k < 4; k++)
+                        s += GAMMA[mu][a][k] * GAMMA[nu][k][b] - GAMMA[nu][a][k] * GAMMA[mu][k][b];
+                    sigma[mu][nu][a][b] = 0.5 * I * s;
+                }
+    /* candidate sites: lx, lx + lmu, and their shifts by +-nu */
+    long cand[64];
+    int nc = 0;
+    long base[2] = {lx, neighbour(g, lx, lmu, +1)};
+    for (int b = 0; b < 2; b++) {
+        cand[nc++] = base[b];
+        for (int nu = 0; nu < 4; nu++) {
+            if (nu == lmu) continue;
+            cand[nc++] = neighbour(g, base[b], nu, +1);
+            cand[nc++] = neighbour(g, base[b], nu, -1);
+        }
+    }
+    int ns = 0;
+    for (int i = 0; i < nc; i++) {
+        int dup = 0;
+        for (int j = 0; j < ns; j++)
+            if (sites[j] == cand[i]) dup = 1;
+        if (dup) continue;
+        long y = cand[i];
+        cplx dC[NSC * NSC];
+        for (int k = 0; k < NSC * NSC; k++) dC[k] = 0;
+        int any = 0;
+        for (int mu = 0; mu < 4; mu++)
+            for (int nu = 0; nu < 4; nu++) {
+                if (mu == nu) continue;
+                cplx dQ[9], dF[9];
+                if (!clover_leaves_deriv(g, y, mu, nu, lx, lmu, T, dQ)) continue;
+                any = 1;
+                for (int a = 0; a < 3; a++)
+                    for (int b = 0; b < 3; b++) dF[3 * a + b] = (dQ[3 * a + b] - conj(dQ[3 * b + a])) / 8.0;
+                cplx pref = g->csw * 0.25 * I;
+                for (int al = 0; al < 4; al++)
+                    for (int be = 0; be < 4; be++) {
+                        cplx s = pref * sigma[mu][nu][al][be];
+                        if (s == 0) continue;
+                        for (int a = 0; a < 3; a++)
+                            for (int b = 0; b < 3; b++) dC[(3 * al + a) * NSC + 3 * be + b] += s * dF[3 * a + b];
+                    }
+            }
+        if (!any) continue;
+        sites[ns++] = y;
+        for (int k = 0; k < nin; k++)
+            for (int i2 = 0; i2 < NSC; i2++) {
+                cplx acc = 0;
+                for (int j = 0; j < NSC; j++) acc += dC[i2 * NSC + j] * in[k][(size_t)y * NSC + j];
+                out[k][(size_t)y * NSC + i2] += acc;
+            }
+    }
+    return ns;
+}
+
+/* sum_k c_k sum_y L_k(y)^dag (dD R_k)(y) for the derivative of D with respect to link (lx, lmu),
+ * generator a; work: a zeroed full-lattice vector per pair (left zeroed on return) */
+static cplx dD_bilinear(const orc_lat *g, long lx, int lmu, const cplx *T, int npair, cplx *const *L,
+                        cplx *const *R, const double *c, cplx *const *work)
+{
+    long sites[64];
+    long xp = neighbour(g, lx, lmu, +1);
+    double ph = hop_phase(g, lx, lmu, +1);
+    /* hopping: (x, x+mu) entry -1/2 (1 - g) dU, (x+mu, x) entry -1/2 (1 + g) dU^dag */
+    cplx dU[9], dUd[9], t[9], ud[9];
+    const cplx *u = link(g, lx, lmu);
+    m3_mul(T, u, t);
+    for (int k = 0; k < 9; k++) dU[k] = I * t[k];
+    m3_dag(u, ud);
+    m3_mul(ud, T, t);
+    for (int k = 0; k < 9; k++) dUd[k] = -I * t[k];
+    cplx acc = 0;
+    for (int pr = 0; pr < npair; pr++)
+        for (int side = 0; side < 2; side++) {
+            long row = side ? xp : lx, col = side ? lx : xp;
+            const cplx *W = side ? dUd : dU;
+            double sg = side ? 1.0 : -1.0; /* (1 + sg g) */
+            const cplx *r = R[pr] + (size_t)col * NSC;
+            cplx Wr[NSC], o[NSC];
+            for (int al = 0; al < 4; al++)
+                for (int a = 0; a < 3; a++) {
+                    cplx v = 0;
+                    for (int b = 0; b < 3; b++) v += W[3 * a + b] * r[3 * al + b];
+                    Wr[3 * al + a] = v;
+                }
+            for (int al = 0; al < 4; al++)
+                for (int a = 0; a < 3; a++) {
+                    cplx v = Wr[3 * al + a];
+                    for (int be = 0; be < 4; be++) v += sg * GAMMA[lmu][al][be] * Wr[3 * be + a];
+                    o[3 * al + a] = -0.5 * ph * v;
+                }
+            const cplx *l = L[pr] + (size_t)row * NSC;
+            for (int i = 0; i < NSC; i++) acc += c[pr] * conj(l[i]) * o[i];
+        }
+    /* clover: dC built once, applied to every pair */
+    if (g->csw != 0.0) {
+        int ns = apply_dclover(g, lx, lmu, T, npair, R, work, sites);
+        for (int pr = 0; pr < npair; pr++)
+            for (int k = 0; k < ns; k++) {
+                long y = sites[k];
+                for (int i = 0; i < NSC; i++) {
+                    acc += c[pr] * conj(L[pr][(size_t)y * NSC + i]) * work[pr][(size_t)y * NSC + i];
+                    work[pr][(size_t)y * NSC + i] = 0;
+                }
+            }
+    }
+    return acc;
+}
+
+/*
+ * Link and mass derivatives of e = eta^dag (Mh^dag Mh - 1) eta (one noise vector eta on supp P):
+ *   de = 2 Re <y, dMh eta> with y = Mh eta;  dMh = A2^-1 (dA1 - dA2 Mh);  z = A2^-dag y;
+ *   A_k^-dag = P(1 - D_wb^dag Dcal_bw^dag)P, Dcal_bw^dag y = [(D^dag)^-1 y]_w;
+ *   <z, dA v> = -<z, dX v>, X = B^-1 C W^-1 E, expanded by the product rule into
+ *   <zt, dD (q - a)> + <wt, dD (a - v)>, a = W^-1 E v, q = B^-1 C a, zt = B^-dag z,
+ *   wt = W^-dag C^dag zt (adjoints from D^dag written out; solves by CGNR).
+ * dU[(x*4 + mu)*8 + a] = d e / dt for U_mu(x) -> exp(i t lambda_a/2) U_mu(x); *dm2 = d e / d m2.
+ */
+int orc_force(void *p, double m1, double m2, const double *eta_d, double tol_block, double tol_outer, long maxiter,
+              double *e_out, double *dU, double *dm2)
+{
+    const orc_lat *g = (const orc_lat *)p;
+    const cplx *eta = (const cplx *)eta_d;
+    long n = g->V * NSC;
+    double rel;
+    int status = 0;
+    cplx *y = (cplx *)calloc(n, sizeof(cplx)), *u = (cplx *)calloc(n, sizeof(cplx));
+    cplx *z = (cplx *)calloc(n, sizeof(cplx)), *t = (cplx *)calloc(n, sizeof(cplx));
+    cplx *work = (cplx *)calloc(n, sizeof(cplx));
+    cplx *Lk[2][2], *Rk[2][2];
+    for (int k = 0; k < 2; k++)
+        for (int q = 0; q < 2; q++) {
+            Lk[k][q] = (cplx *)calloc(n, sizeof(cplx));
+            Rk[k][q] = (cplx *)calloc(n, sizeof(cplx));
+        }
+    if (orc_exponent(p, m1, m2, eta_d, tol_block, tol_outer, maxiter, e_out, NULL, (double *)y, NULL)) status = -1;
+    for (long i = 0; i < n; i++) y[i] += eta[i];
+
+    /* z = y - P D_wb^dag u_w,  D(m2)^dag u = (y_b ; 0) */
+    if (cgnr_d(g, m2, 1, SEL_ALL, y, u, tol_outer, maxiter, &rel) < 0) status = -1;
+    for (long x = 0; x < g->V; x++)
+        if (g->colour[x] == 0)
+            for (int i = 0; i < NSC; i++) u[(size_t)x * NSC + i] = 0;
+    apply_dirac(g, 0.0, 1, SEL_BLACK, SEL_WHITE, u, t);
+    for (long i = 0; i < n; i++) z[i] = y[i] - t[i];
+    mask_suppP(g, z);
+
+    double masses[2] = {m1, m2};
+    const cplx *vk[2] = {eta, y};
+    cplx *a = (cplx *)calloc(n, sizeof(cplx)), *q = (cplx *)calloc(n, sizeof(cplx));
+    cplx *zt = (cplx *)calloc(n, sizeof(cplx)), *wt = (cplx *)calloc(n, sizeof(cplx));
+    double dm2_acc = 0.0;
+    for (int k = 0; k < 2; k++) {
+        double m = masses[k];
+        apply_dirac(g, 0.0, 0, SEL_WHITE, SEL_BLACK, vk[k], t);          /* E v */
+        if (cgnr_d(g, m, 0, SEL_WHITE, t, a, tol_block, maxiter, &rel) < 0) status = -1;
+        apply_dirac(g, 0.0, 0, SEL_BLACK, SEL_WHITE, a, t);              /* C a */
+        if (cgnr_d(g, m, 0, SEL_BLACK, t, q, tol_block, maxiter, &rel) < 0) status = -1;
+        if (cgnr_d(g, m, 1, SEL_BLACK, z, zt, tol_block, maxiter, &rel) < 0) status = -1;
+        apply_dirac(g, 0.0, 1, SEL_WHITE, SEL_BLACK, zt, t);             /* C^dag zt */
+        if (cgnr_d(g, m, 1, SEL_WHITE, t, wt, tol_block, maxiter, &rel) < 0) status = -1;
+        for (long i = 0; i < n; i++) {
+            Lk[k][0][i] = zt[i];
+            Rk[k][0][i] = q[i] - a[i];
+            Lk[k][1][i] = wt[i];
+            Rk[k][1][i] = a[i] - vk[k][i];
+        }
+        if (k == 1) dm2_acc = -2.0 * (creal(vdot(n, zt, q)) + creal(vdot(n, wt, a)));
+    }
+    if (dm2) *dm2 = dm2_acc;
+    if (dU) {
+        cplx *Lp[4] = {Lk[0][0], Lk[0][1], Lk[1][0], Lk[1][1]};
+        cplx *Rp[4] = {Rk[0][0], Rk[0][1], Rk[1][0], Rk[1][1]};
+        const double cp[4] = {1.0, 1.0, -1.0, -1.0};
+#pragma omp parallel
+        {
+            cplx *w[4];
+            for (int k = 0; k < 4; k++) w[k] = (cplx *)calloc(n, sizeof(cplx));
+#pragma omp for schedule(dynamic, 16)
+            for (long x = 0; x < g->V; x++)
+                for (int mu = 0; mu < 4; mu++)
+                    for (int aa = 0; aa < 8; aa++) {
+                        cplx T[9];
+                        gell_mann_half(aa, T);
+                        cplx s = dD_bilinear(g, x, mu, T, 4, Lp, Rp, cp, w);
+                        dU[((size_t)x * 4 + mu) * 8 + aa] = 2.0 * creal(s);
+                    }
+            for (int k = 0; k < 4; k++) free(w[k]);
+        }
+    }
+    free(y); free(u); free(z); free(t); free(work); free(a); free(q); free(zt); free(wt);
+    for (int k = 0; k < 2; k++)
+        for (int q2 = 0; q2 < 2; q2++) {
+            free(Lk[k][q2]);
+            free(Rk[k][q2]);
+        }
+    return status;
 }

@@ -25,7 +25,7 @@ EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", 
            "ddrw_set_params", "ddrw_set_solver", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
-           "ddrw_autotune", "ddrw_autotune_report"]
+           "ddrw_autotune", "ddrw_autotune_report", "ddrw_force"]
 
 #: kernel classes of ddrw_profile_read
 PROF_DSLASH64, PROF_DSLASH32, PROF_DSLASH64_BLK, PROF_DSLASH32_BLK, PROF_BLOCK64, PROF_BLOCK32, PROF_LAUNCHES = range(7)
@@ -87,6 +87,8 @@ def load(path: str | None = None):
                                       dp, ctypes.POINTER(SolveInfo)]),
         "ddrw_profile": (st, [vp, ctypes.c_int]),
         "ddrw_autotune": (st, [vp, ctypes.c_int]),
+        "ddrw_force": (st, [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp, dp, dp, dp,
+                            ctypes.POINTER(SolveInfo)]),
         "ddrw_autotune_report": (st, [vp, ctypes.c_char_p, ctypes.c_long]),
         "ddrw_solve_block_noalloc": (st, [vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.POINTER(SolveInfo)]),
         "ddrw_profile_read": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_double),
@@ -158,6 +160,7 @@ class Context:
         self._check(self.L.ddrw_load_gauge(self._h, _ptr(U)), "ddrw_load_gauge")
 
     def set_params(self, csw, m1, m2, antiperiodic_t=False):
+        self._csw, self._m1, self._m2 = float(csw), float(m1), float(m2)
         self._check(self.L.ddrw_set_params(self._h, float(csw), float(m1), float(m2), int(antiperiodic_t)),
                     "ddrw_set_params")
 
@@ -219,6 +222,18 @@ class Context:
                                   _ptr(e), _ptr(lw), _ptr(rv), _ptr(delta), ctypes.byref(info))
         self._check(st, "ddrw_estimate")
         return e, float(lw[0]), float(rv[0]), info.as_dict()
+
+    def force(self, nhit, seed=2, hit_offset=0, eta=None, weights=None, dU=None, want_dm2=True):
+        """Exponents, link force sum_j w_j de_j/dU (written into dU, [V,4,8] float64, if given) and
+        de_j/dm2.  Returns (exponents, dm2, solve info)."""
+        e = np.zeros(nhit, dtype=np.float64)
+        dm = np.zeros(nhit, dtype=np.float64) if want_dm2 else None
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+        info = SolveInfo()
+        st = self.L.ddrw_force(self._h, int(nhit), ctypes.c_uint64(seed), ctypes.c_uint64(hit_offset), _ptr(eta),
+                               _ptr(w), _ptr(e), _ptr(dU), _ptr(dm), ctypes.byref(info))
+        self._check(st, "ddrw_force")
+        return e, dm, info.as_dict()
 
     def autotune(self, enable=True):
         self._check(self.L.ddrw_autotune(self._h, int(enable)), "ddrw_autotune")

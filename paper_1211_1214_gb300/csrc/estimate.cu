@@ -287,6 +287,22 @@ static ddrw_status estimate_chunk(ddrw_ctx *ctx, int nmass, const double *m2, in
     return conv;
 }
 
+// The forward chain of the estimate for the force: the noise field (nhit rhs), delta = A(m2)^-1 r
+// and the exponents, for the context's m1 and m2 (copies of the estimate's work fields).
+ddrw_status estimate_fields_for_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64_t hit0, const double *eta_user,
+                                      double2 *eta_out, double2 *delta_out, double *exponents, SolveStats &stats)
+{
+    ddrw_status st = estimate_chunk(ctx, 1, &ctx->m2, nhit, seed, hit0, eta_user, exponents, nullptr, stats);
+    if (st && st != DDRW_ENOCONV) return st;
+    double2 *F[5];
+    ddrw_status s2 = fields(ctx, "est_f", 5, nhit, F);
+    if (s2) return s2;
+    const size_t fb = sizeof(double2) * 12 * ctx->V * nhit;
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(eta_out, F[0], fb, cudaMemcpyDeviceToDevice, ctx->stream));
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(delta_out, F[2], fb, cudaMemcpyDeviceToDevice, ctx->stream));
+    return st;
+}
+
 // right-hand sides that fit the free device memory (about 3 KB per site and right-hand side of
 // FP64/FP32 fields in the estimate, the block solves and the outer solve), at most 64
 static int rhs_budget(ddrw_ctx *ctx)

@@ -71,19 +71,22 @@ def _expm_i_traceless_hermitian(Q: np.ndarray) -> np.ndarray:
     c0 = np.real(a[:, 0] * (b[:, 1] * c[:, 2] - b[:, 2] * c[:, 1]) - a[:, 1] * (b[:, 0] * c[:, 2] - b[:, 2] * c[:, 0])
                  + a[:, 2] * (b[:, 0] * c[:, 1] - b[:, 1] * c[:, 0]))
     c1s = np.maximum(c1, 1e-300)
-    arg = np.clip(0.5 * c0 * (3.0 / c1s) ** 1.5, -1.0, 1.0)
+    with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
+        arg = np.clip(0.5 * c0 * (3.0 / c1s) ** 1.5, -1.0, 1.0)
     phi = np.arccos(arg) / 3.0
     rad = 2.0 * np.sqrt(c1s / 3.0)
     lam = np.stack([rad * np.cos(phi - 2.0 * np.pi * k / 3.0) for k in range(3)], axis=-1)
     l0, l1, l2 = lam[:, 0], lam[:, 1], lam[:, 2]
     d = np.stack([(l0 - l1) * (l0 - l2), (l1 - l0) * (l1 - l2), (l2 - l0) * (l2 - l1)], axis=-1)
     e = np.exp(1j * lam)
-    w = e / np.where(np.abs(d) > 0, d, 1.0)
+    with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
+        w = e / np.where(np.abs(d) > 0, d, 1.0)
     A = w.sum(-1)
     B = (w * lam).sum(-1)
     C = w[:, 0] * l1 * l2 + w[:, 1] * l0 * l2 + w[:, 2] * l0 * l1
     out = A[:, None, None] * Q2 + B[:, None, None] * Q + C[:, None, None] * np.eye(3)
-    bad = np.abs(d).min(axis=-1) < 1e-6 * np.maximum(c1, 1e-30)
+    # nearly degenerate spectra (and Q = 0, where the trigonometric solution is 0/0) take the series
+    bad = ~(np.abs(d).min(axis=-1) >= 1e-6 * np.maximum(c1, 1e-30)) | ~np.isfinite(out).all(axis=(-2, -1))
     if np.any(bad):
         out[bad] = _expm_batch(1j * Q[bad])
     return out
