@@ -311,7 +311,8 @@ def main():
                       "block_iters_max": infos[-1]["block_iters_max"],
                       "true_rel_residual": infos[-1]["true_rel_residual"]},
            "logW": [float(x) for x in LW], "wall_s_timed": wall,
-           "autotune": ctx.autotune_report().strip().splitlines()}
+           "autotune": ctx.autotune_report().strip().splitlines(),
+           "graph_launches_total": ctx.use_graphs()}
 
     # ---- end to end through the public API with host buffers: per step the gauge configuration
     # is copied from pinned host memory, the clover term and inverses rebuilt, the estimate run and

@@ -183,6 +183,12 @@ ddrw_status ddrw_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64_t hit_offs
 ddrw_status ddrw_solve_block_noalloc(ddrw_ctx *ctx, int colour, double m, const double *b, double *x,
                                      ddrw_solve_info *info);
 
+/* CUDA graphs of the outer Krylov loop (default on): after its first iterations the loop runs as
+ * one graph with a conditional while-node (device-side convergence test, iteration cap).
+ * enable = 1 / 0 switches them, -1 leaves the setting; *graph_launches (optional) receives the
+ * number of graph launches so far.  Block solves are single persistent launches either way. */
+ddrw_status ddrw_use_graphs(ddrw_ctx *ctx, int enable, long *graph_launches);
+
 /* Autotuner of the stencil launches: on the first launch of each shape (precision, block length,
  * parities, right-hand sides, diagonal/post modes) it times right-hand sides per thread {1,2,4}
  * and CTA sizes {64,128,256} with CUDA events and keeps the fastest.  enable = 0 uses a fixed

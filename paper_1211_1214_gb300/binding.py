@@ -25,7 +25,7 @@ EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", 
            "ddrw_set_params", "ddrw_set_solver", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
-           "ddrw_autotune", "ddrw_autotune_report", "ddrw_force"]
+           "ddrw_autotune", "ddrw_autotune_report", "ddrw_force", "ddrw_use_graphs"]
 
 #: kernel classes of ddrw_profile_read
 PROF_DSLASH64, PROF_DSLASH32, PROF_DSLASH64_BLK, PROF_DSLASH32_BLK, PROF_BLOCK64, PROF_BLOCK32, PROF_LAUNCHES = range(7)
@@ -87,6 +87,7 @@ def load(path: str | None = None):
                                       dp, ctypes.POINTER(SolveInfo)]),
         "ddrw_profile": (st, [vp, ctypes.c_int]),
         "ddrw_autotune": (st, [vp, ctypes.c_int]),
+        "ddrw_use_graphs": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long)]),
         "ddrw_force": (st, [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp, dp, dp, dp,
                             ctypes.POINTER(SolveInfo)]),
         "ddrw_autotune_report": (st, [vp, ctypes.c_char_p, ctypes.c_long]),
@@ -234,6 +235,13 @@ class Context:
                                _ptr(w), _ptr(e), _ptr(dU), _ptr(dm), ctypes.byref(info))
         self._check(st, "ddrw_force")
         return e, dm, info.as_dict()
+
+    def use_graphs(self, enable=None):
+        """Switch CUDA graphs of the outer Krylov loop (None: keep); returns graph launches so far."""
+        n = ctypes.c_long()
+        self._check(self.L.ddrw_use_graphs(self._h, -1 if enable is None else int(enable), ctypes.byref(n)),
+                    "ddrw_use_graphs")
+        return n.value
 
     def autotune(self, enable=True):
         self._check(self.L.ddrw_autotune(self._h, int(enable)), "ddrw_autotune")

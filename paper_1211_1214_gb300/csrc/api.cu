@@ -192,6 +192,10 @@ static cudaEvent_t pool_event(ddrw_ctx *ctx)
 ProfScope::ProfScope(ddrw_ctx *c, int k, double b) : ctx(c), kind(k), bytes(b)
 {
     if (!ctx->prof_on) return;
+    // launches captured into a graph are not timed (graph bodies hold no event nodes)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(ctx->stream, &cs);
+    if (cs != cudaStreamCaptureStatusNone) return;
     a = pool_event(ctx);
     cudaEventRecord(a, ctx->stream);
 }
@@ -237,6 +241,14 @@ ddrw_status ddrw_profile(ddrw_ctx *ctx, int enable)
     }
     ctx->prof_on = enable != 0;
     ctx->launches = 0;
+    return DDRW_OK;
+}
+
+ddrw_status ddrw_use_graphs(ddrw_ctx *ctx, int enable, long *graph_launches)
+{
+    if (!ctx) return DDRW_EINVAL;
+    if (enable >= 0) ctx->use_graphs = enable != 0;
+    if (graph_launches) *graph_launches = ctx->graph_launches;
     return DDRW_OK;
 }
 
@@ -386,6 +398,10 @@ void ddrw_destroy(ddrw_ctx *ctx)
     for (auto &r : ctx->prof_pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
+    }
+    for (auto &kv : ctx->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaGraphDestroy(kv.second.graph);
     }
     for (auto e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);

@@ -27,6 +27,12 @@ struct MassInv {
     float4 *A32 = nullptr;   // [2][9][V]
 };
 
+// an instantiated Krylov-loop graph (solver.cu)
+struct GraphEntry {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
 // a tuned stencil launch configuration
 struct TuneEntry {
     int nr, nt;
@@ -89,6 +95,11 @@ struct ddrw_ctx {
     std::map<std::string, ddrw::DevBuf> ws;
     double *h_pinned = nullptr;  // small pinned host buffer for scalars
     size_t h_pinned_bytes = 0;
+
+    // CUDA graphs of the outer Krylov loop, by launch shape and buffers
+    bool use_graphs = true;
+    long graph_launches = 0;
+    std::map<std::array<uintptr_t, 24>, ddrw::GraphEntry> graphs;
 
     // stencil autotuner (dslash_tune.cu)
     bool autotune = true;

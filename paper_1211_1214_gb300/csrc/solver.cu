@@ -6,11 +6,16 @@
 //   Krylov method:       BiCGStab on Mhat x_e = btil_e, all right-hand sides in lockstep with their
 //                        own scalars (device resident); a right-hand side that has converged stops
 //                        updating while the others continue.
+//   graphs:              after the first iterations (which tune the launches) the rest of the loop
+//                        is one CUDA graph: a conditional while-node whose condition kernel stops on
+//                        convergence of every right-hand side or at the iteration cap.
 //   precision:           FP64 defect correction around the inner solve:
 //                        r = b - D x (FP64 stencil), inner solve D e = r / ||r|| in FP64 (FP64 path)
 //                        or FP32 (mixed path), x += ||r|| e, until ||b - D x|| <= tol ||b||.
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "blas.cuh"
@@ -32,10 +37,15 @@ ddrw_status make_massset(ddrw_ctx *ctx, int n, const double *m, MassSet *ms)
 
 namespace {
 
-template <class P> struct EoSpace {
-    using E = typename P::SElem;
-    E *r, *rh, *p, *v, *t, *tmp;
-};
+// sets the while-condition of the captured Krylov loop: continue while any right-hand side is
+// active and the iteration cap is not reached (the cap bounds every device-side loop)
+__global__ void k_bicg_cond(cudaGraphConditionalHandle h, const KScal *sc, int nrhs, int *count, int step, int maxiter)
+{
+    int act = 0;
+    for (int r = 0; r < nrhs; r++) act |= sc[r].active;
+    int it = (*count += step);
+    cudaGraphSetConditional(h, (act && it < maxiter) ? 1u : 0u);
+}
 
 template <class P> void stencil(ddrw_ctx *ctx, const DslashCall &c)
 {
@@ -135,23 +145,105 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
 
     KScal *hs = (KScal *)ctx->h_pinned;
     const int check = sizeof(typename P::R) == 8 ? 1 : 4;
+    auto iteration = [&]() -> ddrw_status {
+        ddrw_status s2;
+        apply_mhat<P>(ctx, ms, nrhs, rs, p, tmp, v);
+        if ((s2 = Blas<P>::bicg_alpha(ctx, ev, rh, v, sc))) return s2;
+        Blas<P>::bicg_s(ctx, ev, r, v, sc);
+        apply_mhat<P>(ctx, ms, nrhs, rs, r, tmp, t);
+        if ((s2 = Blas<P>::bicg_omega(ctx, ev, t, r, sc))) return s2;
+        if ((s2 = Blas<P>::bicg_xr(ctx, ev, x, p, r, t, rh, sc))) return s2;
+        Blas<P>::bicg_p(ctx, ev, p, r, v, sc);
+        return DDRW_OK;
+    };
     int it = 0;
-    for (;;) {
-        for (int k = 0; k < check; k++) {
-            apply_mhat<P>(ctx, ms, nrhs, rs, p, tmp, v);
-            if ((st = Blas<P>::bicg_alpha(ctx, ev, rh, v, sc))) return st;
-            Blas<P>::bicg_s(ctx, ev, r, v, sc);
-            apply_mhat<P>(ctx, ms, nrhs, rs, r, tmp, t);
-            if ((st = Blas<P>::bicg_omega(ctx, ev, t, r, sc))) return st;
-            if ((st = Blas<P>::bicg_xr(ctx, ev, x, p, r, t, rh, sc))) return st;
-            Blas<P>::bicg_p(ctx, ev, p, r, v, sc);
-            it++;
-        }
-        DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, sc, sizeof(KScal) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-        DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    bool done = false;
+    // first iterations eagerly: they tune the stencil launches and create every workspace
+    for (int k = 0; k < check; k++, it++)
+        if ((st = iteration())) return st;
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, sc, sizeof(KScal) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    {
         int active = 0;
         for (int k = 0; k < nrhs; k++) active += hs[k].active;
-        if (!active || it >= maxiter) break;
+        done = !active || it >= maxiter;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(ctx->stream, &cs);
+    if (!done && ctx->use_graphs && cs == cudaStreamCaptureStatusNone) {
+        // the rest of the loop as one CUDA graph: a conditional while-node around `check`
+        // iterations and the condition kernel; no host round trip until convergence or the cap
+        int *count;
+        if ((st = workspace(ctx, "eo_graph_count", sizeof(int), (void **)&count))) return st;
+        std::array<uintptr_t, 24> key{};
+        key[0] = sizeof(typename P::R);
+        key[1] = (uintptr_t)nrhs;
+        key[2] = (uintptr_t)maxiter;
+        const void *ptrs[9] = {r, rh, p, v, t, tmp, x, sc, count};
+        for (int k = 0; k < 9; k++) key[3 + k] = (uintptr_t)ptrs[k];
+        key[12] = (uintptr_t)ms.n;
+        for (int k = 0; k < ms.n && k < 5; k++) {
+            double mk = ms.m[k];
+            memcpy(&key[13 + 2 * k], &mk, sizeof(double));
+            key[14 + 2 * k] = (uintptr_t)ms.inv[k];
+        }
+        auto git = ctx->graphs.find(key);
+        cudaGraphExec_t exec = nullptr;
+        if (git != ctx->graphs.end()) {
+            exec = git->second.exec;
+        } else {
+            cudaGraph_t graph = nullptr;
+            DDRW_CUDA_CHECK(cudaGraphCreate(&graph, 0));
+            cudaGraphConditionalHandle handle;
+            DDRW_CUDA_CHECK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = handle;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node;
+            DDRW_CUDA_CHECK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            DDRW_CUDA_CHECK(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0,
+                                                          cudaStreamCaptureModeThreadLocal));
+            ddrw_status cap = DDRW_OK;
+            for (int k = 0; k < check && !cap; k++) cap = iteration();
+            ++ctx->launches;
+            k_bicg_cond<<<1, 1, 0, ctx->stream>>>(handle, sc, nrhs, count, check, maxiter);
+            cudaGraph_t captured = nullptr;
+            cudaError_t ec = cudaStreamEndCapture(ctx->stream, &captured);
+            if (cap || ec != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                if (cap) return cap;
+                return set_cuda_error(ctx, ec, "cudaStreamEndCapture", __FILE__, __LINE__);
+            }
+            cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+            if (ei != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return set_cuda_error(ctx, ei, "cudaGraphInstantiate", __FILE__, __LINE__);
+            }
+            ctx->graphs[key] = GraphEntry{graph, exec};
+        }
+        const int it0 = it;
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(count, &it, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+        DDRW_CUDA_CHECK(cudaGraphLaunch(exec, ctx->stream));
+        ++ctx->graph_launches;
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(&it, count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, sc, sizeof(KScal) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+        DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        // kernels the graph ran: 9 per iteration (4 stencil sweeps, 5 vector kernels) and one
+        // condition kernel per `check` iterations
+        ctx->launches += (long)(it - it0) * 9 + (it - it0) / check;
+    } else {
+        while (!done) {
+            for (int k = 0; k < check; k++, it++)
+                if ((st = iteration())) return st;
+            DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, sc, sizeof(KScal) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+            DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+            int active = 0;
+            for (int k = 0; k < nrhs; k++) active += hs[k].active;
+            done = !active || it >= maxiter;
+        }
     }
     int itmax = 0;
     for (int k = 0; k < nrhs; k++) itmax = std::max(itmax, hs[k].iters);

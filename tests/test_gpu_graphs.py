@@ -1,0 +1,63 @@
+"""CUDA graphs of the outer Krylov loop and the stencil autotuner: same results with and without
+them, and the graph path is actually taken."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1211_1214_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    dims, l = (16, 16, 16, 16), 4
+    c = binding.Context(dims, (l,) * 4)
+    c.load_gauge(torch.from_numpy(synth.gauge_field(dims, 0.25, seed=1)).cuda())
+    c.set_params(1.5, 0.05, 0.045)
+    yield c, dims
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [binding.MIXED_FP32, binding.FP64])
+def test_graph_and_eager_krylov_loops_agree(ctx, prec):
+    c, dims = ctx
+    c.set_solver(prec, tol_outer=1e-10, tol_block=1e-12)
+    b = torch.from_numpy(synth.spinor_field(dims, seed=61, nrhs=3)).cuda()
+    xs = []
+    for graphs in (False, True):
+        c.use_graphs(graphs)
+        n0 = c.use_graphs()
+        x = torch.zeros_like(b)
+        info = c.solve_D(0.045, b, x, nrhs=3)
+        assert info["true_rel_residual"] <= 1e-10
+        xs.append(x.cpu().numpy())
+        if graphs:
+            assert c.use_graphs() > n0  # the loop ran as a graph
+    assert np.array_equal(xs[0], xs[1])
+    c.use_graphs(True)
+
+
+def test_estimate_same_with_graphs_and_without(ctx):
+    c, dims = ctx
+    c.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-12)
+    c.use_graphs(False)
+    e0, lw0, _, _ = c.estimate(4, seed=3)
+    c.use_graphs(True)
+    e1, lw1, _, _ = c.estimate(4, seed=3)
+    assert np.array_equal(e0, e1)
+
+
+def test_autotuner_off_gives_the_same_numbers(ctx):
+    c, dims = ctx
+    c.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-12)
+    c.autotune(True)
+    e0, _, _, _ = c.estimate(2, seed=4)
+    report = c.autotune_report()
+    assert "nr=" in report
+    c.autotune(False)
+    e1, _, _, _ = c.estimate(2, seed=4)
+    c.autotune(True)
+    # a different launch shape changes only the order of nothing: each site's arithmetic is the same
+    assert np.allclose(e0, e1, rtol=1e-9)
