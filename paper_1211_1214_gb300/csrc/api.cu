@@ -21,10 +21,24 @@ ddrw_status set_cuda_error(ddrw_ctx *ctx, cudaError_t e, const char *what, const
     return set_error(ctx, e == cudaErrorMemoryAllocation ? DDRW_ENOMEM : DDRW_ECUDA, buf);
 }
 
+// Captured Krylov-loop graphs hold raw device pointers (workspaces, reduction buffers, inverses):
+// every graph is destroyed before any such buffer is freed or moved.
+void clear_graphs(ddrw_ctx *ctx)
+{
+    if (ctx->graphs.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaGraphDestroy(kv.second.graph);
+    }
+    ctx->graphs.clear();
+}
+
 ddrw_status workspace(ddrw_ctx *ctx, const char *name, size_t bytes, void **out)
 {
     DevBuf &b = ctx->ws[name];
     if (b.bytes < bytes) {
+        clear_graphs(ctx);
         if (b.p) cudaFree(b.p);
         b.p = nullptr;
         b.bytes = 0;
@@ -81,6 +95,7 @@ ddrw_status mass_inverse(ddrw_ctx *ctx, double m, MassInv **out)
 
 static void free_inverses(ddrw_ctx *ctx)
 {
+    clear_graphs(ctx);
     for (auto &mi : ctx->inv) {
         cudaFree(mi.A64);
         cudaFree(mi.A32);
@@ -399,10 +414,7 @@ void ddrw_destroy(ddrw_ctx *ctx)
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
-    for (auto &kv : ctx->graphs) {
-        cudaGraphExecDestroy(kv.second.exec);
-        cudaGraphDestroy(kv.second.graph);
-    }
+    clear_graphs(ctx);
     for (auto e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -452,6 +464,7 @@ ddrw_status ddrw_load_gauge(ddrw_ctx *ctx, const double *U)
     // the staging buffer for the gauge field is large and used once: release it
     auto it = ctx->ws.find("stage_gauge");
     if (it != ctx->ws.end()) {
+        clear_graphs(ctx);
         cudaStreamSynchronize(ctx->stream);
         cudaFree(it->second.p);
         ctx->ws.erase(it);

@@ -429,6 +429,7 @@ ddrw_status reduce_ws(ddrw_ctx *ctx, int nrhs, double **part, unsigned **ticket)
     *part = (double *)p;
     DevBuf &t = ctx->ws["red_ticket"];
     if (t.bytes < sizeof(unsigned) * (size_t)nrhs) {
+        clear_graphs(ctx);
         if (t.p) cudaFree(t.p);
         t.p = nullptr;
         t.bytes = 0;

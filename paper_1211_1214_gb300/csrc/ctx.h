@@ -147,6 +147,9 @@ struct ProfScope {
 ddrw_status set_error(ddrw_ctx *ctx, ddrw_status st, const std::string &msg);
 ddrw_status set_cuda_error(ddrw_ctx *ctx, cudaError_t e, const char *what, const char *file, int line);
 
+// destroy the captured Krylov-loop graphs (before any buffer they reference is freed or moved)
+void clear_graphs(ddrw_ctx *ctx);
+
 // device workspace of at least `bytes`, reused across calls under `name`
 ddrw_status workspace(ddrw_ctx *ctx, const char *name, size_t bytes, void **out);
 

@@ -182,11 +182,13 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
         const void *ptrs[9] = {r, rh, p, v, t, tmp, x, sc, count};
         for (int k = 0; k < 9; k++) key[3 + k] = (uintptr_t)ptrs[k];
         key[12] = (uintptr_t)ms.n;
+        // masses and the device arrays of their inverses are baked into the captured launches
         for (int k = 0; k < ms.n && k < 5; k++) {
             double mk = ms.m[k];
             memcpy(&key[13 + 2 * k], &mk, sizeof(double));
-            key[14 + 2 * k] = (uintptr_t)ms.inv[k];
+            key[14 + 2 * k] = sizeof(typename P::R) == 8 ? (uintptr_t)ms.inv[k]->A64 : (uintptr_t)ms.inv[k]->A32;
         }
+        if (ms.n > 5) return set_error(ctx, DDRW_EINVAL, "graph key holds up to 5 masses");
         auto git = ctx->graphs.find(key);
         cudaGraphExec_t exec = nullptr;
         if (git != ctx->graphs.end()) {
