@@ -151,6 +151,21 @@ ddrw_status ddrw_estimate_masses(ddrw_ctx *ctx, int nmass, const double *m2, int
                                  uint64_t hit_offset, double *exponents, double *logW, double *rel_var,
                                  ddrw_solve_info *info);
 
+/* Mass interpolation (Eq. 8) with the one-flavour estimator (Eq. 11) and the root trick.
+ * m_i = (i/N) m2 + ((N-i)/N) m1 for i = 0..N; factor i uses Mh_i = A(m_i)^-1 A(m_{i-1}) and its own
+ * noise vectors eta_{i,j} (Philox hits hit_offset + (i-1) nhit + j).  All N factors run as mass
+ * slots of one batched pass when they fit the device memory.  Outputs (each optional):
+ *   exponents[N][nhit]       e_ij = eta^dag (Mh_i^dag Mh_i - 1) eta            (two flavours, Eq. 8)
+ *   exponents_1f[N][nhit][2] eta^dag (Mh_i - 1) eta = <eta, delta>, complex  (one flavour, Eq. 11)
+ *   logW[4]                  log W_gl = sum_i log((1/N_hit) sum_j exp(-e_ij)); log |W_1f| with
+ *                            W_1f = prod_i Re((1/N_hit) sum_j exp(-e1_ij)); sign of W_1f; and the
+ *                            root trick log sqrt(W_gl) = logW[0] / 2
+ *   logW_factors[N], rel_var[N]  per factor: log of its two-flavour estimate, sample variance / mean^2.
+ * 1 <= N <= 8. */
+ddrw_status ddrw_estimate_interp(ddrw_ctx *ctx, int N, int nhit, uint64_t seed, uint64_t hit_offset, double *exponents,
+                                 double *exponents_1f, double *logW, double *logW_factors, double *rel_var,
+                                 ddrw_solve_info *info);
+
 /* The adjoint of the estimate: for each of nhit noise vectors (as in ddrw_estimate) the exponent
  * e_j, its derivative with respect to every link and with respect to m2 (m1 fixed), by reverse
  * mode through the Schur complement (recomputing the solutions, not storing Krylov iterates):

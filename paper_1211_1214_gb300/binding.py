@@ -25,7 +25,8 @@ EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", 
            "ddrw_set_params", "ddrw_set_solver", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
-           "ddrw_autotune", "ddrw_autotune_report", "ddrw_force", "ddrw_use_graphs"]
+           "ddrw_autotune", "ddrw_autotune_report", "ddrw_force", "ddrw_use_graphs",
+           "ddrw_estimate_interp"]
 
 #: kernel classes of ddrw_profile_read
 PROF_DSLASH64, PROF_DSLASH32, PROF_DSLASH64_BLK, PROF_DSLASH32_BLK, PROF_BLOCK64, PROF_BLOCK32, PROF_LAUNCHES = range(7)
@@ -88,6 +89,8 @@ def load(path: str | None = None):
         "ddrw_profile": (st, [vp, ctypes.c_int]),
         "ddrw_autotune": (st, [vp, ctypes.c_int]),
         "ddrw_use_graphs": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long)]),
+        "ddrw_estimate_interp": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp, dp, dp,
+                                      dp, ctypes.POINTER(SolveInfo)]),
         "ddrw_force": (st, [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp, dp, dp, dp,
                             ctypes.POINTER(SolveInfo)]),
         "ddrw_autotune_report": (st, [vp, ctypes.c_char_p, ctypes.c_long]),
@@ -260,6 +263,22 @@ class Context:
         self._check(self.L.ddrw_profile_read(self._h, int(kind), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)),
                     "ddrw_profile_read")
         return n.value, ms.value, b.value
+
+    def estimate_interp(self, N, nhit, seed=2, hit_offset=0):
+        """Mass interpolation in N steps (Eq. 8) with the one-flavour estimator (Eq. 11).  Returns a
+        dict: exponents [N, nhit], exponents_1f [N, nhit] complex, logW (two flavours), logW_1f,
+        sign_1f, logW_root, logW_factors [N], rel_var [N], info."""
+        e = np.zeros((N, nhit), dtype=np.float64)
+        e1 = np.zeros((N, nhit, 2), dtype=np.float64)
+        lw = np.zeros(4, dtype=np.float64)
+        lf = np.zeros(N, dtype=np.float64)
+        rv = np.zeros(N, dtype=np.float64)
+        info = SolveInfo()
+        st = self.L.ddrw_estimate_interp(self._h, int(N), int(nhit), ctypes.c_uint64(seed), ctypes.c_uint64(hit_offset),
+                                         _ptr(e), _ptr(e1), _ptr(lw), _ptr(lf), _ptr(rv), ctypes.byref(info))
+        self._check(st, "ddrw_estimate_interp")
+        return {"exponents": e, "exponents_1f": e1[..., 0] + 1j * e1[..., 1], "logW": lw[0], "logW_1f": lw[1],
+                "sign_1f": lw[2], "logW_root": lw[3], "logW_factors": lf, "rel_var": rv, "info": info.as_dict()}
 
     def estimate_masses(self, m2s, nhit, seed=2, hit_offset=0):
         """Batched estimate for several target masses: (exponents [nmass, nhit], logW [nmass],

@@ -333,7 +333,8 @@ __global__ void __launch_bounds__(NT) k_norm2(VecArgs<P> va, const typename P::S
     if (grid_sum<1, NT>(v, part, ticket)) out[blockIdx.y] = v[0];
 }
 
-// out[r] = (sum |a|^2, Re sum conj(a) b) -- used by the exponent ||delta||^2 + 2 Re <eta, delta>
+// out[3r .. 3r+2] = (sum |d|^2, Re sum conj(d) e, Im sum conj(d) e) -- the exponents
+// ||delta||^2 + 2 Re <eta, delta> and <eta, delta>
 template <class P>
 __global__ void __launch_bounds__(NT) k_norm_dot(VecArgs<P> va, const typename P::SElem *d,
                                                  const typename P::SElem *e, double *out, double *part,
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(NT) k_norm_dot(VecArgs<P> va, const typename P
     using L = El<E>;
     using R = typename L::R;
     const long ro = (long)blockIdx.y * va.rs + va.off;
-    R nn = 0, dr = 0;
+    R nn = 0, dr = 0, di = 0;
     for (long j = (long)blockIdx.x * NT + threadIdx.x; j < va.n; j += (long)gridDim.x * NT)
         for (int k = 0; k < P::SPLANES; k++) {
             cpx<R> c[L::NC], f[L::NC];
@@ -353,12 +354,14 @@ __global__ void __launch_bounds__(NT) k_norm_dot(VecArgs<P> va, const typename P
             for (int q = 0; q < L::NC; q++) {
                 nn += c[q].re * c[q].re + c[q].im * c[q].im;
                 dr += c[q].re * f[q].re + c[q].im * f[q].im;
+                di += c[q].re * f[q].im - c[q].im * f[q].re;
             }
         }
-    double v[2] = {(double)nn, (double)dr};
-    if (grid_sum<2, NT>(v, part, ticket)) {
-        out[2 * blockIdx.y] = v[0];
-        out[2 * blockIdx.y + 1] = v[1];
+    double v[3] = {(double)nn, (double)dr, (double)di};
+    if (grid_sum<3, NT>(v, part, ticket)) {
+        out[3 * blockIdx.y] = v[0];
+        out[3 * blockIdx.y + 1] = v[1];
+        out[3 * blockIdx.y + 2] = v[2];
     }
 }
 

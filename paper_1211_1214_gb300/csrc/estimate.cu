@@ -192,7 +192,7 @@ static ddrw_status apply_dA_fields(ddrw_ctx *ctx, const MassSet &m2s, const Mass
     double *dm;
     if ((st = workspace(ctx, "est_dm", sizeof(double) * MAXM, (void **)&dm))) return st;
     double hdm[MAXM];
-    for (int k = 0; k < MAXM; k++) hdm[k] = k < m2s.n ? m1s.m[0] - m2s.m[k] : 0.0;
+    for (int k = 0; k < MAXM; k++) hdm[k] = k < m2s.n ? m1s.m[k < m1s.n ? k : 0] - m2s.m[k] : 0.0;
     DDRW_CUDA_CHECK(cudaMemcpyAsync(dm, hdm, sizeof(hdm), cudaMemcpyHostToDevice, ctx->stream));
     GeomDev g = geom_dev(ctx);
     int rpm = (nrhs + m2s.n - 1) / m2s.n;
@@ -231,14 +231,20 @@ static ddrw_status fields(ddrw_ctx *ctx, const char *prefix, int n, int nrhs, do
 // One chunk of the estimate: nmass target masses x nhit noise vectors as nrhs = nmass * nhit
 // right-hand sides; writes the FP64 exponents e[k * nhit + j].  eta_user (packed, nhit vectors)
 // or the Philox noise of hits hit0 .. hit0 + nhit - 1.
-static ddrw_status estimate_chunk(ddrw_ctx *ctx, int nmass, const double *m2, int nhit, uint64_t seed, uint64_t hit0,
-                                  const double *eta_user, double *exponents, double *delta_user, SolveStats &stats)
+//
+// Slot k pairs the masses (ma[k], mb[k]): Mh = A(mb)^-1 A(ma) (the sweep uses ma = m1 for every slot,
+// the mass interpolation of Eq. 8 ma = m_{i-1}, mb = m_i).  With distinct_noise every slot draws its
+// own noise vectors (hits hit0 + k * nhit + j), else all slots share hits hit0 + j.  e1 (optional,
+// 2 doubles per rhs) receives the one-flavour exponent eta^dag (Mh - 1) eta = <eta, delta> (Eq. 11).
+static ddrw_status estimate_chunk(ddrw_ctx *ctx, int nmass, const double *ma, const double *m2, int nhit,
+                                  uint64_t seed, uint64_t hit0, bool distinct_noise, const double *eta_user,
+                                  double *exponents, double *e1, double *delta_user, SolveStats &stats)
 {
     const int nrhs = nmass * nhit;
     MassSet m2s, m1s;
     ddrw_status st;
     if ((st = make_massset(ctx, nmass, m2, &m2s))) return st;
-    if ((st = make_massset(ctx, 1, &ctx->m1, &m1s))) return st;
+    if ((st = make_massset(ctx, nmass, ma, &m1s))) return st;
     double2 *F[5];
     if ((st = fields(ctx, "est_f", 5, nrhs, F))) return st;
     double2 *eta = F[0], *r = F[1], *delta = F[2];
@@ -254,7 +260,8 @@ static ddrw_status estimate_chunk(ddrw_ctx *ctx, int nmass, const double *m2, in
         if (nmass > 1) k_replicate<<<(unsigned)((n * nhit + 255) / 256), 256, 0, ctx->stream>>>(n, nhit, nmass, eta);
     } else {
         DDRW_CUDA_CHECK(cudaMemsetAsync(eta, 0, sizeof(double2) * 12 * ctx->V * nrhs, ctx->stream));
-        noise_launch(ctx, seed, hit0, nhit, nmass, eta, nullptr);
+        if (distinct_noise) noise_launch(ctx, seed, hit0, nrhs, 1, eta, nullptr);
+        else noise_launch(ctx, seed, hit0, nhit, nmass, eta, nullptr);
     }
     ddrw_status conv = DDRW_OK;
     if ((st = apply_dA_fields(ctx, m2s, m1s, eta, r, work, nrhs, &stats))) return st;
@@ -264,14 +271,14 @@ static ddrw_status estimate_chunk(ddrw_ctx *ctx, int nmass, const double *m2, in
     else if (st) return st;
     // e = ||delta||^2 + 2 Re <eta, delta> over the black sites
     double *red;
-    if ((st = workspace(ctx, "est_red", sizeof(double) * 4 * nrhs, (void **)&red))) return st;
+    if ((st = workspace(ctx, "est_red", sizeof(double) * 6 * nrhs, (void **)&red))) return st;
     long vbh = (long)ctx->l * ctx->l * ctx->l * ctx->l / 2, nc = (long)ctx->nblk_c * vbh;
     for (int p = 0; p < 2; p++)
         if ((st = Blas<PrecD>::norm_dot(ctx, VecRange{ctx->V, p * ctx->vh, nc, 12 * ctx->V, nrhs}, delta, eta,
-                                        red + 2 * p * nrhs)))
+                                        red + 3 * p * nrhs)))
             return st;
-    std::vector<double> h(4 * nrhs);
-    DDRW_CUDA_CHECK(cudaMemcpyAsync(h.data(), red, sizeof(double) * 4 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<double> h(6 * nrhs);
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(h.data(), red, sizeof(double) * 6 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
     if (delta_user) {
         void *dd;
         bool host;
@@ -281,8 +288,14 @@ static ddrw_status estimate_chunk(ddrw_ctx *ctx, int nmass, const double *m2, in
     }
     if ((st = sync(ctx))) return st;
     for (int rr = 0; rr < nrhs; rr++) {
-        double nn = h[2 * rr] + h[2 * nrhs + 2 * rr], dr = h[2 * rr + 1] + h[2 * nrhs + 2 * rr + 1];
+        // h: |delta|^2, Re sum conj(delta) eta, Im sum conj(delta) eta (two parities)
+        double nn = h[3 * rr] + h[3 * nrhs + 3 * rr], dr = h[3 * rr + 1] + h[3 * nrhs + 3 * rr + 1];
+        double di = h[3 * rr + 2] + h[3 * nrhs + 3 * rr + 2];
         exponents[rr] = nn + 2.0 * dr;
+        if (e1) {  // <eta, delta> = conj(sum conj(delta) eta)
+            e1[2 * rr] = dr;
+            e1[2 * rr + 1] = -di;
+        }
     }
     return conv;
 }
@@ -292,7 +305,8 @@ static ddrw_status estimate_chunk(ddrw_ctx *ctx, int nmass, const double *m2, in
 ddrw_status estimate_fields_for_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64_t hit0, const double *eta_user,
                                       double2 *eta_out, double2 *delta_out, double *exponents, SolveStats &stats)
 {
-    ddrw_status st = estimate_chunk(ctx, 1, &ctx->m2, nhit, seed, hit0, eta_user, exponents, nullptr, stats);
+    ddrw_status st = estimate_chunk(ctx, 1, &ctx->m1, &ctx->m2, nhit, seed, hit0, false, eta_user, exponents, nullptr,
+                                    nullptr, stats);
     if (st && st != DDRW_ENOCONV) return st;
     double2 *F[5];
     ddrw_status s2 = fields(ctx, "est_f", 5, nhit, F);
@@ -333,7 +347,9 @@ ddrw_status estimate_multi(ddrw_ctx *ctx, int nmass, const double *m2, int nhit,
         // the caller's vectors go through in one chunk
         if (nmass * nhit > budget)
             return set_error(ctx, DDRW_ENOMEM, "caller-supplied noise or delta for more right-hand sides than fit");
-        st = estimate_chunk(ctx, nmass, m2, nhit, seed, hit0, eta_user, eall.data(), delta_user, stats);
+        std::vector<double> ma(nmass, ctx->m1);
+        st = estimate_chunk(ctx, nmass, ma.data(), m2, nhit, seed, hit0, false, eta_user, eall.data(), nullptr,
+                            delta_user, stats);
         if (st == DDRW_ENOCONV) conv = st;
         else if (st) return st;
     } else {
@@ -345,7 +361,9 @@ ddrw_status estimate_multi(ddrw_ctx *ctx, int nmass, const double *m2, int nhit,
             for (int j0 = 0; j0 < nhit; j0 += hper) {
                 const int jn = std::min(hper, nhit - j0);
                 std::vector<double> ec((size_t)km * jn);
-                st = estimate_chunk(ctx, km, m2 + k0, jn, seed, hit0 + j0, nullptr, ec.data(), nullptr, stats);
+                std::vector<double> ma(km, ctx->m1);
+                st = estimate_chunk(ctx, km, ma.data(), m2 + k0, jn, seed, hit0 + j0, false, nullptr, ec.data(),
+                                    nullptr, nullptr, stats);
                 if (st == DDRW_ENOCONV) conv = st;
                 else if (st) return st;
                 for (int k = 0; k < km; k++)
@@ -406,6 +424,96 @@ ddrw_status ddrw_estimate(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64_t hit_o
     if (!ctx) return DDRW_EINVAL;
     cudaSetDevice(ctx->device);
     return estimate_multi(ctx, 1, &ctx->m2, nhit, seed, hit_offset, eta, exponents, logW, rel_var, delta, info);
+}
+
+// log of the mean of exp(-e_j) (log-sum-exp) and the sample variance of exp(-e_j) over its squared mean
+static void two_flavour_factor(const double *e, int n, double *logF, double *relvar)
+{
+    double mx = -e[0];
+    for (int j = 1; j < n; j++) mx = std::max(mx, -e[j]);
+    double s = 0, s2 = 0;
+    for (int j = 0; j < n; j++) {
+        double w = std::exp(-e[j] - mx);
+        s += w;
+        s2 += w * w;
+    }
+    double mean = s / n;
+    *logF = mx + std::log(mean);
+    *relvar = n > 1 ? (s2 / n - mean * mean) * n / (n - 1) / (mean * mean) : 0.0;
+}
+
+// Re of the mean of exp(-e1_j) for complex e1 (Eq. 11): (log |Re F|, sign of Re F)
+static void one_flavour_factor(const double *e1, int n, double *logabs, double *sign)
+{
+    double mx = -e1[0];
+    for (int j = 1; j < n; j++) mx = std::max(mx, -e1[2 * j]);
+    double s = 0;
+    for (int j = 0; j < n; j++) s += std::exp(-e1[2 * j] - mx) * std::cos(e1[2 * j + 1]);
+    double mean = s / n;
+    *logabs = mx + std::log(std::fabs(mean));
+    *sign = mean >= 0 ? 1.0 : -1.0;
+}
+
+ddrw_status ddrw_estimate_interp(ddrw_ctx *ctx, int N, int nhit, uint64_t seed, uint64_t hit_offset, double *exponents,
+                                 double *exponents_1f, double *logW, double *logW_factors, double *rel_var,
+                                 ddrw_solve_info *info)
+{
+    if (!ctx) return DDRW_EINVAL;
+    if (N < 1 || N > MAXM || nhit <= 0) return set_error(ctx, DDRW_EINVAL, "1 <= N <= 8 interpolation steps, nhit > 0");
+    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
+    cudaSetDevice(ctx->device);
+    auto t0 = std::chrono::steady_clock::now();
+    // m_i = (i/N) m2 + ((N-i)/N) m1, factor i = 1..N pairs (m_{i-1}, m_i)
+    std::vector<double> ma(N), mb(N);
+    for (int i = 1; i <= N; i++) {
+        ma[i - 1] = ((double)(i - 1) * ctx->m2 + (double)(N - i + 1) * ctx->m1) / N;
+        mb[i - 1] = ((double)i * ctx->m2 + (double)(N - i) * ctx->m1) / N;
+    }
+    const int budget = ctx->max_rhs > 0 ? ctx->max_rhs : rhs_budget(ctx);
+    std::vector<double> e((size_t)N * nhit), e1((size_t)2 * N * nhit);
+    SolveStats stats;
+    ddrw_status conv = DDRW_OK, st;
+    if (N * nhit <= budget) {
+        // every factor as one mass slot, each with its own noise vectors (hits hit_offset + i nhit + j)
+        st = estimate_chunk(ctx, N, ma.data(), mb.data(), nhit, seed, hit_offset, true, nullptr, e.data(), e1.data(),
+                            nullptr, stats);
+        if (st == DDRW_ENOCONV) conv = st;
+        else if (st) return st;
+    } else {
+        const int hper = std::min(nhit, budget);
+        for (int i = 0; i < N; i++)
+            for (int j0 = 0; j0 < nhit; j0 += hper) {
+                const int jn = std::min(hper, nhit - j0);
+                st = estimate_chunk(ctx, 1, &ma[i], &mb[i], jn, seed, hit_offset + (uint64_t)i * nhit + j0, false,
+                                    nullptr, e.data() + (size_t)i * nhit + j0, e1.data() + 2 * ((size_t)i * nhit + j0),
+                                    nullptr, stats);
+                if (st == DDRW_ENOCONV) conv = st;
+                else if (st) return st;
+            }
+    }
+    double l2 = 0, l1 = 0, sg = 1;
+    for (int i = 0; i < N; i++) {
+        double lf, rv, la, sgn;
+        two_flavour_factor(e.data() + (size_t)i * nhit, nhit, &lf, &rv);
+        one_flavour_factor(e1.data() + 2 * (size_t)i * nhit, nhit, &la, &sgn);
+        l2 += lf;
+        l1 += la;
+        sg *= sgn;
+        if (logW_factors) logW_factors[i] = lf;
+        if (rel_var) rel_var[i] = rv;
+    }
+    if (exponents) std::copy(e.begin(), e.end(), exponents);
+    if (exponents_1f) std::copy(e1.begin(), e1.end(), exponents_1f);
+    if (logW) {
+        logW[0] = l2;        // two flavours: log W_gl (Eq. 8)
+        logW[1] = l1;        // one flavour: log |W_1f| (Eq. 11, real part of each factor)
+        logW[2] = sg;        // sign of W_1f
+        logW[3] = 0.5 * l2;  // root trick: log sqrt(W_gl)
+    }
+    fill_info(info, stats, elapsed(t0));
+    for (double v : e)
+        if (!(v == v)) return set_error(ctx, DDRW_ENUMERIC, "NaN exponent");
+    return conv;
 }
 
 ddrw_status ddrw_estimate_masses(ddrw_ctx *ctx, int nmass, const double *m2, int nhit, uint64_t seed,

@@ -505,7 +505,7 @@ extern "C" ddrw_status ddrw_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64
         c[nhit + j] = -w;
     }
     double *cd, *lamd, *red;
-    if ((st = workspace(ctx, "frc_c", sizeof(double) * (R2 + 144 + 8 * R2), (void **)&cd))) return st;
+    if ((st = workspace(ctx, "frc_c", sizeof(double) * (R2 + 144 + 12 * R2), (void **)&cd))) return st;
     lamd = cd + R2;
     red = lamd + 144;
     DDRW_CUDA_CHECK(cudaMemcpyAsync(cd, c.data(), sizeof(double) * R2, cudaMemcpyHostToDevice, ctx->stream));
@@ -514,12 +514,12 @@ extern "C" ddrw_status ddrw_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64
     // de/dm2 = -2 Re[<zt_2, q_2> + <wt_2, a_2>] = -2 Re[<L1, rho> + <L2, sigma>] on the m2 slot
     if (dm2) {
         if ((st = Blas<PrecD>::norm_dot(ctx, VecRange{V, 0, V, rs, nhit}, ZT + rs * nhit, Q + rs * nhit, red))) return st;
-        if ((st = Blas<PrecD>::norm_dot(ctx, VecRange{V, 0, V, rs, nhit}, WT + rs * nhit, A + rs * nhit, red + 2 * nhit)))
+        if ((st = Blas<PrecD>::norm_dot(ctx, VecRange{V, 0, V, rs, nhit}, WT + rs * nhit, A + rs * nhit, red + 3 * nhit)))
             return st;
-        std::vector<double> h(4 * nhit);
-        DDRW_CUDA_CHECK(cudaMemcpyAsync(h.data(), red, sizeof(double) * 4 * nhit, cudaMemcpyDeviceToHost, ctx->stream));
+        std::vector<double> h(6 * nhit);
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(h.data(), red, sizeof(double) * 6 * nhit, cudaMemcpyDeviceToHost, ctx->stream));
         DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
-        for (int j = 0; j < nhit; j++) dm2[j] = -2.0 * (h[2 * j + 1] + h[2 * nhit + 2 * j + 1]);
+        for (int j = 0; j < nhit; j++) dm2[j] = -2.0 * (h[3 * j + 1] + h[3 * nhit + 3 * j + 1]);
     }
     if (dU) {
         double2 *omega;

@@ -348,3 +348,55 @@ def test_estimator_mean_and_variance():
     for j in range(2):
         res = lat.exponent(m1, m2, lat.unpack(eta[j]))
         assert abs(res["e"] - e[j]) < 1e-10 * max(abs(e[j]), 1.0)
+
+
+# ----------------------------------------------------------------------------- one flavour (Eq. 11, Eq. 12), interpolation (Eq. 8)
+
+def test_one_flavour_integral_and_variance():
+    """Eq. 11: the mean of exp(-eta^dag (Mh - 1) eta) -> 1/det Mh (real by g5-hermiticity);
+    Eq. 12: its variance 1/det(Mh^dag + Mh - 1) - 1/det(Mh^dag Mh), by sampling."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, seed=1)
+    lat = oc.Lattice(dims, (2, 2, 2, 2), U, csw=1.0)
+    Mh = od.ratio_matrix(lat, 0.20, 0.15)
+    n = Mh.shape[0]
+    ev = np.linalg.eigvals(Mh)
+    assert np.all(ev.real > 0)                                      # integral defined
+    assert np.all(np.linalg.eigvalsh(Mh + Mh.conj().T) > 1)         # variance defined
+    s, ld = np.linalg.slogdet(Mh)
+    W1 = np.exp(-ld) / s                                            # 1/det Mh
+    assert abs(W1.imag) < 1e-10 * abs(W1)
+    W1 = W1.real
+    s2, ld2 = np.linalg.slogdet(Mh + Mh.conj().T - np.eye(n))
+    _, ldMM = np.linalg.slogdet(Mh.conj().T @ Mh)
+    var = float(np.exp(-ld2).real - np.exp(-ldMM))
+    ns = 12000
+    eta = oc.noise_packed(seed=91, hit0=0, nhit=ns, n=n)
+    e1 = np.sum(eta.conj() * (eta @ (Mh - np.eye(n)).T), axis=1)   # eta^dag (Mh - 1) eta
+    x = np.exp(-e1)
+    assert abs(x.mean().real - W1) < 4 * np.sqrt(var / ns)
+    assert abs(x.mean().imag) < 4 * np.sqrt(var / ns)
+    assert abs(np.mean(np.abs(x - x.mean()) ** 2) / var - 1) < 0.25
+    # sensitivity: the two-flavour value is many standard errors away
+    assert abs(W1 - np.exp(-ldMM)) > 20 * np.sqrt(var / ns)
+    # the oracle's delta gives the same complex exponent
+    for j in range(2):
+        res = lat.exponent(0.20, 0.15, lat.unpack(eta[j]))
+        e1_orc = np.vdot(eta[j], lat.pack(res["delta"]))
+        assert abs(e1_orc - e1[j]) < 1e-10 * max(abs(e1[j]), 1.0)
+
+
+def test_mass_interpolation_telescopes():
+    """Eq. 8: with m_i = (i/N) m2 + ((N-i)/N) m1 the factors Mh_i = A(m_i)^-1 A(m_{i-1}) multiply to
+    det Mh: prod_i 1/det(Mh_i^dag Mh_i) = 1/det(Mh^dag Mh)."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, seed=1)
+    lat = oc.Lattice(dims, (2, 2, 2, 2), U, csw=1.0)
+    m1, m2, N = 0.20, 0.14, 3
+    ms = [(i / N) * m2 + ((N - i) / N) * m1 for i in range(N + 1)]
+    tot = 0.0
+    for i in range(1, N + 1):
+        Mi = od.ratio_matrix(lat, ms[i - 1], ms[i])
+        tot += np.linalg.slogdet(Mi.conj().T @ Mi)[1]
+    one = od.ratio_matrix(lat, m1, m2)
+    assert abs(tot - np.linalg.slogdet(one.conj().T @ one)[1]) < 1e-9
