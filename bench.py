@@ -312,6 +312,14 @@ def main():
     key = binding.PROF_DSLASH32 if prec != binding.FP64 else binding.PROF_DSLASH64
     nl, kms, kbytes = ctx.profile_read(key)
     blk = ctx.profile_read(binding.PROF_BLOCK32 if prec != binding.FP64 else binding.PROF_BLOCK64)
+    shares = {}
+    for name, kind in (("stencil_fp32", binding.PROF_DSLASH32), ("stencil_fp64", binding.PROF_DSLASH64),
+                       ("stencil_fp32_blocks", binding.PROF_DSLASH32_BLK), ("stencil_fp64_blocks", binding.PROF_DSLASH64_BLK),
+                       ("block_solver_fp32", binding.PROF_BLOCK32), ("block_solver_fp64", binding.PROF_BLOCK64),
+                       ("krylov_vectors", binding.PROF_BLAS)):
+        n_, t_, _ = ctx.profile_read(kind)
+        if n_:
+            shares[name] = {"launches": n_, "ms": round(t_, 2), "share": round(t_ / ms_prof, 4)}
     ctx.profile(False)
     ctx.use_graphs(True)
     t_max = max_over_ranks(ms, dist, dev)
@@ -330,7 +338,8 @@ def main():
                 "share_of_step": (kms / ms_prof) if ms_prof > 0 else None,
                 "block_solver_share_of_step": (blk[1] / ms_prof) if ms_prof > 0 else None,
                 "measured_on": "one extra step of the same workload with the Krylov-loop graphs off "
-                               f"({ms_prof:.0f} ms), every stencil launch timed by CUDA events"}
+                               f"({ms_prof:.0f} ms), every stencil launch timed by CUDA events",
+                "step_breakdown": shares}
 
     out = {"metric": METRIC, "value": value, "unit": "estimates/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -217,8 +217,9 @@ ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
  * their summed compulsory bytes (each field counted once per launch: spinors per right-hand
  * side, links and clover terms once).  Classes: 0 FP64 stencil, 1 FP32 stencil (all hops),
  * 2 / 3 FP64 / FP32 stencil restricted to hops inside or between blocks, 4 / 5 FP64 / FP32
- * persistent block solver (bytes not counted); class 6 returns in *launches the number of kernel
- * launches of every kind since the last reset.  ddrw_profile(ctx, enable) resets the counters. */
+ * persistent block solver (bytes not counted), 6 Krylov vector kernels and reductions (bytes not
+ * counted); class 7 returns in *launches the number of kernel launches of every kind since the
+ * last reset.  ddrw_profile(ctx, enable) resets the counters. */
 ddrw_status ddrw_profile(ddrw_ctx *ctx, int enable);
 ddrw_status ddrw_profile_read(ddrw_ctx *ctx, int kind, long *launches, double *ms, double *bytes);
 

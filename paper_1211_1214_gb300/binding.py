@@ -29,7 +29,7 @@ EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", 
            "ddrw_estimate_interp"]
 
 #: kernel classes of ddrw_profile_read
-PROF_DSLASH64, PROF_DSLASH32, PROF_DSLASH64_BLK, PROF_DSLASH32_BLK, PROF_BLOCK64, PROF_BLOCK32, PROF_LAUNCHES = range(7)
+PROF_DSLASH64, PROF_DSLASH32, PROF_DSLASH64_BLK, PROF_DSLASH32_BLK, PROF_BLOCK64, PROF_BLOCK32, PROF_BLAS, PROF_LAUNCHES = range(8)
 
 
 class DDRWError(RuntimeError):

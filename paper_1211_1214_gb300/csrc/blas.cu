@@ -454,6 +454,7 @@ ddrw_status Blas<P>::bicg_init(ddrw_ctx *ctx, const VecRange &vr, E *r, E *rh, E
     if (st) return st;
     VecArgs<P> va{vr.V, vr.off, vr.n, vr.rs};
     dim3 g(grid_for(vr.n), vr.nrhs);
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
     ++ctx->launches;
     k_bicg_init<P><<<g, NT, 0, ctx->stream>>>(va, r, rh, p, x, sc, part, tk);
     return DDRW_OK;
@@ -467,6 +468,7 @@ ddrw_status Blas<P>::bicg_alpha(ddrw_ctx *ctx, const VecRange &vr, const E *rh, 
     ddrw_status st = reduce_ws(ctx, vr.nrhs, &part, &tk);
     if (st) return st;
     VecArgs<P> va{vr.V, vr.off, vr.n, vr.rs};
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
     ++ctx->launches;
     k_bicg_alpha<P><<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(va, rh, v, sc, part, tk);
     return DDRW_OK;
@@ -476,6 +478,7 @@ template <class P>
 void Blas<P>::bicg_s(ddrw_ctx *ctx, const VecRange &vr, E *r, const E *v, const KScal *sc)
 {
     VecArgs<P> va{vr.V, vr.off, vr.n, vr.rs};
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
     ++ctx->launches;
     k_bicg_s<P><<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(va, r, v, sc);
 }
@@ -488,6 +491,7 @@ ddrw_status Blas<P>::bicg_omega(ddrw_ctx *ctx, const VecRange &vr, const E *t, c
     ddrw_status st = reduce_ws(ctx, vr.nrhs, &part, &tk);
     if (st) return st;
     VecArgs<P> va{vr.V, vr.off, vr.n, vr.rs};
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
     ++ctx->launches;
     k_bicg_omega<P><<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(va, t, r, sc, part, tk);
     return DDRW_OK;
@@ -502,6 +506,7 @@ ddrw_status Blas<P>::bicg_xr(ddrw_ctx *ctx, const VecRange &vr, E *x, const E *p
     ddrw_status st = reduce_ws(ctx, vr.nrhs, &part, &tk);
     if (st) return st;
     VecArgs<P> va{vr.V, vr.off, vr.n, vr.rs};
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
     ++ctx->launches;
     k_bicg_xr<P><<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(va, x, p, r, t, rh, sc, part, tk);
     return DDRW_OK;
@@ -511,6 +516,7 @@ template <class P>
 void Blas<P>::bicg_p(ddrw_ctx *ctx, const VecRange &vr, E *p, const E *r, const E *v, const KScal *sc)
 {
     VecArgs<P> va{vr.V, vr.off, vr.n, vr.rs};
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
     ++ctx->launches;
     k_bicg_p<P><<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(va, p, r, v, sc);
 }
@@ -523,6 +529,7 @@ ddrw_status Blas<P>::norm2(ddrw_ctx *ctx, const VecRange &vr, const E *f, double
     ddrw_status st = reduce_ws(ctx, vr.nrhs, &part, &tk);
     if (st) return st;
     VecArgs<P> va{vr.V, vr.off, vr.n, vr.rs};
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
     ++ctx->launches;
     k_norm2<P><<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(va, f, out, part, tk);
     return DDRW_OK;
@@ -536,6 +543,7 @@ ddrw_status Blas<P>::norm_dot(ddrw_ctx *ctx, const VecRange &vr, const E *d, con
     ddrw_status st = reduce_ws(ctx, vr.nrhs, &part, &tk);
     if (st) return st;
     VecArgs<P> va{vr.V, vr.off, vr.n, vr.rs};
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
     ++ctx->launches;
     k_norm_dot<P><<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(va, d, e, out, part, tk);
     return DDRW_OK;
@@ -545,18 +553,21 @@ template <class P>
 void Blas<P>::axpby(ddrw_ctx *ctx, const VecRange &vr, double a, const E *x, double b, E *y)
 {
     VecArgs<P> va{vr.V, vr.off, vr.n, vr.rs};
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
     ++ctx->launches;
     k_axpby<P><<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(va, a, x, b, y);
 }
 
 void to32(ddrw_ctx *ctx, const VecRange &vr, long rs32, const double2 *in, float4 *out, const double *scale)
 {
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
     ++ctx->launches;
     k_to32<<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(vr.V, vr.off, vr.n, vr.rs, rs32, in, out, scale);
 }
 
 void add32(ddrw_ctx *ctx, const VecRange &vr, long rs32, const float4 *e, double2 *x, const double *scale)
 {
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
     ++ctx->launches;
     k_add32<<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(vr.V, vr.off, vr.n, vr.rs, rs32, e, x, scale);
 }

@@ -131,7 +131,8 @@ enum {
     PROF_DSLASH32_BLK = 3,
     PROF_BLOCK64 = 4,       // persistent block solver, FP64
     PROF_BLOCK32 = 5,       // persistent block solver, FP32
-    PROF_NKIND = 6
+    PROF_BLAS = 6,          // Krylov vector kernels and reductions
+    PROF_NKIND = 7
 };
 
 // Records CUDA events around the launches in its scope when profiling is on.
