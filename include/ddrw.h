@@ -76,7 +76,7 @@ typedef struct {
 /* Create a context on CUDA device `device` for a T x X x Y x Z lattice cut into hypercubic blocks
  * of length block[0] = block[1] = block[2] = block[3] = l (Eq. 1; Sec. 2 uses 6^4 and 8^4 blocks).
  * l must be 2, 4, 6 or 8, divide every dimension, and leave an even number (>= 2) of blocks in
- * each direction, so that neighbouring blocks always have opposite colours.  cuda_stream is a
+ * each direction, so that neighbouring blocks always have opposite colours; at most 2^27 sites.  cuda_stream is a
  * cudaStream_t (NULL: the context creates its own).  DDRW_EINVAL on a bad geometry. */
 ddrw_status ddrw_create(ddrw_ctx **out, const int dims[4], const int block[4], int device, void *cuda_stream);
 void ddrw_destroy(ddrw_ctx *ctx);

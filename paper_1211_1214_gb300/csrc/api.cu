@@ -303,7 +303,7 @@ ddrw_status ddrw_create(ddrw_ctx **out, const int dims[4], const int block[4], i
         ctx->NB[mu] = dims[mu] / l;
         ctx->V *= dims[mu];
     }
-    if (ctx->V > (1L << 30)) {
+    if (ctx->V > (1L << 27)) {  // in-field offsets of the kernels are 32-bit
         delete ctx;
         return DDRW_EINVAL;
     }

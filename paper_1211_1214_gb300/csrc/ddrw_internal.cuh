@@ -76,8 +76,8 @@ __device__ __forceinline__ void decode_site(long s, const GeomDev &g, Site<BL> &
 // Neighbour of st one step in direction mu (dir = +1/-1).  *cross is set when the hop leaves the
 // block; *phase is the boundary sign of the hop.
 template <int BL>
-__device__ __forceinline__ long neighbour(const Site<BL> &st, int mu, int dir, const GeomDev &g, bool *cross,
-                                          int *phase)
+__device__ __forceinline__ int neighbour(const Site<BL> &st, int mu, int dir, const GeomDev &g, bool *cross,
+                                         int *phase)
 {
     int c0 = st.c[0], c1 = st.c[1], c2 = st.c[2], c3 = st.c[3];
     int cm = st.c[mu] + dir;
@@ -98,7 +98,7 @@ __device__ __forceinline__ long neighbour(const Site<BL> &st, int mu, int dir, c
     else if (mu == 2) c2 = cm;
     else c3 = cm;
     int lb = ((c0 * BL + c1) * BL + c2) * BL + c3;
-    return (long)(1 - st.p) * g.vh + (long)blk * BlockShape<BL>::VBH + (lb >> 1);
+    return (1 - st.p) * (int)g.vh + blk * BlockShape<BL>::VBH + (lb >> 1);
 }
 
 // lexicographic site index of an internal site (boundary layout)
@@ -245,15 +245,16 @@ struct PrecD {
     using UElem = double2;
     using CElem = double2;
 
-    __device__ static __forceinline__ void load_spinor(const SElem *__restrict__ f, long stride, long s, Spinor<R> &p)
+    // in-field offsets are 32-bit (k * stride + s < 2^31: at most 2^27 sites)
+    __device__ static __forceinline__ void load_spinor(const SElem *__restrict__ f, int stride, int s, Spinor<R> &p)
     {
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-            double2 v = __ldg(f + k * stride + s);
+            double2 v = __ldg(f + (k * stride + s));
             p.v[k / 3][k % 3] = {v.x, v.y};
         }
     }
-    __device__ static __forceinline__ void load_spinor_rw(const SElem *f, long stride, long s, Spinor<R> &p)
+    __device__ static __forceinline__ void load_spinor_rw(const SElem *f, int stride, int s, Spinor<R> &p)
     {
 #pragma unroll
         for (int k = 0; k < 12; k++) {
@@ -261,36 +262,36 @@ struct PrecD {
             p.v[k / 3][k % 3] = {v.x, v.y};
         }
     }
-    __device__ static __forceinline__ void store_spinor(SElem *__restrict__ f, long stride, long s, const Spinor<R> &p)
+    __device__ static __forceinline__ void store_spinor(SElem *__restrict__ f, int stride, int s, const Spinor<R> &p)
     {
 #pragma unroll
         for (int k = 0; k < 12; k++) f[k * stride + s] = make_double2(p.v[k / 3][k % 3].re, p.v[k / 3][k % 3].im);
     }
     // the 6 components of chirality ch (spins 2ch, 2ch+1): planes 6ch .. 6ch+5
-    __device__ static __forceinline__ void load_chiral(const SElem *__restrict__ f, long stride, long s, int ch, cpx<R> *v)
+    __device__ static __forceinline__ void load_chiral(const SElem *__restrict__ f, int stride, int s, int ch, cpx<R> *v)
     {
 #pragma unroll
         for (int k = 0; k < 6; k++) {
-            double2 e = __ldg(f + (6 * ch + k) * stride + s);
+            double2 e = __ldg(f + ((6 * ch + k) * stride + s));
             v[k] = {e.x, e.y};
         }
     }
-    __device__ static __forceinline__ void load_link(const UElem *__restrict__ U, long V, int mu, long s, Link<R> &L)
+    __device__ static __forceinline__ void load_link(const UElem *__restrict__ U, int V, int mu, int s, Link<R> &L)
     {
-        const UElem *b = U + (long)mu * 9 * V + s;
+        const UElem *b = U + (long)mu * 9 * V;
 #pragma unroll
         for (int k = 0; k < 9; k++) {
-            double2 v = __ldg(b + k * V);
+            double2 v = __ldg(b + (k * V + s));
             L.m[k / 3][k % 3] = {v.x, v.y};
         }
     }
     // reals 0..35 of chirality block ch
-    __device__ static __forceinline__ void load_clover(const CElem *__restrict__ Cl, long V, long s, int ch, R *c)
+    __device__ static __forceinline__ void load_clover(const CElem *__restrict__ Cl, int V, int s, int ch, R *c)
     {
-        const CElem *b = Cl + (long)ch * 18 * V + s;
+        const CElem *b = Cl + (long)ch * 18 * V;
 #pragma unroll
         for (int k = 0; k < 18; k++) {
-            double2 v = __ldg(b + k * V);
+            double2 v = __ldg(b + (k * V + s));
             c[2 * k] = v.x;
             c[2 * k + 1] = v.y;
         }
@@ -306,16 +307,16 @@ struct PrecS {
     using UElem = float4;
     using CElem = float4;
 
-    __device__ static __forceinline__ void load_spinor(const SElem *__restrict__ f, long stride, long s, Spinor<R> &p)
+    __device__ static __forceinline__ void load_spinor(const SElem *__restrict__ f, int stride, int s, Spinor<R> &p)
     {
 #pragma unroll
         for (int k = 0; k < 6; k++) {
-            float4 v = __ldg(f + k * stride + s);
+            float4 v = __ldg(f + (k * stride + s));
             p.v[(2 * k) / 3][(2 * k) % 3] = {v.x, v.y};
             p.v[(2 * k + 1) / 3][(2 * k + 1) % 3] = {v.z, v.w};
         }
     }
-    __device__ static __forceinline__ void load_spinor_rw(const SElem *f, long stride, long s, Spinor<R> &p)
+    __device__ static __forceinline__ void load_spinor_rw(const SElem *f, int stride, int s, Spinor<R> &p)
     {
 #pragma unroll
         for (int k = 0; k < 6; k++) {
@@ -324,7 +325,7 @@ struct PrecS {
             p.v[(2 * k + 1) / 3][(2 * k + 1) % 3] = {v.z, v.w};
         }
     }
-    __device__ static __forceinline__ void store_spinor(SElem *__restrict__ f, long stride, long s, const Spinor<R> &p)
+    __device__ static __forceinline__ void store_spinor(SElem *__restrict__ f, int stride, int s, const Spinor<R> &p)
     {
 #pragma unroll
         for (int k = 0; k < 6; k++) {
@@ -333,20 +334,20 @@ struct PrecS {
         }
     }
     // the 6 components of chirality ch (spins 2ch, 2ch+1): planes 3ch .. 3ch+2
-    __device__ static __forceinline__ void load_chiral(const SElem *__restrict__ f, long stride, long s, int ch, cpx<R> *v)
+    __device__ static __forceinline__ void load_chiral(const SElem *__restrict__ f, int stride, int s, int ch, cpx<R> *v)
     {
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            float4 e = __ldg(f + (3 * ch + k) * stride + s);
+            float4 e = __ldg(f + ((3 * ch + k) * stride + s));
             v[2 * k] = {e.x, e.y};
             v[2 * k + 1] = {e.z, e.w};
         }
     }
     // two stored rows; row 2 = conj(row0 x row1) (U in SU(3))
-    __device__ static __forceinline__ void load_link(const UElem *__restrict__ U, long V, int mu, long s, Link<R> &L)
+    __device__ static __forceinline__ void load_link(const UElem *__restrict__ U, int V, int mu, int s, Link<R> &L)
     {
-        const UElem *b = U + (long)mu * 3 * V + s;
-        float4 a0 = __ldg(b), a1 = __ldg(b + V), a2 = __ldg(b + 2 * V);
+        const UElem *b = U + (long)mu * 3 * V;
+        float4 a0 = __ldg(b + s), a1 = __ldg(b + (V + s)), a2 = __ldg(b + (2 * V + s));
         L.m[0][0] = {a0.x, a0.y};
         L.m[0][1] = {a0.z, a0.w};
         L.m[0][2] = {a1.x, a1.y};
@@ -364,12 +365,12 @@ struct PrecS {
             L.m[2][c] = {t.re, -t.im};
         }
     }
-    __device__ static __forceinline__ void load_clover(const CElem *__restrict__ Cl, long V, long s, int ch, R *c)
+    __device__ static __forceinline__ void load_clover(const CElem *__restrict__ Cl, int V, int s, int ch, R *c)
     {
-        const CElem *b = Cl + (long)ch * 9 * V + s;
+        const CElem *b = Cl + (long)ch * 9 * V;
 #pragma unroll
         for (int k = 0; k < 9; k++) {
-            float4 v = __ldg(b + k * V);
+            float4 v = __ldg(b + (k * V + s));
             c[4 * k] = v.x;
             c[4 * k + 1] = v.y;
             c[4 * k + 2] = v.z;

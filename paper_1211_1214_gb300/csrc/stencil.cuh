@@ -23,7 +23,7 @@ __device__ __forceinline__ void hop_dir(const GeomDev &g, const Site<BL> &st, lo
     bool cross;
     int ph;
     {
-        long sf = neighbour<BL>(st, MU, +1, g, &cross, &ph);
+        int sf = neighbour<BL>(st, MU, +1, g, &cross, &ph);
         if (HOPSEL == 0 || (HOPSEL == 1 && !cross) || (HOPSEL == 2 && cross)) {
             Spinor<R> p;
             if (RO) P::load_spinor(in, g.V, sf, p);
@@ -42,7 +42,7 @@ __device__ __forceinline__ void hop_dir(const GeomDev &g, const Site<BL> &st, lo
         }
     }
     {
-        long sb = neighbour<BL>(st, MU, -1, g, &cross, &ph);
+        int sb = neighbour<BL>(st, MU, -1, g, &cross, &ph);
         if (HOPSEL == 0 || (HOPSEL == 1 && !cross) || (HOPSEL == 2 && cross)) {
             Spinor<R> p;
             if (RO) P::load_spinor(in, g.V, sb, p);
@@ -85,14 +85,14 @@ __device__ __forceinline__ void hop_dir_multi(const GeomDev &g, const Site<BL> &
     bool cross;
     int ph;
     {
-        long sf = neighbour<BL>(st, MU, +1, g, &cross, &ph);
+        int sf = neighbour<BL>(st, MU, +1, g, &cross, &ph);
         if (HOPSEL == 0 || (HOPSEL == 1 && !cross) || (HOPSEL == 2 && cross)) {
             Link<R> L;
             P::load_link(U, g.V, MU, s, L);
 #pragma unroll
             for (int r = 0; r < NR; r++) {
                 Spinor<R> p;
-                P::load_spinor(in + r * rstride, g.V, sf, p);
+                P::load_spinor(in + r * rstride, (int)g.V, sf, p);
                 Half<R> h, w;
                 project<MU, -1>(p, h);
                 link_mul(L, h, w);
@@ -106,14 +106,14 @@ __device__ __forceinline__ void hop_dir_multi(const GeomDev &g, const Site<BL> &
         }
     }
     {
-        long sb = neighbour<BL>(st, MU, -1, g, &cross, &ph);
+        int sb = neighbour<BL>(st, MU, -1, g, &cross, &ph);
         if (HOPSEL == 0 || (HOPSEL == 1 && !cross) || (HOPSEL == 2 && cross)) {
             Link<R> L;
             P::load_link(U, g.V, MU, sb, L);
 #pragma unroll
             for (int r = 0; r < NR; r++) {
                 Spinor<R> p;
-                P::load_spinor(in + r * rstride, g.V, sb, p);
+                P::load_spinor(in + r * rstride, (int)g.V, sb, p);
                 Half<R> h, w;
                 project<MU, +1>(p, h);
                 link_dag_mul(L, h, w);
