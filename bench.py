@@ -313,13 +313,13 @@ def main():
     nl, kms, kbytes = ctx.profile_read(key)
     blk = ctx.profile_read(binding.PROF_BLOCK32 if prec != binding.FP64 else binding.PROF_BLOCK64)
     shares = {}
-    for name, kind in (("stencil_fp32", binding.PROF_DSLASH32), ("stencil_fp64", binding.PROF_DSLASH64),
+    for cls, kind in (("stencil_fp32", binding.PROF_DSLASH32), ("stencil_fp64", binding.PROF_DSLASH64),
                        ("stencil_fp32_blocks", binding.PROF_DSLASH32_BLK), ("stencil_fp64_blocks", binding.PROF_DSLASH64_BLK),
                        ("block_solver_fp32", binding.PROF_BLOCK32), ("block_solver_fp64", binding.PROF_BLOCK64),
-                       ("krylov_vectors", binding.PROF_BLAS)):
+                       ("krylov_vectors", binding.PROF_BLAS), ("residual_stencil_ds", binding.PROF_DSLASH_DS)):
         n_, t_, _ = ctx.profile_read(kind)
         if n_:
-            shares[name] = {"launches": n_, "ms": round(t_, 2), "share": round(t_ / ms_prof, 4)}
+            shares[cls] = {"launches": n_, "ms": round(t_, 2), "share": round(t_ / ms_prof, 4)}
     ctx.profile(False)
     ctx.use_graphs(True)
     t_max = max_over_ranks(ms, dist, dev)

@@ -58,7 +58,8 @@ typedef enum {
 
 typedef enum {
     DDRW_FP64 = 0,       /* every kernel in FP64 */
-    DDRW_MIXED_FP32 = 1, /* inner solves in FP32 storage and arithmetic, FP64 defect correction */
+    DDRW_MIXED_FP32 = 1, /* inner solves in FP32 storage and arithmetic; defect correction on FP64
+                            fields with residuals b - D x in double-single arithmetic (ddrw_apply_D_ds) */
     DDRW_MIXED_FP16 = 2  /* reserved: FP16 storage is not built; ddrw_set_solver rejects it (DDRW_EINVAL) */
 } ddrw_prec;
 
@@ -102,6 +103,11 @@ ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, dou
 
 /* out = D(m) in for nrhs full-lattice spinor fields, in FP64. */
 ddrw_status ddrw_apply_D(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs);
+
+/* out = D(m) in evaluated in the double-single arithmetic (FP32 pairs, ~44 significant bits) that
+ * the mixed precisions use for their defect-correction residuals b - D x; for checking that
+ * arithmetic against ddrw_apply_D. */
+ddrw_status ddrw_apply_D_ds(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs);
 
 /* out = D_{rows,cols}(m) in: the block of Eq. 1 with rows in colour `rows` and columns in colour
  * `cols` (DDRW_BLACK, DDRW_WHITE or DDRW_ALL); rows outside `rows` are set to zero.  D_bb and
@@ -218,8 +224,8 @@ ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
  * side, links and clover terms once).  Classes: 0 FP64 stencil, 1 FP32 stencil (all hops),
  * 2 / 3 FP64 / FP32 stencil restricted to hops inside or between blocks, 4 / 5 FP64 / FP32
  * persistent block solver (bytes not counted), 6 Krylov vector kernels and reductions (bytes not
- * counted); class 7 returns in *launches the number of kernel launches of every kind since the
- * last reset.  ddrw_profile(ctx, enable) resets the counters. */
+ * counted), 7 double-single residual stencil; class 8 returns in *launches the number of kernel
+ * launches of every kind since the last reset.  ddrw_profile(ctx, enable) resets the counters. */
 ddrw_status ddrw_profile(ddrw_ctx *ctx, int enable);
 ddrw_status ddrw_profile_read(ddrw_ctx *ctx, int kind, long *launches, double *ms, double *bytes);
 

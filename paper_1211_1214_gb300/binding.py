@@ -26,10 +26,11 @@ EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", 
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
            "ddrw_autotune", "ddrw_autotune_report", "ddrw_force", "ddrw_use_graphs",
-           "ddrw_estimate_interp"]
+           "ddrw_estimate_interp", "ddrw_apply_D_ds"]
 
 #: kernel classes of ddrw_profile_read
-PROF_DSLASH64, PROF_DSLASH32, PROF_DSLASH64_BLK, PROF_DSLASH32_BLK, PROF_BLOCK64, PROF_BLOCK32, PROF_BLAS, PROF_LAUNCHES = range(8)
+PROF_DSLASH64, PROF_DSLASH32, PROF_DSLASH64_BLK, PROF_DSLASH32_BLK, PROF_BLOCK64, PROF_BLOCK32, PROF_BLAS, PROF_DSLASH_DS, \
+    PROF_LAUNCHES = range(9)
 
 
 class DDRWError(RuntimeError):
@@ -75,6 +76,7 @@ def load(path: str | None = None):
         "ddrw_set_params": (st, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
         "ddrw_set_solver": (st, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
         "ddrw_apply_D": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
+        "ddrw_apply_D_ds": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_apply_block": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_solve_block": (st, [vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
         "ddrw_solve_D": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
@@ -174,6 +176,9 @@ class Context:
 
     def apply_D(self, m, x, out, nrhs=1):
         self._check(self.L.ddrw_apply_D(self._h, float(m), _ptr(x), _ptr(out), int(nrhs)), "ddrw_apply_D")
+
+    def apply_D_ds(self, m, x, out, nrhs=1):
+        self._check(self.L.ddrw_apply_D_ds(self._h, float(m), _ptr(x), _ptr(out), int(nrhs)), "ddrw_apply_D_ds")
 
     def apply_block(self, rows, cols, m, x, out, nrhs=1):
         self._check(self.L.ddrw_apply_block(self._h, int(rows), int(cols), float(m), _ptr(x), _ptr(out), int(nrhs)),

@@ -167,6 +167,30 @@ long host_internal_index(const ddrw_ctx *ctx, const std::vector<int> &blk_index,
     return (long)p * ctx->vh + (long)blk_index[B] * vbh + (lb >> 1);
 }
 
+ddrw_status residual_stencil(ddrw_ctx *ctx, DslashCall c, bool ds)
+{
+    if (!ds) {
+        dslash64(ctx, c);
+        return DDRW_OK;
+    }
+    // the stencil reads `in` at the hop neighbours and `x` at the site; both are the same field here
+    if (c.x && c.x != c.in) return set_error(ctx, DDRW_EINVAL, "double-single residual needs x == in");
+    if (c.hopsel == 2) return set_error(ctx, DDRW_EINVAL, "double-single residual of a hop between blocks");
+    float4 *xs;
+    ddrw_status st = workspace(ctx, "ds_split", sizeof(float4) * (size_t)c.rstride * c.nrhs, (void **)&xs);
+    if (st) return st;
+    // only the sites the stencil reads: its own blocks (hops inside blocks) or every site
+    long vbh = (long)ctx->l * ctx->l * ctx->l * ctx->l / 2;
+    if (c.hopsel == 1)
+        split64(ctx, (const double2 *)c.in, xs, ctx->V, ctx->vh, c.blk0 * vbh, c.nblk * vbh, 0, 2, c.nrhs, c.rstride);
+    else
+        split64(ctx, (const double2 *)c.in, xs, ctx->V, ctx->vh, 0, ctx->vh, 0, 2, c.nrhs, c.rstride);
+    c.in = xs;
+    c.x = xs;
+    dslash_ds(ctx, c);
+    return DDRW_OK;
+}
+
 // zero the sites of one colour (both parities) in nrhs FP64 fields
 __global__ void k_zero_colour(double2 *f, long V, long vh, long lo, long n, int nrhs)
 {
@@ -386,7 +410,9 @@ ddrw_status ddrw_create(ddrw_ctx **out, const int dims[4], const int block[4], i
     if (cudaMalloc(&ctx->U64, sizeof(double2) * 36 * V) != cudaSuccess ||
         cudaMalloc(&ctx->U32, sizeof(float4) * 12 * V) != cudaSuccess ||
         cudaMalloc(&ctx->C64, sizeof(double2) * 36 * V) != cudaSuccess ||
-        cudaMalloc(&ctx->C32, sizeof(float4) * 18 * V) != cudaSuccess)
+        cudaMalloc(&ctx->C32, sizeof(float4) * 18 * V) != cudaSuccess ||
+        cudaMalloc(&ctx->Udd, sizeof(float4) * 36 * V) != cudaSuccess ||
+        cudaMalloc(&ctx->Cdd, sizeof(float4) * 36 * V) != cudaSuccess)
         return fail(DDRW_ENOMEM);
     if (cudaMallocHost(&ctx->h_pinned, 1 << 20) != cudaSuccess) return fail(DDRW_ENOMEM);
     ctx->h_pinned_bytes = 1 << 20;
@@ -408,6 +434,8 @@ void ddrw_destroy(ddrw_ctx *ctx)
     cudaFree(ctx->U32);
     cudaFree(ctx->C64);
     cudaFree(ctx->C32);
+    cudaFree(ctx->Udd);
+    cudaFree(ctx->Cdd);
     free_inverses(ctx);
     for (auto &kv : ctx->ws) cudaFree(kv.second.p);
     for (auto &r : ctx->prof_pending) {
@@ -441,6 +469,10 @@ static ddrw_status rebuild(ddrw_ctx *ctx)
 {
     build_clover(ctx);
     DDRW_CUDA_CHECK(cudaGetLastError());
+    // split copies of links and clover for the double-single residual stencil
+    // 36 planes of V elements each: three "fields" of 12 planes
+    split64(ctx, ctx->U64, ctx->Udd, ctx->V, 0, 0, ctx->V, 0, 1, 3, 12L * ctx->V);
+    split64(ctx, ctx->C64, ctx->Cdd, ctx->V, 0, 0, ctx->V, 0, 1, 3, 12L * ctx->V);
     free_inverses(ctx);
     MassInv *mi;
     ddrw_status st = mass_inverse(ctx, ctx->m1, &mi);
@@ -557,6 +589,43 @@ ddrw_status ddrw_apply_block(ddrw_ctx *ctx, int rows, int cols, double m, const 
 ddrw_status ddrw_apply_D(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs)
 {
     return ddrw_apply_block(ctx, DDRW_ALL, DDRW_ALL, m, in, out, nrhs);
+}
+
+ddrw_status ddrw_apply_D_ds(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs)
+{
+    if (!ctx || !in || !out || nrhs <= 0) return set_error(ctx, DDRW_EINVAL, "bad argument");
+    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
+    cudaSetDevice(ctx->device);
+    size_t ubytes = sizeof(double) * 24 * (size_t)ctx->V * nrhs;
+    size_t fbytes = sizeof(double2) * 12 * (size_t)ctx->V * nrhs;
+    const void *din;
+    void *dout;
+    bool host_out;
+    double2 *fin, *fout;
+    ddrw_status st;
+    if ((st = stage_in(ctx, in, ubytes, "stage_in", &din))) return st;
+    if ((st = stage_out(ctx, out, ubytes, "stage_out", &dout, &host_out))) return st;
+    if ((st = workspace(ctx, "api_f0", fbytes, (void **)&fin))) return st;
+    if ((st = workspace(ctx, "api_f1", fbytes, (void **)&fout))) return st;
+    pack_spinor64(ctx, (const double *)din, fin, nrhs);
+    DslashCall c;
+    c.in = fin;
+    c.x = fin;
+    c.out = fout;
+    c.rstride = 12 * ctx->V;
+    c.nrhs = nrhs;
+    c.masses[0] = m;
+    c.alpha = 1.0;
+    c.beta = -0.5;
+    c.diag = 1;
+    c.par0 = 0;
+    c.npar = 2;
+    c.blk0 = 0;
+    c.nblk = ctx->nblk;
+    if ((st = residual_stencil(ctx, c, true))) return st;
+    unpack_spinor64(ctx, fout, (double *)dout, nrhs);
+    if ((st = finish_out(ctx, out, dout, ubytes, host_out))) return st;
+    return sync(ctx);
 }
 
 }  // extern "C"

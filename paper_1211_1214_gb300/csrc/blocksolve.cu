@@ -91,6 +91,8 @@ ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const do
     ddrw_status st;
     std::vector<double> bb, rr;
     if ((st = colour_norms(ctx, colour, b, nrhs, bb))) return st;
+    for (int r = 0; r < nrhs; r++)
+        if (!std::isfinite(bb[r])) return set_error(ctx, DDRW_ENUMERIC, "non-finite right-hand side");
     int *stat;
     if ((st = workspace(ctx, "blk_stat", sizeof(int) * 2, (void **)&stat))) return st;
     double2 *res64, *e64 = nullptr;
@@ -188,7 +190,7 @@ ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const do
         c.npar = 2;
         c.blk0 = colour == DDRW_BLACK ? 0 : ctx->nblk_c;
         c.nblk = ctx->nblk_c;
-        dslash64(ctx, c);
+        if ((st = residual_stencil(ctx, c, mixed))) return st;
         if (stats) stats->fp64_dslash_half += 1;
         for (int p = 0; p < 2; p++) Blas<PrecD>::axpby(ctx, colour_range(ctx, colour, p, nrhs, rs64), 1.0, b, 1.0, res64);
         if ((st = colour_norms(ctx, colour, res64, nrhs, rr))) return st;
@@ -198,7 +200,8 @@ ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const do
         }
         double worst = 0;
         for (int r = 0; r < nrhs; r++)
-            if (bb[r] > 0) worst = std::max(worst, std::sqrt(rr[r] / bb[r]));
+            if (!std::isfinite(rr[r])) worst = NAN;
+            else if (bb[r] > 0 && !(worst != worst)) worst = std::max(worst, std::sqrt(rr[r] / bb[r]));
         if (stats) stats->block_rel_residual = std::max(stats->block_rel_residual, worst);
         if (!(worst == worst)) return set_error(ctx, DDRW_ENUMERIC, "NaN in a block solve");
         if (worst <= tol) return DDRW_OK;

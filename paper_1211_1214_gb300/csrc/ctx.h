@@ -89,6 +89,8 @@ struct ddrw_ctx {
     float4 *U32 = nullptr;   // [4][3][V] two-row
     double2 *C64 = nullptr;  // [2][18][V]
     float4 *C32 = nullptr;   // [2][9][V]
+    float4 *Udd = nullptr;   // [4][9][V] links split into FP32 pairs (double-single stencil)
+    float4 *Cdd = nullptr;   // [2][18][V] clover split into FP32 pairs
     std::deque<ddrw::MassInv> inv;  // deque: MassInv addresses stay valid as entries are added
 
     // workspaces by name (grow-only)
@@ -132,7 +134,8 @@ enum {
     PROF_BLOCK64 = 4,       // persistent block solver, FP64
     PROF_BLOCK32 = 5,       // persistent block solver, FP32
     PROF_BLAS = 6,          // Krylov vector kernels and reductions
-    PROF_NKIND = 7
+    PROF_DSLASH_DS = 7,     // double-single residual stencil (mixed path)
+    PROF_NKIND = 8
 };
 
 // Records CUDA events around the launches in its scope when profiling is on.
@@ -198,6 +201,15 @@ struct DslashCall {
 };
 void dslash64(ddrw_ctx *ctx, const DslashCall &c);
 void dslash32(ddrw_ctx *ctx, const DslashCall &c);
+// double-single stencil: in / x are split fields (float4 per complex), out an FP64 field
+void dslash_ds(ddrw_ctx *ctx, const DslashCall &c);
+// FP64 -> split elements at k V + p vh + off + j (k < 12 planes, parities p = par0 .. par0 + npar - 1,
+// j < len) of nrhs fields rs elements apart; the same offsets in out
+void split64(ddrw_ctx *ctx, const double2 *in, float4 *out, long V, long vh, long off, long len, int par0, int npar,
+             int nrhs, long rs);
+// out = alpha D x + ... as DslashCall c on FP64 fields, in FP64 (ds = false) or in double-single
+// arithmetic through a split copy of the input (ds = true)
+ddrw_status residual_stencil(ddrw_ctx *ctx, DslashCall c, bool ds);
 
 // x = D_cc(ms)^-1 b on the sites of colour c (persistent block solver + FP64 defect correction)
 ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const double2 *b, double2 *x, int nrhs,

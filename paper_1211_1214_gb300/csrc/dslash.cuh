@@ -18,7 +18,10 @@
 // tuning runs are harmless.
 #pragma once
 
+#include <type_traits>
+
 #include "ctx.h"
+#include "ddprec.cuh"
 #include "stencil.cuh"
 
 namespace ddrw {
@@ -140,7 +143,10 @@ DsArgs<P> make_args(ddrw_ctx *ctx, const DslashCall &c)
         a.mass4[k] = R(4.0 + c.masses[kk]);
         a.Ainv[k] = (const typename P::CElem *)c.Ainv[kk];
     }
-    if constexpr (sizeof(R) == 8) {
+    if constexpr (std::is_same<P, PrecDD>::value) {
+        a.U = (const typename P::UElem *)ctx->Udd;
+        a.Cl = (const typename P::CElem *)ctx->Cdd;
+    } else if constexpr (sizeof(R) == 8) {
         a.U = (const typename P::UElem *)ctx->U64;
         a.Cl = (const typename P::CElem *)ctx->C64;
     } else {
@@ -157,16 +163,22 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
     long n = (long)c.npar * c.nblk * BlockShape<BL>::VBH;
     unsigned grid = (unsigned)(((n + cfg.nt - 1) / cfg.nt) * (c.nrhs / cfg.nr));
     ++ctx->launches;
-    if (c.hopsel == 0) {
-        switch (cfg.nr) {
-        case 4: k_dslash<P, BL, 0, 4><<<grid, cfg.nt, 0, ctx->stream>>>(g, a); break;
-        case 2: k_dslash<P, BL, 0, 2><<<grid, cfg.nt, 0, ctx->stream>>>(g, a); break;
-        default: k_dslash<P, BL, 0, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a); break;
-        }
-    } else if (c.hopsel == 1) {
-        k_dslash<P, BL, 1, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
+    if constexpr (std::is_same<P, PrecDD>::value) {  // one right-hand side per thread
+        if (c.hopsel == 0) k_dslash<P, BL, 0, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
+        else if (c.hopsel == 1) k_dslash<P, BL, 1, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
+        else k_dslash<P, BL, 2, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
     } else {
-        k_dslash<P, BL, 2, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
+        if (c.hopsel == 0) {
+            switch (cfg.nr) {
+            case 4: k_dslash<P, BL, 0, 4><<<grid, cfg.nt, 0, ctx->stream>>>(g, a); break;
+            case 2: k_dslash<P, BL, 0, 2><<<grid, cfg.nt, 0, ctx->stream>>>(g, a); break;
+            default: k_dslash<P, BL, 0, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a); break;
+            }
+        } else if (c.hopsel == 1) {
+            k_dslash<P, BL, 1, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
+        } else {
+            k_dslash<P, BL, 2, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
+        }
     }
 }
 
@@ -201,8 +213,10 @@ void launch_bl(ddrw_ctx *ctx, const DslashCall &c)
     long n = (long)c.npar * c.nblk * BlockShape<BL>::VBH;
     if (n == 0 || c.nrhs == 0) return;
     DsConfig cfg;
-    if (c.hopsel == 0) cfg = tuned_config(ctx, c, sizeof(R) == 8 ? 64 : 32, BL, &run_cfg<P, BL>);
-    int kind = (sizeof(R) == 8 ? PROF_DSLASH64 : PROF_DSLASH32) + (c.hopsel != 0 ? 2 : 0);
+    constexpr bool split = std::is_same<P, PrecDD>::value;
+    if constexpr (!split)
+        if (c.hopsel == 0) cfg = tuned_config(ctx, c, sizeof(R) == 8 ? 64 : 32, BL, &run_cfg<P, BL>);
+    int kind = split ? PROF_DSLASH_DS : (sizeof(R) == 8 ? PROF_DSLASH64 : PROF_DSLASH32) + (c.hopsel != 0 ? 2 : 0);
     ProfScope ps(ctx, kind, compulsory_bytes<P>(c, n));
     launch_cfg<P, BL>(ctx, c, make_args<P, BL>(ctx, c), cfg);
 }

@@ -288,6 +288,8 @@ ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, dou
     ddrw_status st;
     std::vector<double> bb, rr;
     if ((st = full_norms(ctx, b, nrhs, bb))) return st;
+    for (int r = 0; r < nrhs; r++)
+        if (!std::isfinite(bb[r])) return set_error(ctx, DDRW_ENUMERIC, "non-finite right-hand side");
     double2 *res, *e64 = nullptr;
     float4 *b32 = nullptr, *e32 = nullptr;
     double *scale_d = nullptr;
@@ -353,13 +355,14 @@ ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, dou
         c.nblk = ctx->nblk;
         c.par0 = 0;
         c.npar = 2;
-        dslash64(ctx, c);
+        if ((st = residual_stencil(ctx, c, mixed))) return st;
         if (stats) stats->fp64_dslash_full += 1;
         Blas<PrecD>::axpby(ctx, VecRange{V, 0, V, rs64, nrhs}, 1.0, b, 1.0, res);
         if ((st = full_norms(ctx, res, nrhs, rr))) return st;
         double worst = 0;
         for (int r = 0; r < nrhs; r++)
-            if (bb[r] > 0) worst = std::max(worst, std::sqrt(rr[r] / bb[r]));
+            if (!std::isfinite(rr[r])) worst = NAN;
+            else if (bb[r] > 0 && !(worst != worst)) worst = std::max(worst, std::sqrt(rr[r] / bb[r]));
         if (stats) {
             stats->outer_cycles = cycles + 1;
             stats->outer_rel_residual = worst;

@@ -1,0 +1,74 @@
+"""Failure detection without a GPU fault: every failure is made on the host (bad arguments,
+an iteration cap of 1, NaN in a host input buffer) and must come back as a status code with a
+message, leaving the context usable."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1211_1214_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    dims, l = (8, 8, 8, 8), 4
+    c = binding.Context(dims, (l,) * 4)
+    c.load_gauge(synth.gauge_field(dims, 0.25, seed=1))
+    c.set_params(1.5, 0.05, 0.045)
+    yield c, dims
+    c.close()
+
+
+def test_iteration_cap_reports_no_convergence_and_fills_outputs(ctx):
+    c, dims = ctx
+    c.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13, maxiter=1)
+    b = synth.spinor_field(dims, seed=81)
+    x = np.zeros_like(b)
+    with pytest.raises(binding.DDRWError) as ei:
+        c.solve_D(0.045, b, x)
+    assert ei.value.status == 4  # DDRW_ENOCONV
+    assert np.linalg.norm(x) > 0  # the last iterate is returned
+    c.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13, maxiter=20000)
+    info = c.solve_D(0.045, b, x)  # the context still works
+    assert info["true_rel_residual"] <= 1e-10
+
+
+def test_nan_in_a_host_input_is_reported(ctx):
+    c, dims = ctx
+    c.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+    b = synth.spinor_field(dims, seed=82)
+    b[17, 2, 1] = np.nan
+    x = np.zeros_like(b)
+    with pytest.raises(binding.DDRWError) as ei:
+        c.solve_D(0.045, b, x)
+    assert ei.value.status in (4, 5)  # no convergence or a non-finite reduction
+    b2 = synth.spinor_field(dims, seed=83)
+    assert c.solve_D(0.045, b2, x)["true_rel_residual"] <= 1e-10
+
+
+def test_bad_arguments(ctx):
+    c, dims = ctx
+    b = synth.spinor_field(dims, seed=84)
+    with pytest.raises(binding.DDRWError) as ei:
+        c.solve_block(2, 0.045, b, np.zeros_like(b))  # colour must be black or white
+    assert ei.value.status == 1
+    with pytest.raises(binding.DDRWError) as ei:
+        c.set_solver(binding.MIXED_FP16)  # reserved precision
+    assert ei.value.status == 1
+    with pytest.raises(binding.DDRWError) as ei:
+        c.estimate_interp(9, 2)  # at most 8 interpolation steps
+    assert ei.value.status == 1
+    st = c.L.ddrw_apply_D(c._h, 0.1, None, None, 1)
+    assert st == 1
+    assert b"bad argument" in c.L.ddrw_last_error(c._h)
+
+
+def test_calls_before_a_gauge_field_are_refused():
+    c = binding.Context((4, 4, 4, 4), (2, 2, 2, 2))
+    b = synth.spinor_field((4, 4, 4, 4), seed=85)
+    with pytest.raises(binding.DDRWError) as ei:
+        c.apply_D(0.1, b, np.zeros_like(b))
+    assert ei.value.status == 7  # DDRW_ESTATE
+    c.close()
