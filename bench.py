@@ -230,7 +230,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="64x32^3")
-    ap.add_argument("--prec", choices=["mixed32", "fp64"], default="mixed32")
+    ap.add_argument("--prec", choices=["mixed32", "mixed16", "mixedbf16", "fp64"], default="mixed32")
     ap.add_argument("--fp64-hits", type=int, default=2, help="noise vectors of the FP64-path comparison (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -264,7 +264,11 @@ def main():
     ctx = binding.Context(w["dims"], w["l"], device=local, stream=stream.cuda_stream)
     ctx.load_gauge(U_pin.to(dev))
     ctx.set_params(w["csw"], w["m1"], w["m2s"][0])
-    prec = binding.MIXED_FP32 if args.prec == "mixed32" else binding.FP64
+    prec = {"mixed32": binding.MIXED_FP32, "mixed16": binding.MIXED_FP16, "mixedbf16": binding.MIXED_BF16,
+            "fp64": binding.FP64}[args.prec]
+    low16 = prec in (binding.MIXED_FP16, binding.MIXED_BF16)
+    inner_name = {binding.MIXED_FP32: "FP32", binding.MIXED_FP16: "FP16-storage/FP32-arithmetic",
+                  binding.MIXED_BF16: "BF16-storage/FP32-arithmetic", binding.FP64: "FP64"}[prec]
     tol_block = 1e-10 if prec != binding.FP64 else 1e-13
     ctx.set_solver(prec, tol_outer=1e-10, tol_block=tol_block)
     nhit, m2s = w["nhit"], list(w["m2s"])
@@ -309,14 +313,17 @@ def main():
     evp1.record(stream)
     torch.cuda.synchronize()
     ms_prof = evp0.elapsed_time(evp1)
-    key = binding.PROF_DSLASH32 if prec != binding.FP64 else binding.PROF_DSLASH64
+    key = binding.PROF_DSLASH16 if low16 else binding.PROF_DSLASH32 if prec != binding.FP64 else binding.PROF_DSLASH64
     nl, kms, kbytes = ctx.profile_read(key)
-    blk = ctx.profile_read(binding.PROF_BLOCK32 if prec != binding.FP64 else binding.PROF_BLOCK64)
+    blk = ctx.profile_read(binding.PROF_BLOCK16 if low16 else binding.PROF_BLOCK32 if prec != binding.FP64
+                           else binding.PROF_BLOCK64)
     shares = {}
     for cls, kind in (("stencil_fp32", binding.PROF_DSLASH32), ("stencil_fp64", binding.PROF_DSLASH64),
                        ("stencil_fp32_blocks", binding.PROF_DSLASH32_BLK), ("stencil_fp64_blocks", binding.PROF_DSLASH64_BLK),
                        ("block_solver_fp32", binding.PROF_BLOCK32), ("block_solver_fp64", binding.PROF_BLOCK64),
-                       ("krylov_vectors", binding.PROF_BLAS), ("residual_stencil_ds", binding.PROF_DSLASH_DS)):
+                       ("krylov_vectors", binding.PROF_BLAS), ("residual_stencil_ds", binding.PROF_DSLASH_DS),
+                       ("stencil_16bit", binding.PROF_DSLASH16), ("stencil_16bit_blocks", binding.PROF_DSLASH16_BLK),
+                       ("block_solver_16bit", binding.PROF_BLOCK16)):
         n_, t_, _ = ctx.profile_read(kind)
         if n_:
             shares[cls] = {"launches": n_, "ms": round(t_, 2), "share": round(t_ / ms_prof, 4)}
@@ -328,7 +335,8 @@ def main():
     peaks = measured_peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = (kbytes / (kms / 1e3) / 1e9) if kms > 0 else None
-    kname = "k_dslash<PrecS,%d,0>" % w["l"] if prec != binding.FP64 else "k_dslash<PrecD,%d,0>" % w["l"]
+    kname = "k_dslash<%s,%d,0>" % ({binding.MIXED_FP32: "PrecS", binding.MIXED_FP16: "PrecLow<false>",
+                                    binding.MIXED_BF16: "PrecLow<true>", binding.FP64: "PrecD"}[prec], w["l"])
     traffic = ncu_traffic(kname)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
@@ -343,9 +351,10 @@ def main():
 
     out = {"metric": METRIC, "value": value, "unit": "estimates/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32/f64" if prec != binding.FP64 else "f64",
+           "vs_baseline": None, "dtype": ("f16/f32/f64" if prec == binding.MIXED_FP16 else "bf16/f32/f64" if prec == binding.MIXED_BF16
+                     else "f32/f64" if prec != binding.FP64 else "f64"),
            "data": "synthetic (U = exp(i eps H) Gaussian su(3) links, Philox complex Gaussian noise)",
-           "config": {"workload": describe(name, w, "FP32" if prec != binding.FP64 else "FP64"),
+           "config": {"workload": describe(name, w, inner_name),
                       "lattice": list(w["dims"]), "block": w["l"], "nhit": nhit, "m1": w["m1"], "m2": m2s,
                       "estimates_per_step": per_step, "tol_outer": 1e-10, "tol_block": tol_block,
                       "l2": "inputs larger than L2 (gauge, clover and fields are GBs)",

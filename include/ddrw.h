@@ -60,7 +60,10 @@ typedef enum {
     DDRW_FP64 = 0,       /* every kernel in FP64 */
     DDRW_MIXED_FP32 = 1, /* inner solves in FP32 storage and arithmetic; defect correction on FP64
                             fields with residuals b - D x in double-single arithmetic (ddrw_apply_D_ds) */
-    DDRW_MIXED_FP16 = 2  /* reserved: FP16 storage is not built; ddrw_set_solver rejects it (DDRW_EINVAL) */
+    DDRW_MIXED_FP16 = 2, /* inner solves on FP16 storage (per-site FP32 norm for spinors, two-row
+                            links, 16-bit clover and inverses) with FP32 arithmetic; FP64 defect
+                            correction as for DDRW_MIXED_FP32 */
+    DDRW_MIXED_BF16 = 3  /* as DDRW_MIXED_FP16 with BF16 storage */
 } ddrw_prec;
 
 typedef enum { DDRW_BLACK = 0, DDRW_WHITE = 1, DDRW_ALL = 2 } ddrw_colour;
@@ -211,11 +214,19 @@ ddrw_status ddrw_solve_block_noalloc(ddrw_ctx *ctx, int colour, double m, const 
 ddrw_status ddrw_use_graphs(ddrw_ctx *ctx, int enable, long *graph_launches);
 
 /* Autotuner of the stencil launches: on the first launch of each shape (precision, block length,
- * parities, right-hand sides, diagonal/post modes) it times right-hand sides per thread {1,2,4}
- * and CTA sizes {64,128,256} with CUDA events and keeps the fastest.  enable = 0 uses a fixed
- * choice; either call clears the tuned table.  The report lists the tuned shapes, one per line. */
+ * parities, right-hand sides, diagonal/post modes) it times right-hand sides per thread {1,2,4},
+ * sites per CTA row {64,128,256}, right-hand-side rows per CTA {1,2} and unrolled or rolled hop
+ * code with CUDA events and keeps the fastest.  enable = 0 uses a fixed choice; either call
+ * clears the tuned table.  The report lists the tuned shapes, one per line. */
 ddrw_status ddrw_autotune(ddrw_ctx *ctx, int enable);
 ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
+
+/* Pins the configuration of every tunable stencil launch (overrides the autotuner): nr
+ * right-hand sides per thread (1, 2 or 4), nt sites per CTA row (32 .. 256, a multiple of 32),
+ * nw right-hand-side rows per CTA (nt * nw <= 256), roll 0 / 1 (unrolled / rolled hop code).
+ * A launch whose right-hand sides per mass slot are not a multiple of nr * nw runs with nr = nw = 1.
+ * nr = 0 returns to autotuning.  DDRW_EINVAL for values outside these ranges. */
+ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll);
 
 /* Kernel timing for measurement (not part of the method): with profiling enabled, CUDA events
  * bracket every launch of the instrumented kernel classes on the context's stream, and
@@ -224,8 +235,9 @@ ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
  * side, links and clover terms once).  Classes: 0 FP64 stencil, 1 FP32 stencil (all hops),
  * 2 / 3 FP64 / FP32 stencil restricted to hops inside or between blocks, 4 / 5 FP64 / FP32
  * persistent block solver (bytes not counted), 6 Krylov vector kernels and reductions (bytes not
- * counted), 7 double-single residual stencil; class 8 returns in *launches the number of kernel
- * launches of every kind since the last reset.  ddrw_profile(ctx, enable) resets the counters. */
+ * counted), 7 double-single residual stencil, 8 and 9 the stencil on 16-bit storage (all hops /
+ * block-restricted), 10 the persistent block solver on 16-bit storage (bytes not counted); class 11
+ * returns in *launches the number of kernel launches of every kind since the last reset.  ddrw_profile(ctx, enable) resets the counters. */
 ddrw_status ddrw_profile(ddrw_ctx *ctx, int enable);
 ddrw_status ddrw_profile_read(ddrw_ctx *ctx, int kind, long *launches, double *ms, double *bytes);
 

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-FP64, MIXED_FP32, MIXED_FP16 = 0, 1, 2
+FP64, MIXED_FP32, MIXED_FP16, MIXED_BF16 = 0, 1, 2, 3
 BLACK, WHITE, ALL = 0, 1, 2
 
 _STATUS = {0: "DDRW_OK", 1: "DDRW_EINVAL", 2: "DDRW_ENOMEM", 3: "DDRW_ECUDA", 4: "DDRW_ENOCONV",
@@ -25,12 +25,12 @@ EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", 
            "ddrw_set_params", "ddrw_set_solver", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
-           "ddrw_autotune", "ddrw_autotune_report", "ddrw_force", "ddrw_use_graphs",
+           "ddrw_autotune", "ddrw_autotune_report", "ddrw_stencil_config", "ddrw_force", "ddrw_use_graphs",
            "ddrw_estimate_interp", "ddrw_apply_D_ds"]
 
 #: kernel classes of ddrw_profile_read
 PROF_DSLASH64, PROF_DSLASH32, PROF_DSLASH64_BLK, PROF_DSLASH32_BLK, PROF_BLOCK64, PROF_BLOCK32, PROF_BLAS, PROF_DSLASH_DS, \
-    PROF_LAUNCHES = range(9)
+    PROF_DSLASH16, PROF_DSLASH16_BLK, PROF_BLOCK16, PROF_LAUNCHES = range(12)
 
 
 class DDRWError(RuntimeError):
@@ -90,6 +90,7 @@ def load(path: str | None = None):
                                       dp, ctypes.POINTER(SolveInfo)]),
         "ddrw_profile": (st, [vp, ctypes.c_int]),
         "ddrw_autotune": (st, [vp, ctypes.c_int]),
+        "ddrw_stencil_config": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "ddrw_use_graphs": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long)]),
         "ddrw_estimate_interp": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp, dp, dp,
                                       dp, ctypes.POINTER(SolveInfo)]),
@@ -253,6 +254,10 @@ class Context:
 
     def autotune(self, enable=True):
         self._check(self.L.ddrw_autotune(self._h, int(enable)), "ddrw_autotune")
+
+    def stencil_config(self, nr=0, nt=128, nw=1, roll=0):
+        """Pin the stencil launch configuration (nr = 0: back to the autotuner)."""
+        self._check(self.L.ddrw_stencil_config(self._h, int(nr), int(nt), int(nw), int(roll)), "ddrw_stencil_config")
 
     def autotune_report(self):
         buf = ctypes.create_string_buffer(1 << 16)

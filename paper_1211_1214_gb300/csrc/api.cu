@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include "blas.cuh"
 #include "ctx.h"
 
 namespace ddrw {
@@ -80,13 +81,20 @@ ddrw_status mass_inverse(ddrw_ctx *ctx, double m, MassInv **out)
         }
     MassInv mi;
     mi.m = m;
-    DDRW_CUDA_CHECK(cudaMalloc(&mi.A64, sizeof(double2) * 36 * (size_t)ctx->V));
-    cudaError_t e = cudaMalloc(&mi.A32, sizeof(float4) * 18 * (size_t)ctx->V);
+    cudaError_t e = cudaMalloc(&mi.A64, sizeof(double2) * 36 * (size_t)ctx->V);
+    if (e == cudaSuccess) e = cudaMalloc(&mi.A32, sizeof(float4) * 18 * (size_t)ctx->V);
+    if (e == cudaSuccess) e = cudaMalloc(&mi.A16, sizeof(uint2) * 18 * (size_t)ctx->V);
+    if (e == cudaSuccess) e = cudaMalloc(&mi.Ab16, sizeof(uint2) * 18 * (size_t)ctx->V);
     if (e != cudaSuccess) {
         cudaFree(mi.A64);
-        return set_cuda_error(ctx, e, "cudaMalloc(A32)", __FILE__, __LINE__);
+        cudaFree(mi.A32);
+        cudaFree(mi.A16);
+        cudaFree(mi.Ab16);
+        return set_cuda_error(ctx, e, "cudaMalloc(in-block inverse)", __FILE__, __LINE__);
     }
     build_inverse(ctx, m, mi);
+    f32_to_low(ctx, mi.A32, mi.A16, 18L * ctx->V, false);
+    f32_to_low(ctx, mi.A32, mi.Ab16, 18L * ctx->V, true);
     DDRW_CUDA_CHECK(cudaGetLastError());
     ctx->inv.push_back(mi);
     *out = &ctx->inv.back();
@@ -99,6 +107,8 @@ static void free_inverses(ddrw_ctx *ctx)
     for (auto &mi : ctx->inv) {
         cudaFree(mi.A64);
         cudaFree(mi.A32);
+        cudaFree(mi.A16);
+        cudaFree(mi.Ab16);
     }
     ctx->inv.clear();
 }
@@ -411,6 +421,10 @@ ddrw_status ddrw_create(ddrw_ctx **out, const int dims[4], const int block[4], i
         cudaMalloc(&ctx->U32, sizeof(float4) * 12 * V) != cudaSuccess ||
         cudaMalloc(&ctx->C64, sizeof(double2) * 36 * V) != cudaSuccess ||
         cudaMalloc(&ctx->C32, sizeof(float4) * 18 * V) != cudaSuccess ||
+        cudaMalloc(&ctx->U16, sizeof(uint2) * 12 * V) != cudaSuccess ||
+        cudaMalloc(&ctx->Ub16, sizeof(uint2) * 12 * V) != cudaSuccess ||
+        cudaMalloc(&ctx->C16, sizeof(uint2) * 18 * V) != cudaSuccess ||
+        cudaMalloc(&ctx->Cb16, sizeof(uint2) * 18 * V) != cudaSuccess ||
         cudaMalloc(&ctx->Udd, sizeof(float4) * 36 * V) != cudaSuccess ||
         cudaMalloc(&ctx->Cdd, sizeof(float4) * 36 * V) != cudaSuccess)
         return fail(DDRW_ENOMEM);
@@ -434,6 +448,10 @@ void ddrw_destroy(ddrw_ctx *ctx)
     cudaFree(ctx->U32);
     cudaFree(ctx->C64);
     cudaFree(ctx->C32);
+    cudaFree(ctx->U16);
+    cudaFree(ctx->Ub16);
+    cudaFree(ctx->C16);
+    cudaFree(ctx->Cb16);
     cudaFree(ctx->Udd);
     cudaFree(ctx->Cdd);
     free_inverses(ctx);
@@ -469,6 +487,11 @@ static ddrw_status rebuild(ddrw_ctx *ctx)
 {
     build_clover(ctx);
     DDRW_CUDA_CHECK(cudaGetLastError());
+    // 16-bit copies of the two-row links and the clover term for the FP16 / BF16 inner solves
+    f32_to_low(ctx, ctx->U32, ctx->U16, 12L * ctx->V, false);
+    f32_to_low(ctx, ctx->U32, ctx->Ub16, 12L * ctx->V, true);
+    f32_to_low(ctx, ctx->C32, ctx->C16, 18L * ctx->V, false);
+    f32_to_low(ctx, ctx->C32, ctx->Cb16, 18L * ctx->V, true);
     // split copies of links and clover for the double-single residual stencil
     // 36 planes of V elements each: three "fields" of 12 planes
     split64(ctx, ctx->U64, ctx->Udd, ctx->V, 0, 0, ctx->V, 0, 1, 3, 12L * ctx->V);
@@ -520,8 +543,7 @@ ddrw_status ddrw_set_params(ddrw_ctx *ctx, double csw, double m1, double m2, int
 ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, double tol_block, int maxiter)
 {
     if (!ctx) return DDRW_EINVAL;
-    if (prec < DDRW_FP64 || prec > DDRW_MIXED_FP16) return set_error(ctx, DDRW_EINVAL, "unknown precision");
-    if (prec == DDRW_MIXED_FP16) return set_error(ctx, DDRW_EINVAL, "FP16 storage is not built in this library");
+    if (prec < DDRW_FP64 || prec > DDRW_MIXED_BF16) return set_error(ctx, DDRW_EINVAL, "unknown precision");
     if (!(tol_outer > 0) || !(tol_block > 0) || maxiter <= 0) return set_error(ctx, DDRW_EINVAL, "bad tolerance");
     ctx->prec = prec;
     ctx->tol_outer = tol_outer;

@@ -8,6 +8,7 @@
 // also performs the scalar update of the Krylov recurrence.
 #include "blas.cuh"
 #include "ctx.h"
+#include "lowprec.cuh"
 
 namespace ddrw {
 
@@ -94,24 +95,21 @@ __global__ void __launch_bounds__(NT) k_bicg_init(VecArgs<P> va, typename P::SEl
                                                   typename P::SElem *p, typename P::SElem *x, KScal *sc,
                                                   double *part, unsigned *ticket)
 {
-    using E = typename P::SElem;
-    using L = El<E>;
-    using R = typename L::R;
-    const long ro = (long)blockIdx.y * va.rs + va.off;
+    using R = typename P::R;
+    const long rb = (long)blockIdx.y * va.rs;
     R acc = 0;
     for (long j = (long)blockIdx.x * NT + threadIdx.x; j < va.n; j += (long)gridDim.x * NT)
-        for (int k = 0; k < P::SPLANES; k++) {
-            long a = ro + k * va.V + j;
-            cpx<R> c[L::NC], z[L::NC];
-            L::ld(r + a, c);
+        for (int k = 0; k < P::NCHUNK; k++) {
+            cpx<R> c[P::CW], z[P::CW];
+            P::ld_chunk(r + rb, va.V, va.off + j, k, c);
 #pragma unroll
-            for (int q = 0; q < L::NC; q++) {
+            for (int q = 0; q < P::CW; q++) {
                 acc += c[q].re * c[q].re + c[q].im * c[q].im;
                 z[q] = {R(0), R(0)};
             }
-            L::st(rh + a, c);
-            L::st(p + a, c);
-            L::st(x + a, z);
+            P::st_chunk(rh + rb, va.V, va.off + j, k, c);
+            P::st_chunk(p + rb, va.V, va.off + j, k, c);
+            P::st_chunk(x + rb, va.V, va.off + j, k, z);
         }
     double v[1] = {(double)acc};
     if (grid_sum<1, NT>(v, part, ticket)) {
@@ -129,20 +127,17 @@ __global__ void __launch_bounds__(NT) k_bicg_alpha(VecArgs<P> va, const typename
                                                    const typename P::SElem *v, KScal *sc, double *part,
                                                    unsigned *ticket)
 {
-    using E = typename P::SElem;
-    using L = El<E>;
-    using R = typename L::R;
+    using R = typename P::R;
     if (!sc[blockIdx.y].active) return;
-    const long ro = (long)blockIdx.y * va.rs + va.off;
+    const long rb = (long)blockIdx.y * va.rs;
     R are = 0, aim = 0;
     for (long j = (long)blockIdx.x * NT + threadIdx.x; j < va.n; j += (long)gridDim.x * NT)
-        for (int k = 0; k < P::SPLANES; k++) {
-            long a = ro + k * va.V + j;
-            cpx<R> c[L::NC], d[L::NC];
-            L::ld(rh + a, c);
-            L::ld(v + a, d);
+        for (int k = 0; k < P::NCHUNK; k++) {
+            cpx<R> c[P::CW], d[P::CW];
+            P::ld_chunk(rh + rb, va.V, va.off + j, k, c);
+            P::ld_chunk(v + rb, va.V, va.off + j, k, d);
 #pragma unroll
-            for (int q = 0; q < L::NC; q++) {
+            for (int q = 0; q < P::CW; q++) {
                 cpx<R> t = cmulc(c[q], d[q]);
                 are += t.re;
                 aim += t.im;
@@ -167,22 +162,19 @@ template <class P>
 __global__ void __launch_bounds__(NT) k_bicg_s(VecArgs<P> va, typename P::SElem *r, const typename P::SElem *v,
                                                const KScal *sc)
 {
-    using E = typename P::SElem;
-    using L = El<E>;
-    using R = typename L::R;
+    using R = typename P::R;
     const KScal &s = sc[blockIdx.y];
     if (!s.active) return;
     const cpx<R> al = {R(s.alpha.x), R(s.alpha.y)};
-    const long ro = (long)blockIdx.y * va.rs + va.off;
+    const long rb = (long)blockIdx.y * va.rs;
     for (long j = (long)blockIdx.x * NT + threadIdx.x; j < va.n; j += (long)gridDim.x * NT)
-        for (int k = 0; k < P::SPLANES; k++) {
-            long a = ro + k * va.V + j;
-            cpx<R> c[L::NC], d[L::NC];
-            L::ld(r + a, c);
-            L::ld(v + a, d);
+        for (int k = 0; k < P::NCHUNK; k++) {
+            cpx<R> c[P::CW], d[P::CW];
+            P::ld_chunk(r + rb, va.V, va.off + j, k, c);
+            P::ld_chunk(v + rb, va.V, va.off + j, k, d);
 #pragma unroll
-            for (int q = 0; q < L::NC; q++) c[q] = c[q] - cmul(al, d[q]);
-            L::st(r + a, c);
+            for (int q = 0; q < P::CW; q++) c[q] = c[q] - cmul(al, d[q]);
+            P::st_chunk(r + rb, va.V, va.off + j, k, c);
         }
 }
 
@@ -191,20 +183,17 @@ __global__ void __launch_bounds__(NT) k_bicg_omega(VecArgs<P> va, const typename
                                                    const typename P::SElem *r, KScal *sc, double *part,
                                                    unsigned *ticket)
 {
-    using E = typename P::SElem;
-    using L = El<E>;
-    using R = typename L::R;
+    using R = typename P::R;
     if (!sc[blockIdx.y].active) return;
-    const long ro = (long)blockIdx.y * va.rs + va.off;
+    const long rb = (long)blockIdx.y * va.rs;
     R tsr = 0, tsi = 0, tt = 0;
     for (long j = (long)blockIdx.x * NT + threadIdx.x; j < va.n; j += (long)gridDim.x * NT)
-        for (int k = 0; k < P::SPLANES; k++) {
-            long a = ro + k * va.V + j;
-            cpx<R> c[L::NC], d[L::NC];
-            L::ld(t + a, c);
-            L::ld(r + a, d);
+        for (int k = 0; k < P::NCHUNK; k++) {
+            cpx<R> c[P::CW], d[P::CW];
+            P::ld_chunk(t + rb, va.V, va.off + j, k, c);
+            P::ld_chunk(r + rb, va.V, va.off + j, k, d);
 #pragma unroll
-            for (int q = 0; q < L::NC; q++) {
+            for (int q = 0; q < P::CW; q++) {
                 cpx<R> z = cmulc(c[q], d[q]);
                 tsr += z.re;
                 tsi += z.im;
@@ -231,25 +220,22 @@ __global__ void __launch_bounds__(NT) k_bicg_xr(VecArgs<P> va, typename P::SElem
                                                 const typename P::SElem *rh, KScal *sc, double *part,
                                                 unsigned *ticket)
 {
-    using E = typename P::SElem;
-    using L = El<E>;
-    using R = typename L::R;
+    using R = typename P::R;
     const KScal &s0 = sc[blockIdx.y];
     if (!s0.active) return;
     const cpx<R> al = {R(s0.alpha.x), R(s0.alpha.y)}, om = {R(s0.omega.x), R(s0.omega.y)};
-    const long ro = (long)blockIdx.y * va.rs + va.off;
+    const long rb = (long)blockIdx.y * va.rs;
     R rhre = 0, rhim = 0, rr = 0;
     for (long j = (long)blockIdx.x * NT + threadIdx.x; j < va.n; j += (long)gridDim.x * NT)
-        for (int k = 0; k < P::SPLANES; k++) {
-            long a = ro + k * va.V + j;
-            cpx<R> xv[L::NC], pv[L::NC], sv[L::NC], tv[L::NC], hv[L::NC];
-            L::ld(x + a, xv);
-            L::ld(p + a, pv);
-            L::ld(r + a, sv);
-            L::ld(t + a, tv);
-            L::ld(rh + a, hv);
+        for (int k = 0; k < P::NCHUNK; k++) {
+            cpx<R> xv[P::CW], pv[P::CW], sv[P::CW], tv[P::CW], hv[P::CW];
+            P::ld_chunk(x + rb, va.V, va.off + j, k, xv);
+            P::ld_chunk(p + rb, va.V, va.off + j, k, pv);
+            P::ld_chunk(r + rb, va.V, va.off + j, k, sv);
+            P::ld_chunk(t + rb, va.V, va.off + j, k, tv);
+            P::ld_chunk(rh + rb, va.V, va.off + j, k, hv);
 #pragma unroll
-            for (int q = 0; q < L::NC; q++) {
+            for (int q = 0; q < P::CW; q++) {
                 xv[q] = xv[q] + cmul(al, pv[q]) + cmul(om, sv[q]);
                 sv[q] = sv[q] - cmul(om, tv[q]);
                 cpx<R> z = cmulc(hv[q], sv[q]);
@@ -257,8 +243,8 @@ __global__ void __launch_bounds__(NT) k_bicg_xr(VecArgs<P> va, typename P::SElem
                 rhim += z.im;
                 rr += sv[q].re * sv[q].re + sv[q].im * sv[q].im;
             }
-            L::st(x + a, xv);
-            L::st(r + a, sv);
+            P::st_chunk(x + rb, va.V, va.off + j, k, xv);
+            P::st_chunk(r + rb, va.V, va.off + j, k, sv);
         }
     double val[3] = {(double)rhre, (double)rhim, (double)rr};
     if (grid_sum<3, NT>(val, part, ticket)) {
@@ -290,23 +276,20 @@ template <class P>
 __global__ void __launch_bounds__(NT) k_bicg_p(VecArgs<P> va, typename P::SElem *p, const typename P::SElem *r,
                                                const typename P::SElem *v, const KScal *sc)
 {
-    using E = typename P::SElem;
-    using L = El<E>;
-    using R = typename L::R;
+    using R = typename P::R;
     const KScal &s = sc[blockIdx.y];
     if (!s.active) return;
     const cpx<R> be = {R(s.beta.x), R(s.beta.y)}, om = {R(s.omega.x), R(s.omega.y)};
-    const long ro = (long)blockIdx.y * va.rs + va.off;
+    const long rb = (long)blockIdx.y * va.rs;
     for (long j = (long)blockIdx.x * NT + threadIdx.x; j < va.n; j += (long)gridDim.x * NT)
-        for (int k = 0; k < P::SPLANES; k++) {
-            long a = ro + k * va.V + j;
-            cpx<R> pv[L::NC], rv[L::NC], vv[L::NC];
-            L::ld(p + a, pv);
-            L::ld(r + a, rv);
-            L::ld(v + a, vv);
+        for (int k = 0; k < P::NCHUNK; k++) {
+            cpx<R> pv[P::CW], rv[P::CW], vv[P::CW];
+            P::ld_chunk(p + rb, va.V, va.off + j, k, pv);
+            P::ld_chunk(r + rb, va.V, va.off + j, k, rv);
+            P::ld_chunk(v + rb, va.V, va.off + j, k, vv);
 #pragma unroll
-            for (int q = 0; q < L::NC; q++) pv[q] = rv[q] + cmul(be, pv[q] - cmul(om, vv[q]));
-            L::st(p + a, pv);
+            for (int q = 0; q < P::CW; q++) pv[q] = rv[q] + cmul(be, pv[q] - cmul(om, vv[q]));
+            P::st_chunk(p + rb, va.V, va.off + j, k, pv);
         }
 }
 
@@ -317,17 +300,15 @@ template <class P>
 __global__ void __launch_bounds__(NT) k_norm2(VecArgs<P> va, const typename P::SElem *f, double *out,
                                               double *part, unsigned *ticket)
 {
-    using E = typename P::SElem;
-    using L = El<E>;
-    using R = typename L::R;
-    const long ro = (long)blockIdx.y * va.rs + va.off;
+    using R = typename P::R;
+    const long rb = (long)blockIdx.y * va.rs;
     R acc = 0;
     for (long j = (long)blockIdx.x * NT + threadIdx.x; j < va.n; j += (long)gridDim.x * NT)
-        for (int k = 0; k < P::SPLANES; k++) {
-            cpx<R> c[L::NC];
-            L::ld(f + ro + k * va.V + j, c);
+        for (int k = 0; k < P::NCHUNK; k++) {
+            cpx<R> c[P::CW];
+            P::ld_chunk(f + rb, va.V, va.off + j, k, c);
 #pragma unroll
-            for (int q = 0; q < L::NC; q++) acc += c[q].re * c[q].re + c[q].im * c[q].im;
+            for (int q = 0; q < P::CW; q++) acc += c[q].re * c[q].re + c[q].im * c[q].im;
         }
     double v[1] = {(double)acc};
     if (grid_sum<1, NT>(v, part, ticket)) out[blockIdx.y] = v[0];
@@ -340,18 +321,16 @@ __global__ void __launch_bounds__(NT) k_norm_dot(VecArgs<P> va, const typename P
                                                  const typename P::SElem *e, double *out, double *part,
                                                  unsigned *ticket)
 {
-    using E = typename P::SElem;
-    using L = El<E>;
-    using R = typename L::R;
-    const long ro = (long)blockIdx.y * va.rs + va.off;
+    using R = typename P::R;
+    const long rb = (long)blockIdx.y * va.rs;
     R nn = 0, dr = 0, di = 0;
     for (long j = (long)blockIdx.x * NT + threadIdx.x; j < va.n; j += (long)gridDim.x * NT)
-        for (int k = 0; k < P::SPLANES; k++) {
-            cpx<R> c[L::NC], f[L::NC];
-            L::ld(d + ro + k * va.V + j, c);
-            L::ld(e + ro + k * va.V + j, f);
+        for (int k = 0; k < P::NCHUNK; k++) {
+            cpx<R> c[P::CW], f[P::CW];
+            P::ld_chunk(d + rb, va.V, va.off + j, k, c);
+            P::ld_chunk(e + rb, va.V, va.off + j, k, f);
 #pragma unroll
-            for (int q = 0; q < L::NC; q++) {
+            for (int q = 0; q < P::CW; q++) {
                 nn += c[q].re * c[q].re + c[q].im * c[q].im;
                 dr += c[q].re * f[q].re + c[q].im * f[q].im;
                 di += c[q].re * f[q].im - c[q].im * f[q].re;
@@ -370,50 +349,69 @@ template <class P>
 __global__ void __launch_bounds__(NT) k_axpby(VecArgs<P> va, double a, const typename P::SElem *x, double b,
                                               typename P::SElem *y)
 {
-    using E = typename P::SElem;
-    using L = El<E>;
-    using R = typename L::R;
-    const long ro = (long)blockIdx.y * va.rs + va.off;
+    using R = typename P::R;
+    const long rb = (long)blockIdx.y * va.rs;
     for (long j = (long)blockIdx.x * NT + threadIdx.x; j < va.n; j += (long)gridDim.x * NT)
-        for (int k = 0; k < P::SPLANES; k++) {
-            long ad = ro + k * va.V + j;
-            cpx<R> c[L::NC], d[L::NC];
-            L::ld(x + ad, c);
-            L::ld(y + ad, d);
+        for (int k = 0; k < P::NCHUNK; k++) {
+            cpx<R> c[P::CW], d[P::CW];
+            P::ld_chunk(x + rb, va.V, va.off + j, k, c);
+            P::ld_chunk(y + rb, va.V, va.off + j, k, d);
 #pragma unroll
-            for (int q = 0; q < L::NC; q++) d[q] = R(a) * c[q] + R(b) * d[q];
-            L::st(y + ad, d);
+            for (int q = 0; q < P::CW; q++) d[q] = R(a) * c[q] + R(b) * d[q];
+            P::st_chunk(y + rb, va.V, va.off + j, k, d);
         }
 }
 
-// FP64 -> FP32 with a per-right-hand-side scale: out = in * scale[r]
-__global__ void __launch_bounds__(NT) k_to32(long V, long off, long n, long rs64, long rs32, const double2 *in,
-                                             float4 *out, const double *scale)
+// FP64 -> storage precision P with a per-right-hand-side scale: out = in * scale[r]
+template <class P>
+__global__ void __launch_bounds__(NT) k_to_low(long V, long off, long n, long rs64, long rsl, const double2 *in,
+                                               typename P::SElem *out, const double *scale)
 {
+    using R = typename P::R;
     const double sc = scale ? scale[blockIdx.y] : 1.0;
+    const double2 *ib = in + (long)blockIdx.y * rs64;
+    typename P::SElem *ob = out + (long)blockIdx.y * rsl;
     for (long j = (long)blockIdx.x * NT + threadIdx.x; j < n; j += (long)gridDim.x * NT)
-        for (int k = 0; k < 6; k++) {
-            double2 a = in[(long)blockIdx.y * rs64 + (2 * k) * V + off + j];
-            double2 b = in[(long)blockIdx.y * rs64 + (2 * k + 1) * V + off + j];
-            out[(long)blockIdx.y * rs32 + k * V + off + j] =
-                make_float4((float)(a.x * sc), (float)(a.y * sc), (float)(b.x * sc), (float)(b.y * sc));
+        for (int k = 0; k < P::NCHUNK; k++) {
+            cpx<R> c[P::CW];
+#pragma unroll
+            for (int q = 0; q < P::CW; q++) {
+                double2 a = ib[(long)(k * P::CW + q) * V + off + j];
+                c[q] = {R(a.x * sc), R(a.y * sc)};
+            }
+            P::st_chunk(ob, V, off + j, k, c);
         }
 }
 
-// x64 += scale[r] * e32
-__global__ void __launch_bounds__(NT) k_add32(long V, long off, long n, long rs64, long rs32, const float4 *e,
-                                              double2 *x, const double *scale)
+// x64 += scale[r] * e (e in storage precision P)
+template <class P>
+__global__ void __launch_bounds__(NT) k_add_low(long V, long off, long n, long rs64, long rsl,
+                                                const typename P::SElem *e, double2 *x, const double *scale)
 {
+    using R = typename P::R;
     const double sc = scale ? scale[blockIdx.y] : 1.0;
+    const typename P::SElem *eb = e + (long)blockIdx.y * rsl;
+    double2 *xb = x + (long)blockIdx.y * rs64;
     for (long j = (long)blockIdx.x * NT + threadIdx.x; j < n; j += (long)gridDim.x * NT)
-        for (int k = 0; k < 6; k++) {
-            float4 v = e[(long)blockIdx.y * rs32 + k * V + off + j];
-            double2 *a = x + (long)blockIdx.y * rs64 + (2 * k) * V + off + j;
-            double2 *b = x + (long)blockIdx.y * rs64 + (2 * k + 1) * V + off + j;
-            double2 av = *a, bv = *b;
-            *a = make_double2(av.x + sc * v.x, av.y + sc * v.y);
-            *b = make_double2(bv.x + sc * v.z, bv.y + sc * v.w);
+        for (int k = 0; k < P::NCHUNK; k++) {
+            cpx<R> c[P::CW];
+            P::ld_chunk(eb, V, off + j, k, c);
+#pragma unroll
+            for (int q = 0; q < P::CW; q++) {
+                double2 *a = xb + (long)(k * P::CW + q) * V + off + j;
+                double2 av = *a;
+                *a = make_double2(av.x + sc * (double)c[q].re, av.y + sc * (double)c[q].im);
+            }
         }
+}
+
+// FP32 link / clover planes -> 16-bit planes of the same order
+template <bool BF> __global__ void k_f32_to_low(long n, const float4 *__restrict__ in, uint2 *out)
+{
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 v = in[i];
+    out[i] = make_uint2(Pack16<BF>::pack(v.x, v.y), Pack16<BF>::pack(v.z, v.w));
 }
 
 // ----------------------------------------------------------------------------- host side
@@ -558,21 +556,41 @@ void Blas<P>::axpby(ddrw_ctx *ctx, const VecRange &vr, double a, const E *x, dou
     k_axpby<P><<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(va, a, x, b, y);
 }
 
-void to32(ddrw_ctx *ctx, const VecRange &vr, long rs32, const double2 *in, float4 *out, const double *scale)
+template <class P>
+void to_low(ddrw_ctx *ctx, const VecRange &vr, long rsl, const double2 *in, typename P::SElem *out,
+            const double *scale)
 {
     ProfScope ps(ctx, PROF_BLAS, 0.0);
     ++ctx->launches;
-    k_to32<<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(vr.V, vr.off, vr.n, vr.rs, rs32, in, out, scale);
+    k_to_low<P><<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(vr.V, vr.off, vr.n, vr.rs, rsl, in, out, scale);
 }
 
-void add32(ddrw_ctx *ctx, const VecRange &vr, long rs32, const float4 *e, double2 *x, const double *scale)
+template <class P>
+void add_low(ddrw_ctx *ctx, const VecRange &vr, long rsl, const typename P::SElem *e, double2 *x, const double *scale)
 {
     ProfScope ps(ctx, PROF_BLAS, 0.0);
     ++ctx->launches;
-    k_add32<<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(vr.V, vr.off, vr.n, vr.rs, rs32, e, x, scale);
+    k_add_low<P><<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(vr.V, vr.off, vr.n, vr.rs, rsl, e, x, scale);
 }
+
+void f32_to_low(ddrw_ctx *ctx, const float4 *in, uint2 *out, long n, bool bf)
+{
+    ++ctx->launches;
+    unsigned g = (unsigned)((n + 255) / 256);
+    if (bf) k_f32_to_low<true><<<g, 256, 0, ctx->stream>>>(n, in, out);
+    else k_f32_to_low<false><<<g, 256, 0, ctx->stream>>>(n, in, out);
+}
+
+#define DDRW_LOW_INST(P)                                                                                      \
+    template void to_low<P>(ddrw_ctx *, const VecRange &, long, const double2 *, P::SElem *, const double *); \
+    template void add_low<P>(ddrw_ctx *, const VecRange &, long, const P::SElem *, double2 *, const double *);
+DDRW_LOW_INST(PrecS)
+DDRW_LOW_INST(PrecH)
+DDRW_LOW_INST(PrecB)
 
 template struct Blas<PrecD>;
 template struct Blas<PrecS>;
+template struct Blas<PrecH>;
+template struct Blas<PrecB>;
 
 }  // namespace ddrw

@@ -6,33 +6,6 @@
 
 namespace ddrw {
 
-// One 16-byte field element as complex numbers in its arithmetic type (double2: 1, float4: 2).
-template <class E> struct El;
-template <> struct El<double2> {
-    using R = double;
-    static constexpr int NC = 1;
-    __device__ static __forceinline__ void ld(const double2 *p, cpx<R> *c)
-    {
-        double2 v = *p;
-        c[0] = {v.x, v.y};
-    }
-    __device__ static __forceinline__ void st(double2 *p, const cpx<R> *c) { *p = make_double2(c[0].re, c[0].im); }
-};
-template <> struct El<float4> {
-    using R = float;
-    static constexpr int NC = 2;
-    __device__ static __forceinline__ void ld(const float4 *p, cpx<R> *c)
-    {
-        float4 v = *p;
-        c[0] = {v.x, v.y};
-        c[1] = {v.z, v.w};
-    }
-    __device__ static __forceinline__ void st(float4 *p, const cpx<R> *c)
-    {
-        *p = make_float4(c[0].re, c[0].im, c[1].re, c[1].im);
-    }
-};
-
 // Krylov scalars of one right-hand side, resident on the device.
 struct KScal {
     double2 rho, alpha, omega, beta;
@@ -64,8 +37,14 @@ template <class P> struct Blas {
     static void axpby(ddrw_ctx *ctx, const VecRange &vr, double a, const E *x, double b, E *y);
 };
 
-// FP64 <-> FP32 fields over a range, with a per-right-hand-side scale (may be null)
-void to32(ddrw_ctx *ctx, const VecRange &vr, long rs32, const double2 *in, float4 *out, const double *scale);
-void add32(ddrw_ctx *ctx, const VecRange &vr, long rs32, const float4 *e, double2 *x, const double *scale);
+// FP64 fields <-> storage precision P (FP32, FP16, BF16) over a range, with a per-right-hand-side
+// scale (may be null); rsl is the field stride of the P fields
+template <class P>
+void to_low(ddrw_ctx *ctx, const VecRange &vr, long rsl, const double2 *in, typename P::SElem *out,
+            const double *scale);
+template <class P>
+void add_low(ddrw_ctx *ctx, const VecRange &vr, long rsl, const typename P::SElem *e, double2 *x, const double *scale);
+// FP32 link / clover planes -> 16-bit planes of the same order (n float4 elements; bf: BF16, else FP16)
+void f32_to_low(ddrw_ctx *ctx, const float4 *in, uint2 *out, long n, bool bf);
 
 }  // namespace ddrw

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "blocksolve.cuh"
+#include "lowprec.cuh"
 
 namespace ddrw {
 
@@ -49,16 +50,10 @@ static void fill_args(ddrw_ctx *ctx, BlkArgs<P> &a, const MassSet &ms, int colou
     for (int k = 0; k < MAXM; k++) {
         int kk = k < nm ? k : nm - 1;
         a.mass4[k] = R(4.0 + ms.m[kk]);
-        if constexpr (sizeof(R) == 8) a.Ainv[k] = (const typename P::CElem *)ms.inv[kk]->A64;
-        else a.Ainv[k] = (const typename P::CElem *)ms.inv[kk]->A32;
+        a.Ainv[k] = (const typename P::CElem *)ainv_for(ms.inv[kk], P::ID);
     }
-    if constexpr (sizeof(R) == 8) {
-        a.U = (const typename P::UElem *)ctx->U64;
-        a.Cl = (const typename P::CElem *)ctx->C64;
-    } else {
-        a.U = (const typename P::UElem *)ctx->U32;
-        a.Cl = (const typename P::CElem *)ctx->C32;
-    }
+    a.U = (const typename P::UElem *)links_for(ctx, P::ID);
+    a.Cl = (const typename P::CElem *)clover_for(ctx, P::ID);
     a.blk0 = colour == DDRW_BLACK ? 0 : ctx->nblk_c;
 }
 
@@ -81,13 +76,49 @@ static ddrw_status colour_norms(ddrw_ctx *ctx, int colour, const double2 *f, int
     return DDRW_OK;
 }
 
+// One inner cycle of the mixed block solve in storage policy P: the colour's sites of rhs, scaled
+// by scale_d[r], go to P's storage, the persistent kernel solves them to tol_inner, and the
+// solution, scaled back by scale_d[nrhs + r], is added to x (zeroed first on the first cycle).
+template <class P>
+static ddrw_status low_cycle(ddrw_ctx *ctx, int colour, const MassSet &ms, const double2 *rhs, double2 *x, bool first,
+                             int nrhs, void *const *w, const double *scale_d, double tol_inner, int maxiter, int *stat)
+{
+    using E = typename P::SElem;
+    const long rs64 = 12 * ctx->V, rsl = P::field_elems(ctx->V);
+    const size_t fl = sizeof(E) * rsl * nrhs;
+    void *bl, *el;
+    ddrw_status st;
+    if ((st = workspace(ctx, "blkl_b", fl, &bl))) return st;
+    if ((st = workspace(ctx, "blkl_e", fl, &el))) return st;
+    for (int p = 0; p < 2; p++) to_low<P>(ctx, colour_range(ctx, colour, p, nrhs, rs64), rsl, rhs, (E *)bl, scale_d);
+    BlkArgs<P> a;
+    a.b = (const E *)bl;
+    a.x = (E *)el;
+    a.r = (E *)w[0]; a.rh = (E *)w[1]; a.p = (E *)w[2];
+    a.v = (E *)w[3]; a.t = (E *)w[4]; a.tmp = (E *)w[5];
+    a.rstride = rsl;
+    a.rpm = (nrhs + std::max(ms.n, 1) - 1) / std::max(ms.n, 1);
+    fill_args(ctx, a, ms, colour);
+    a.tol2 = tol_inner * tol_inner;
+    a.maxiter = maxiter;
+    a.stat = stat;
+    launch_block(ctx, a, nrhs);
+    if (first) zero_colour64(ctx, x, colour, nrhs);
+    for (int p = 0; p < 2; p++) add_low<P>(ctx, colour_range(ctx, colour, p, nrhs, rs64), rsl, (const E *)el, x, scale_d + nrhs);
+    return DDRW_OK;
+}
+
 // x = D_cc(ms)^-1 b on the sites of colour c (FP64 fields, full-field layout, nrhs rhs).
 // Sites of the other colour in x are left untouched.
 ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const double2 *b, double2 *x, int nrhs,
-                          double tol, int maxiter, bool mixed, SolveStats *stats)
+                          double tol, int maxiter, ddrw_prec prec, SolveStats *stats)
 {
-    const long V = ctx->V, rs64 = 12 * V, rs32 = 6 * V;
-    const size_t f64 = sizeof(double2) * rs64 * nrhs, f32 = sizeof(float4) * rs32 * nrhs;
+    const bool mixed = prec != DDRW_FP64;
+    const long V = ctx->V, rs64 = 12 * V;
+    // the inner Krylov vectors: FP64 fields, or the largest low-precision field (FP32)
+    const size_t f64 = sizeof(double2) * rs64 * nrhs, f32 = sizeof(float4) * 6 * V * nrhs;
+    // deepest relative residual an inner solve is asked for: what its storage reliably reaches
+    const double floor = prec == DDRW_MIXED_FP32 ? 1e-6 : prec == DDRW_MIXED_FP16 ? 1e-3 : 5e-3;
     ddrw_status st;
     std::vector<double> bb, rr;
     if ((st = colour_norms(ctx, colour, b, nrhs, bb))) return st;
@@ -104,18 +135,15 @@ ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const do
     const char *names32[6] = {"blk32_r", "blk32_rh", "blk32_p", "blk32_v", "blk32_t", "blk32_tmp"};
     for (int k = 0; k < 6; k++)
         if ((st = workspace(ctx, mixed ? names32[k] : names64[k], mixed ? f32 : f64, &w[k]))) return st;
-    float4 *b32 = nullptr, *e32 = nullptr;
     double *scale_d = nullptr;
     if (mixed) {
-        if ((st = workspace(ctx, "blk32_b", f32, (void **)&b32))) return st;
-        if ((st = workspace(ctx, "blk32_e", f32, (void **)&e32))) return st;
         if ((st = workspace(ctx, "blk_scale", sizeof(double) * 2 * nrhs, (void **)&scale_d))) return st;
     } else {
         if ((st = workspace(ctx, "blk_e64", f64, (void **)&e64))) return st;
     }
-    // tolerance of one inner solve: the target itself in FP64; in FP32 what is still missing to
-    // reach tol (margin 2, worst right-hand side), but no deeper than 1e-6
-    double tol_inner = mixed ? std::max(tol, 1e-6) : tol * 0.5;
+    // tolerance of one inner solve: the target itself in FP64; in low precision what is still
+    // missing to reach tol (margin 2, worst right-hand side), but no deeper than the floor
+    double tol_inner = mixed ? std::max(tol, floor) : tol * 0.5;
     const double2 *rhs = b;  // first cycle: r = b, x = 0
     bool first = true;
     int cycles = 0;
@@ -127,7 +155,7 @@ ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const do
             double need = 1.0;
             for (int r = 0; r < nrhs; r++)
                 if (nr[r] > 0) need = std::min(need, 0.5 * tol * std::sqrt(bb[r] / nr[r]));
-            tol_inner = std::max(1e-6, std::min(need, 0.5));
+            tol_inner = std::max(floor, std::min(need, 0.5));
             for (int r = 0; r < nrhs; r++) {
                 double n = std::sqrt(nr[r]);
                 scale[r] = n > 0 ? 1.0 / n : 0.0;
@@ -136,21 +164,13 @@ ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const do
             DDRW_CUDA_CHECK(cudaMemcpyAsync(scale_d, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
             DDRW_CUDA_CHECK(cudaMemcpyAsync(scale_d + nrhs, unscale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice,
                                             ctx->stream));
-            for (int p = 0; p < 2; p++) to32(ctx, colour_range(ctx, colour, p, nrhs, rs64), rs32, rhs, b32, scale_d);
-            BlkArgs<PrecS> a;
-            a.b = b32;
-            a.x = e32;
-            a.r = (float4 *)w[0]; a.rh = (float4 *)w[1]; a.p = (float4 *)w[2];
-            a.v = (float4 *)w[3]; a.t = (float4 *)w[4]; a.tmp = (float4 *)w[5];
-            a.rstride = rs32;
-            a.rpm = (nrhs + std::max(ms.n, 1) - 1) / std::max(ms.n, 1);
-            fill_args(ctx, a, ms, colour);
-            a.tol2 = tol_inner * tol_inner;
-            a.maxiter = maxiter;
-            a.stat = stat;
-            launch_block(ctx, a, nrhs);
-            if (first) zero_colour64(ctx, x, colour, nrhs);
-            for (int p = 0; p < 2; p++) add32(ctx, colour_range(ctx, colour, p, nrhs, rs64), rs32, e32, x, scale_d + nrhs);
+            if (prec == DDRW_MIXED_FP32)
+                st = low_cycle<PrecS>(ctx, colour, ms, rhs, x, first, nrhs, w, scale_d, tol_inner, maxiter, stat);
+            else if (prec == DDRW_MIXED_FP16)
+                st = low_cycle<PrecH>(ctx, colour, ms, rhs, x, first, nrhs, w, scale_d, tol_inner, maxiter, stat);
+            else
+                st = low_cycle<PrecB>(ctx, colour, ms, rhs, x, first, nrhs, w, scale_d, tol_inner, maxiter, stat);
+            if (st) return st;
         } else {
             BlkArgs<PrecD> a;
             a.b = rhs;

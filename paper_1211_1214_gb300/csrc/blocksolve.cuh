@@ -4,6 +4,7 @@
 
 #include "blas.cuh"
 #include "ctx.h"
+#include "lowprec.cuh"
 #include "stencil.cuh"
 
 namespace ddrw {
@@ -147,9 +148,8 @@ __global__ void __launch_bounds__(NT) k_block_solve(GeomDev g, BlkArgs<P> a)
 {
     using R = typename P::R;
     using E = typename P::SElem;
-    using L = El<E>;
     constexpr int VBH = BlockShape<BL>::VBH;
-    constexpr int NP = P::SPLANES;
+    constexpr int NP = P::NCHUNK, CW = P::CW;
     __shared__ double sm[NT / 32][3];
     // right-hand side fastest: the CTAs of one block run together and share its links in L2
     const int rhs = blockIdx.x;
@@ -167,11 +167,11 @@ __global__ void __launch_bounds__(NT) k_block_solve(GeomDev g, BlkArgs<P> a)
     R bbl = 0;
     for (int h = threadIdx.x; h < VBH; h += NT)
         for (int k = 0; k < NP; k++) {
-            cpx<R> c[L::NC], d[L::NC];
-            L::ld(b + k * V + e0 + h, c);
-            L::ld(b + k * V + o0 + h, d);
+            cpx<R> c[CW], d[CW];
+            P::ld_chunk(b, V, e0 + h, k, c);
+            P::ld_chunk(b, V, o0 + h, k, d);
 #pragma unroll
-            for (int q = 0; q < L::NC; q++)
+            for (int q = 0; q < CW; q++)
                 bbl += c[q].re * c[q].re + c[q].im * c[q].im + d[q].re * d[q].re + d[q].im * d[q].im;
         }
     for (int h = threadIdx.x; h < VBH; h += NT) site_odd<P, BL>(g, o0 + h, nullptr, b, R(0), a.U, Ainv, tmp);
@@ -184,17 +184,16 @@ __global__ void __launch_bounds__(NT) k_block_solve(GeomDev g, BlkArgs<P> a)
     R rl = 0;
     for (int h = threadIdx.x; h < VBH; h += NT)
         for (int k = 0; k < NP; k++) {
-            long ad = k * V + e0 + h;
-            cpx<R> c[L::NC], z[L::NC];
-            L::ld(r + ad, c);
+            cpx<R> c[CW], z[CW];
+            P::ld_chunk(r, V, e0 + h, k, c);
 #pragma unroll
-            for (int q = 0; q < L::NC; q++) {
+            for (int q = 0; q < CW; q++) {
                 rl += c[q].re * c[q].re + c[q].im * c[q].im;
                 z[q] = {R(0), R(0)};
             }
-            L::st(rh + ad, c);
-            L::st(p + ad, c);
-            L::st(x + ad, z);
+            P::st_chunk(rh, V, e0 + h, k, c);
+            P::st_chunk(p, V, e0 + h, k, c);
+            P::st_chunk(x, V, e0 + h, k, z);
         }
     red[0] = (double)rl;
     cta_sum<3, NT>(red, sm);
@@ -223,13 +222,12 @@ __global__ void __launch_bounds__(NT) k_block_solve(GeomDev g, BlkArgs<P> a)
         // s = r - alpha v (in r)
         for (int h = threadIdx.x; h < VBH; h += NT)
             for (int k = 0; k < NP; k++) {
-                long ad = k * V + e0 + h;
-                cpx<R> c[L::NC], d[L::NC];
-                L::ld(r + ad, c);
-                L::ld(v + ad, d);
+                    cpx<R> c[CW], d[CW];
+                P::ld_chunk(r, V, e0 + h, k, c);
+                P::ld_chunk(v, V, e0 + h, k, d);
 #pragma unroll
-                for (int q = 0; q < L::NC; q++) c[q] = c[q] - cmul(al, d[q]);
-                L::st(r + ad, c);
+                for (int q = 0; q < CW; q++) c[q] = c[q] - cmul(al, d[q]);
+                P::st_chunk(r, V, e0 + h, k, c);
             }
         __syncthreads();
         // t = S s  and  (t, s), (t, t)
@@ -253,15 +251,14 @@ __global__ void __launch_bounds__(NT) k_block_solve(GeomDev g, BlkArgs<P> a)
         R hre = 0, him = 0, rrl = 0;
         for (int h = threadIdx.x; h < VBH; h += NT)
             for (int k = 0; k < NP; k++) {
-                long ad = k * V + e0 + h;
-                cpx<R> xv[L::NC], pv[L::NC], sv[L::NC], tv[L::NC], hv[L::NC];
-                L::ld(x + ad, xv);
-                L::ld(p + ad, pv);
-                L::ld(r + ad, sv);
-                L::ld(t + ad, tv);
-                L::ld(rh + ad, hv);
+                    cpx<R> xv[CW], pv[CW], sv[CW], tv[CW], hv[CW];
+                P::ld_chunk(x, V, e0 + h, k, xv);
+                P::ld_chunk(p, V, e0 + h, k, pv);
+                P::ld_chunk(r, V, e0 + h, k, sv);
+                P::ld_chunk(t, V, e0 + h, k, tv);
+                P::ld_chunk(rh, V, e0 + h, k, hv);
 #pragma unroll
-                for (int q = 0; q < L::NC; q++) {
+                for (int q = 0; q < CW; q++) {
                     xv[q] = xv[q] + cmul(al, pv[q]) + cmul(om, sv[q]);
                     sv[q] = sv[q] - cmul(om, tv[q]);
                     cpx<R> z = cmulc(hv[q], sv[q]);
@@ -269,8 +266,8 @@ __global__ void __launch_bounds__(NT) k_block_solve(GeomDev g, BlkArgs<P> a)
                     him += z.im;
                     rrl += sv[q].re * sv[q].re + sv[q].im * sv[q].im;
                 }
-                L::st(x + ad, xv);
-                L::st(r + ad, sv);
+                P::st_chunk(x, V, e0 + h, k, xv);
+                P::st_chunk(r, V, e0 + h, k, sv);
             }
         red[0] = (double)hre;
         red[1] = (double)him;
@@ -293,14 +290,13 @@ __global__ void __launch_bounds__(NT) k_block_solve(GeomDev g, BlkArgs<P> a)
         // p = r + beta (p - omega v)
         for (int h = threadIdx.x; h < VBH; h += NT)
             for (int k = 0; k < NP; k++) {
-                long ad = k * V + e0 + h;
-                cpx<R> pv[L::NC], rv[L::NC], vv[L::NC];
-                L::ld(p + ad, pv);
-                L::ld(r + ad, rv);
-                L::ld(v + ad, vv);
+                    cpx<R> pv[CW], rv[CW], vv[CW];
+                P::ld_chunk(p, V, e0 + h, k, pv);
+                P::ld_chunk(r, V, e0 + h, k, rv);
+                P::ld_chunk(v, V, e0 + h, k, vv);
 #pragma unroll
-                for (int q = 0; q < L::NC; q++) pv[q] = rv[q] + cmul(be, pv[q] - cmul(om, vv[q]));
-                L::st(p + ad, pv);
+                for (int q = 0; q < CW; q++) pv[q] = rv[q] + cmul(be, pv[q] - cmul(om, vv[q]));
+                P::st_chunk(p, V, e0 + h, k, pv);
             }
         __syncthreads();
     }
@@ -320,7 +316,7 @@ void launch_block_kernel(ddrw_ctx *ctx, const BlkArgs<P> &a, int nrhs)
     dim3 grid((unsigned)nrhs, (unsigned)ctx->nblk_c);
     constexpr int VBH = BlockShape<BL>::VBH;
     constexpr int NT = VBH <= 32 ? 32 : (VBH <= 128 ? 128 : 256);
-    ProfScope ps(ctx, sizeof(typename P::R) == 8 ? PROF_BLOCK64 : PROF_BLOCK32, 0.0);
+    ProfScope ps(ctx, P::ID == 64 ? PROF_BLOCK64 : P::ID == 32 ? PROF_BLOCK32 : PROF_BLOCK16, 0.0);
     ++ctx->launches;
     k_block_solve<P, BL, NT><<<grid, NT, 0, ctx->stream>>>(g, a);
 }

@@ -1,0 +1,6 @@
+// one instantiation of the persistent block solver (see blocksolve.cuh)
+#include "blocksolve.cuh"
+
+namespace ddrw {
+template void launch_block_kernel<PrecB, 8>(ddrw_ctx *ctx, const BlkArgs<PrecB> &a, int nrhs);
+}

@@ -25,7 +25,16 @@ struct MassInv {
     double m;
     double2 *A64 = nullptr;  // [2][18][V]
     float4 *A32 = nullptr;   // [2][9][V]
+    uint2 *A16 = nullptr;    // [2][9][V] FP16
+    uint2 *Ab16 = nullptr;   // [2][9][V] BF16
 };
+
+// the in-block inverse of mass slot m in the storage of policy id (64, 32, 16 = FP16, 17 = BF16)
+inline const void *ainv_for(const MassInv *m, int id)
+{
+    return id == 64 ? (const void *)m->A64 : id == 32 ? (const void *)m->A32 : id == 16 ? (const void *)m->A16
+                                                                                     : (const void *)m->Ab16;
+}
 
 // an instantiated Krylov-loop graph (solver.cu)
 struct GraphEntry {
@@ -35,7 +44,8 @@ struct GraphEntry {
 
 // a tuned stencil launch configuration
 struct TuneEntry {
-    int nr, nt;
+    int nr, nt, nw, roll;  // right-hand sides per thread, sites per CTA row, right-hand-side groups
+                           // per CTA, rolled hop bodies
     float ms;
 };
 
@@ -89,6 +99,10 @@ struct ddrw_ctx {
     float4 *U32 = nullptr;   // [4][3][V] two-row
     double2 *C64 = nullptr;  // [2][18][V]
     float4 *C32 = nullptr;   // [2][9][V]
+    uint2 *U16 = nullptr;    // [4][3][V] two-row FP16
+    uint2 *Ub16 = nullptr;   // [4][3][V] two-row BF16
+    uint2 *C16 = nullptr;    // [2][9][V] FP16
+    uint2 *Cb16 = nullptr;   // [2][9][V] BF16
     float4 *Udd = nullptr;   // [4][9][V] links split into FP32 pairs (double-single stencil)
     float4 *Cdd = nullptr;   // [2][18][V] clover split into FP32 pairs
     std::deque<ddrw::MassInv> inv;  // deque: MassInv addresses stay valid as entries are added
@@ -103,8 +117,9 @@ struct ddrw_ctx {
     long graph_launches = 0;
     std::map<std::array<uintptr_t, 24>, ddrw::GraphEntry> graphs;
 
-    // stencil autotuner (dslash_tune.cu)
+    // stencil autotuner (dslash_tune.cu); pinned_nr > 0 overrides it with the pinned configuration
     bool autotune = true;
+    int pinned_nr = 0, pinned_nt = 128, pinned_nw = 1, pinned_roll = 0;
     std::map<std::array<int, 8>, ddrw::TuneEntry> tune;
 
     // kernel timing (ddrw_profile): CUDA events around the instrumented launches
@@ -135,7 +150,10 @@ enum {
     PROF_BLOCK32 = 5,       // persistent block solver, FP32
     PROF_BLAS = 6,          // Krylov vector kernels and reductions
     PROF_DSLASH_DS = 7,     // double-single residual stencil (mixed path)
-    PROF_NKIND = 8
+    PROF_DSLASH16 = 8,      // 16-bit storage (FP16 or BF16) stencil, all hops
+    PROF_DSLASH16_BLK = 9,  // 16-bit storage stencil, block-restricted hops
+    PROF_BLOCK16 = 10,      // persistent block solver on 16-bit storage
+    PROF_NKIND = 11
 };
 
 // Records CUDA events around the launches in its scope when profiling is on.
@@ -177,6 +195,29 @@ void unpack_spinor64(ddrw_ctx *ctx, const double2 *f, double *user, int nrhs);
 void pack_P64(ddrw_ctx *ctx, const double2 *f, double *packed, int nrhs);
 void unpack_P64(ddrw_ctx *ctx, const double *packed, double2 *f, int nrhs);  // zero outside supp P
 
+// links and clover term in the storage of policy id (128 = double-single split, 64, 32, 16 = FP16,
+// 17 = BF16)
+inline const void *links_for(const ddrw_ctx *ctx, int id)
+{
+    switch (id) {
+    case 128: return ctx->Udd;
+    case 64: return ctx->U64;
+    case 32: return ctx->U32;
+    case 16: return ctx->U16;
+    default: return ctx->Ub16;
+    }
+}
+inline const void *clover_for(const ddrw_ctx *ctx, int id)
+{
+    switch (id) {
+    case 128: return ctx->Cdd;
+    case 64: return ctx->C64;
+    case 32: return ctx->C32;
+    case 16: return ctx->C16;
+    default: return ctx->Cb16;
+    }
+}
+
 void pack_gauge(ddrw_ctx *ctx, const double *Ulex);  // fills U64 and U32
 void build_clover(ddrw_ctx *ctx);                    // fills C64 and C32 from U64
 void build_inverse(ddrw_ctx *ctx, double m, MassInv &mi);
@@ -201,6 +242,8 @@ struct DslashCall {
 };
 void dslash64(ddrw_ctx *ctx, const DslashCall &c);
 void dslash32(ddrw_ctx *ctx, const DslashCall &c);
+void dslash16(ddrw_ctx *ctx, const DslashCall &c);   // FP16 storage, FP32 arithmetic
+void dslashb16(ddrw_ctx *ctx, const DslashCall &c);  // BF16 storage, FP32 arithmetic
 // double-single stencil: in / x are split fields (float4 per complex), out an FP64 field
 void dslash_ds(ddrw_ctx *ctx, const DslashCall &c);
 // FP64 -> split elements at k V + p vh + off + j (k < 12 planes, parities p = par0 .. par0 + npar - 1,
@@ -213,7 +256,7 @@ ddrw_status residual_stencil(ddrw_ctx *ctx, DslashCall c, bool ds);
 
 // x = D_cc(ms)^-1 b on the sites of colour c (persistent block solver + FP64 defect correction)
 ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const double2 *b, double2 *x, int nrhs,
-                          double tol, int maxiter, bool mixed, SolveStats *stats);
+                          double tol, int maxiter, ddrw_prec prec, SolveStats *stats);
 // x = D(ms)^-1 b on the full lattice (even-odd BiCGStab + FP64 defect correction)
 ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, double2 *x, int nrhs, double tol,
                          int maxiter, ddrw_prec prec, SolveStats *stats);

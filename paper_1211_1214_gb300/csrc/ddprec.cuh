@@ -58,6 +58,8 @@ __device__ __forceinline__ bool operator!=(dd a, dd b) { return a.hi != b.hi || 
 struct PrecDD {
     using R = dd;
     using SElem = float4;  // one complex number (re.hi, re.lo, im.hi, im.lo)
+    static constexpr int ID = 128;
+    static constexpr double SBYTES = 192, UBYTES = 144, CBYTES = 576;
     static constexpr int SPLANES = 12;
     static constexpr int UPLANES = 9;
     static constexpr int CPLANES = 36;

@@ -235,15 +235,31 @@ __device__ __forceinline__ void link_dag_mul(const Link<R> &U, const Half<R> &h,
 // A policy P gives the arithmetic type P::R and how spinors, links and clover blocks are stored.
 //   PrecD: FP64 everything, full 3x3 links (9 double2 planes per direction), clover 36 double2.
 //   PrecS: FP32 spinors (6 float4 planes), two-row links (3 float4 planes), clover 18 float4.
+//   PrecH / PrecB (lowprec.cuh): FP16 / BF16 storage with per-site norms, FP32 arithmetic.
+// BLAS kernels reach a field through ld_chunk / st_chunk: NCHUNK chunks of CW complex numbers per
+// site (a 16-bit site is one chunk, because its norm covers all 12 components).
 
 struct PrecD {
     using R = double;
     using SElem = double2;
+    static constexpr int ID = 64;
     static constexpr int SPLANES = 12;
     static constexpr int UPLANES = 9;   // per direction
     static constexpr int CPLANES = 36;  // per site, both chiralities
+    static constexpr double SBYTES = 192, UBYTES = 144, CBYTES = 576;  // spinor, link, clover
+    static constexpr int NCHUNK = 12, CW = 1;  // BLAS granularity: one element of one complex
     using UElem = double2;
     using CElem = double2;
+    __host__ __device__ static long field_elems(long V) { return SPLANES * V; }
+    __device__ static __forceinline__ void ld_chunk(const SElem *f, long V, long s, int k, cpx<R> *c)
+    {
+        double2 v = f[k * V + s];
+        c[0] = {v.x, v.y};
+    }
+    __device__ static __forceinline__ void st_chunk(SElem *f, long V, long s, int k, const cpx<R> *c)
+    {
+        f[k * V + s] = make_double2(c[0].re, c[0].im);
+    }
 
     // in-field offsets are 32-bit (k * stride + s < 2^31: at most 2^27 sites)
     __device__ static __forceinline__ void load_spinor(const SElem *__restrict__ f, int stride, int s, Spinor<R> &p)
@@ -301,11 +317,25 @@ struct PrecD {
 struct PrecS {
     using R = float;
     using SElem = float4;
+    static constexpr int ID = 32;
     static constexpr int SPLANES = 6;
     static constexpr int UPLANES = 3;
     static constexpr int CPLANES = 18;
+    static constexpr double SBYTES = 96, UBYTES = 48, CBYTES = 288;
+    static constexpr int NCHUNK = 6, CW = 2;
     using UElem = float4;
     using CElem = float4;
+    __host__ __device__ static long field_elems(long V) { return SPLANES * V; }
+    __device__ static __forceinline__ void ld_chunk(const SElem *f, long V, long s, int k, cpx<R> *c)
+    {
+        float4 v = f[k * V + s];
+        c[0] = {v.x, v.y};
+        c[1] = {v.z, v.w};
+    }
+    __device__ static __forceinline__ void st_chunk(SElem *f, long V, long s, int k, const cpx<R> *c)
+    {
+        f[k * V + s] = make_float4(c[0].re, c[0].im, c[1].re, c[1].im);
+    }
 
     __device__ static __forceinline__ void load_spinor(const SElem *__restrict__ f, int stride, int s, Spinor<R> &p)
     {

@@ -22,6 +22,7 @@
 
 #include "ctx.h"
 #include "ddprec.cuh"
+#include "lowprec.cuh"
 #include "stencil.cuh"
 
 namespace ddrw {
@@ -41,13 +42,15 @@ template <class P> struct DsArgs {
     const typename P::CElem *Ainv[MAXM];  // A(m)^-1 per slot
 };
 
-template <class P, int BL, int HOPSEL, int NR>
+template <class P, int BL, int HOPSEL, int NR, int ROLL = 0>
 __global__ void __launch_bounds__(256) k_dslash(GeomDev g, DsArgs<P> a)
 {
     using R = typename P::R;
-    const int ngrp = a.nrhs / NR;
-    const int grp = blockIdx.x % ngrp;
-    const long tile = blockIdx.x / ngrp;
+    // groups of NR right-hand sides; a CTA holds blockDim.y groups (one per row of threads) of
+    // the same site tile, so its rows share the tile's links and clover terms in L1
+    const int ncg = a.nrhs / (NR * (int)blockDim.y);
+    const int grp = (blockIdx.x % ncg) * blockDim.y + threadIdx.y;
+    const long tile = blockIdx.x / ncg;
     const long nper = (long)a.nblk * BlockShape<BL>::VBH;
     const long i = tile * blockDim.x + threadIdx.x;
     if (i >= nper * a.npar) return;
@@ -63,10 +66,14 @@ __global__ void __launch_bounds__(256) k_dslash(GeomDev g, DsArgs<P> a)
     for (int r = 0; r < NR; r++) zero(acc[r]);
     if (a.beta != R(0)) {
         const typename P::SElem *in = a.in + roff;
-        hop_dir_multi<P, BL, HOPSEL, 0, NR>(g, st, s, in, a.rstride, a.U, acc);
-        hop_dir_multi<P, BL, HOPSEL, 1, NR>(g, st, s, in, a.rstride, a.U, acc);
-        hop_dir_multi<P, BL, HOPSEL, 2, NR>(g, st, s, in, a.rstride, a.U, acc);
-        hop_dir_multi<P, BL, HOPSEL, 3, NR>(g, st, s, in, a.rstride, a.U, acc);
+        if constexpr (ROLL) {
+            hop_multi_rolled<P, BL, HOPSEL, NR>(g, st, (int)s, in, a.rstride, a.U, acc);
+        } else {
+            hop_dir_multi<P, BL, HOPSEL, 0, NR>(g, st, s, in, a.rstride, a.U, acc);
+            hop_dir_multi<P, BL, HOPSEL, 1, NR>(g, st, s, in, a.rstride, a.U, acc);
+            hop_dir_multi<P, BL, HOPSEL, 2, NR>(g, st, s, in, a.rstride, a.U, acc);
+            hop_dir_multi<P, BL, HOPSEL, 3, NR>(g, st, s, in, a.rstride, a.U, acc);
+        }
 #pragma unroll
         for (int r = 0; r < NR; r++) scale(acc[r], a.beta);
     }
@@ -115,7 +122,9 @@ __global__ void __launch_bounds__(256) k_dslash(GeomDev g, DsArgs<P> a)
 // launch configuration of one stencil launch
 struct DsConfig {
     int nr = 1;    // right-hand sides per thread
-    int nt = 128;  // threads per CTA
+    int nt = 128;  // sites per CTA (threads per CTA row)
+    int nw = 1;    // CTA rows: groups of nr right-hand sides per CTA (nt * nw <= 256)
+    int roll = 0;  // 1: forward and backward hops share the direction bodies (smaller code)
 };
 
 template <class P, int BL>
@@ -143,16 +152,8 @@ DsArgs<P> make_args(ddrw_ctx *ctx, const DslashCall &c)
         a.mass4[k] = R(4.0 + c.masses[kk]);
         a.Ainv[k] = (const typename P::CElem *)c.Ainv[kk];
     }
-    if constexpr (std::is_same<P, PrecDD>::value) {
-        a.U = (const typename P::UElem *)ctx->Udd;
-        a.Cl = (const typename P::CElem *)ctx->Cdd;
-    } else if constexpr (sizeof(R) == 8) {
-        a.U = (const typename P::UElem *)ctx->U64;
-        a.Cl = (const typename P::CElem *)ctx->C64;
-    } else {
-        a.U = (const typename P::UElem *)ctx->U32;
-        a.Cl = (const typename P::CElem *)ctx->C32;
-    }
+    a.U = (const typename P::UElem *)links_for(ctx, P::ID);
+    a.Cl = (const typename P::CElem *)clover_for(ctx, P::ID);
     return a;
 }
 
@@ -161,23 +162,29 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
 {
     GeomDev g = geom_dev(ctx);
     long n = (long)c.npar * c.nblk * BlockShape<BL>::VBH;
-    unsigned grid = (unsigned)(((n + cfg.nt - 1) / cfg.nt) * (c.nrhs / cfg.nr));
+    // launches that are not tuned (block-restricted hops, double-single) take one row
+    if (c.hopsel != 0 || std::is_same<P, PrecDD>::value) cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
+    unsigned grid = (unsigned)(((n + cfg.nt - 1) / cfg.nt) * (c.nrhs / (cfg.nr * cfg.nw)));
+    dim3 blk((unsigned)cfg.nt, (unsigned)cfg.nw);
     ++ctx->launches;
     if constexpr (std::is_same<P, PrecDD>::value) {  // one right-hand side per thread
-        if (c.hopsel == 0) k_dslash<P, BL, 0, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
-        else if (c.hopsel == 1) k_dslash<P, BL, 1, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
-        else k_dslash<P, BL, 2, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
+        if (c.hopsel == 0) k_dslash<P, BL, 0, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
+        else if (c.hopsel == 1) k_dslash<P, BL, 1, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
+        else k_dslash<P, BL, 2, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
     } else {
         if (c.hopsel == 0) {
-            switch (cfg.nr) {
-            case 4: k_dslash<P, BL, 0, 4><<<grid, cfg.nt, 0, ctx->stream>>>(g, a); break;
-            case 2: k_dslash<P, BL, 0, 2><<<grid, cfg.nt, 0, ctx->stream>>>(g, a); break;
-            default: k_dslash<P, BL, 0, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a); break;
+            switch (cfg.nr * 2 + cfg.roll) {
+            case 8: k_dslash<P, BL, 0, 4><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 9: k_dslash<P, BL, 0, 4, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 4: k_dslash<P, BL, 0, 2><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 5: k_dslash<P, BL, 0, 2, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 3: k_dslash<P, BL, 0, 1, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            default: k_dslash<P, BL, 0, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
             }
         } else if (c.hopsel == 1) {
-            k_dslash<P, BL, 1, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
+            k_dslash<P, BL, 1, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
         } else {
-            k_dslash<P, BL, 2, 1><<<grid, cfg.nt, 0, ctx->stream>>>(g, a);
+            k_dslash<P, BL, 2, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
         }
     }
 }
@@ -188,8 +195,7 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
 template <class P>
 double compulsory_bytes(const DslashCall &c, long n)
 {
-    const double S = sizeof(typename P::SElem) * P::SPLANES, Lk = sizeof(typename P::UElem) * P::UPLANES,
-                 Cb = sizeof(typename P::CElem) * P::CPLANES;
+    const double S = P::SBYTES, Lk = P::UBYTES, Cb = P::CBYTES;
     double per = S * c.nrhs * ((c.beta != 0.0) + 1 + (c.diag != 0));
     if (c.beta != 0.0) per += (c.npar == 1 ? 8.0 : 4.0) * Lk;
     if (c.diag == 1) per += Cb;
@@ -215,8 +221,10 @@ void launch_bl(ddrw_ctx *ctx, const DslashCall &c)
     DsConfig cfg;
     constexpr bool split = std::is_same<P, PrecDD>::value;
     if constexpr (!split)
-        if (c.hopsel == 0) cfg = tuned_config(ctx, c, sizeof(R) == 8 ? 64 : 32, BL, &run_cfg<P, BL>);
-    int kind = split ? PROF_DSLASH_DS : (sizeof(R) == 8 ? PROF_DSLASH64 : PROF_DSLASH32) + (c.hopsel != 0 ? 2 : 0);
+        if (c.hopsel == 0) cfg = tuned_config(ctx, c, P::ID, BL, &run_cfg<P, BL>);
+    int kind = split ? PROF_DSLASH_DS
+                     : P::ID < 32 ? PROF_DSLASH16 + (c.hopsel != 0)
+                                  : (sizeof(R) == 8 ? PROF_DSLASH64 : PROF_DSLASH32) + (c.hopsel != 0 ? 2 : 0);
     ProfScope ps(ctx, kind, compulsory_bytes<P>(c, n));
     launch_cfg<P, BL>(ctx, c, make_args<P, BL>(ctx, c), cfg);
 }

@@ -3,8 +3,10 @@
 // For each launch shape (precision, block length, parities, right-hand sides, diagonal and
 // post-multiply modes, right-hand sides per mass slot) the first launch times every candidate
 // configuration -- right-hand sides per thread NR in {1, 2, 4} (dividing the right-hand sides per
-// mass slot) and CTA sizes {64, 128, 256} -- with CUDA events on the context's stream, keeps the
-// fastest, and reuses it for every later launch of that shape.  The candidates run on the real
+// mass slot), sites per CTA row in {64, 128, 256}, CTA rows (groups of NR right-hand sides of the
+// same sites, sharing links and clover terms in L1) in {1, 2}, at most 256 threads per CTA, and
+// unrolled or rolled hop bodies -- with CUDA events on the context's stream, keeps the fastest,
+// and reuses it for every later launch of that shape.  The candidates run on the real
 // arguments: a stencil launch never reads its own output sites, so repeating it is harmless.
 // While the stream is being captured into a graph nothing is timed and the default is used.
 #include <cstdio>
@@ -19,9 +21,14 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
 {
     const int nm = c.nmass < 1 ? 1 : c.nmass;
     const int rpm = (c.nrhs + nm - 1) / nm;
+    if (ctx->pinned_nr > 0) {
+        DsConfig p{ctx->pinned_nr, ctx->pinned_nt, ctx->pinned_nw, ctx->pinned_roll};
+        if (c.nrhs % (p.nr * p.nw) || rpm % (p.nr * p.nw)) p.nr = 1, p.nw = 1;
+        return p;
+    }
     std::array<int, 8> key = {prec, bl, c.npar, c.nrhs, c.diag, c.post, rpm, c.beta != 0.0};
     auto it = ctx->tune.find(key);
-    if (it != ctx->tune.end()) return DsConfig{it->second.nr, it->second.nt};
+    if (it != ctx->tune.end()) return DsConfig{it->second.nr, it->second.nt, it->second.nw, it->second.roll};
 
     DsConfig def;
     def.nr = (rpm % 2 == 0 && c.nrhs % 2 == 0) ? 2 : 1;
@@ -29,7 +36,7 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(ctx->stream, &cs);
     if (!ctx->autotune || cs != cudaStreamCaptureStatusNone) {
-        if (cs == cudaStreamCaptureStatusNone) ctx->tune[key] = TuneEntry{def.nr, def.nt, -1.0f};
+        if (cs == cudaStreamCaptureStatusNone) ctx->tune[key] = TuneEntry{def.nr, def.nt, def.nw, def.roll, -1.0f};
         return def;
     }
     cudaEvent_t e0, e1;
@@ -37,11 +44,14 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
     cudaEventCreate(&e1);
     DsConfig best = def;
     float best_ms = 1e30f;
-    const int nrs[3] = {1, 2, 4}, nts[3] = {64, 128, 256};
+    const int nrs[3] = {1, 2, 4}, nts[3] = {64, 128, 256}, nws[2] = {1, 2};
+    for (int roll = 0; roll < 2; roll++)
     for (int nr : nrs) {
         if (c.nrhs % nr || rpm % nr) continue;
+        for (int nw : nws)
         for (int nt : nts) {
-            DsConfig cfg{nr, nt};
+            if ((c.nrhs / nr) % nw || nt * nw > 256) continue;
+            DsConfig cfg{nr, nt, nw, roll};
             run(ctx, c, cfg);  // warm
             cudaEventRecord(e0, ctx->stream);
             run(ctx, c, cfg);
@@ -58,7 +68,7 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->tune[key] = TuneEntry{best.nr, best.nt, best_ms / 2};
+    ctx->tune[key] = TuneEntry{best.nr, best.nt, best.nw, best.roll, best_ms / 2};
     return best;
 }
 
@@ -76,6 +86,23 @@ ddrw_status ddrw_autotune(ddrw_ctx *ctx, int enable)
     return DDRW_OK;
 }
 
+ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll)
+{
+    if (!ctx) return DDRW_EINVAL;
+    if (nr == 0) {
+        ctx->pinned_nr = 0;
+        return DDRW_OK;
+    }
+    if ((nr != 1 && nr != 2 && nr != 4) || nt < 32 || nt > 256 || nt % 32 || nw < 1 || nt * nw > 256 ||
+        (roll != 0 && roll != 1))
+        return set_error(ctx, DDRW_EINVAL, "bad stencil configuration");
+    ctx->pinned_nr = nr;
+    ctx->pinned_nt = nt;
+    ctx->pinned_nw = nw;
+    ctx->pinned_roll = roll;
+    return DDRW_OK;
+}
+
 ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len)
 {
     if (!ctx || !buf || len <= 0) return DDRW_EINVAL;
@@ -83,8 +110,10 @@ ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len)
     for (auto &kv : ctx->tune) {
         const auto &k = kv.first;
         char line[200];
-        snprintf(line, sizeof line, "fp%d l=%d npar=%d nrhs=%d diag=%d post=%d rpm=%d hop=%d -> nr=%d nt=%d ms=%.4f\n", k[0],
-                 k[1], k[2], k[3], k[4], k[5], k[6], k[7], kv.second.nr, kv.second.nt, kv.second.ms);
+        snprintf(line, sizeof line,
+                 "fp%d l=%d npar=%d nrhs=%d diag=%d post=%d rpm=%d hop=%d -> nr=%d nt=%d nw=%d roll=%d ms=%.4f\n", k[0],
+                 k[1], k[2], k[3], k[4], k[5], k[6], k[7], kv.second.nr, kv.second.nt, kv.second.nw, kv.second.roll,
+                 kv.second.ms);
         s += line;
     }
     if ((long)s.size() + 1 > len) return set_error(ctx, DDRW_EINVAL, "report buffer too small");

@@ -176,19 +176,19 @@ static ddrw_status apply_dA_fields(ddrw_ctx *ctx, const MassSet &m2s, const Mass
     ddrw_status st;
     DDRW_CUDA_CHECK(cudaMemsetAsync(u, 0, fb, ctx->stream));
     hop_between(ctx, DDRW_WHITE, eta, u, nrhs);  // u = D_wb eta
-    if ((st = block_solve64(ctx, DDRW_WHITE, m2s, u, a2, nrhs, ctx->tol_block, ctx->maxiter, mixed, stats))) return st;
-    if ((st = block_solve64(ctx, DDRW_WHITE, m1s, a2, a12, nrhs, ctx->tol_block, ctx->maxiter, mixed, stats))) return st;
+    if ((st = block_solve64(ctx, DDRW_WHITE, m2s, u, a2, nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, stats))) return st;
+    if ((st = block_solve64(ctx, DDRW_WHITE, m1s, a2, a12, nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, stats))) return st;
     // c = D_bw a12 (into u, black rows), c2 = D_bw a2
     DDRW_CUDA_CHECK(cudaMemsetAsync(u, 0, fb, ctx->stream));
     DDRW_CUDA_CHECK(cudaMemsetAsync(c2, 0, fb, ctx->stream));
     hop_between(ctx, DDRW_BLACK, a12, u, nrhs);
     hop_between(ctx, DDRW_BLACK, a2, c2, nrhs);
     // t = D_bb(m2)^-1 c2 (into a2); w = c + t (into u)
-    if ((st = block_solve64(ctx, DDRW_BLACK, m2s, c2, a2, nrhs, ctx->tol_block, ctx->maxiter, mixed, stats))) return st;
+    if ((st = block_solve64(ctx, DDRW_BLACK, m2s, c2, a2, nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, stats))) return st;
     Blas<PrecD>::axpby(ctx, VecRange{ctx->V, 0, ctx->V, 12 * ctx->V, nrhs}, 1.0, a2, 1.0, u);
     // r = dm P D_bb(m1)^-1 w
     DDRW_CUDA_CHECK(cudaMemsetAsync(r, 0, fb, ctx->stream));
-    if ((st = block_solve64(ctx, DDRW_BLACK, m1s, u, r, nrhs, ctx->tol_block, ctx->maxiter, mixed, stats))) return st;
+    if ((st = block_solve64(ctx, DDRW_BLACK, m1s, u, r, nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, stats))) return st;
     double *dm;
     if ((st = workspace(ctx, "est_dm", sizeof(double) * MAXM, (void **)&dm))) return st;
     double hdm[MAXM];
@@ -604,10 +604,10 @@ ddrw_status ddrw_apply_schur(ddrw_ctx *ctx, double m, const double *in, double *
     // A v = v - P D_bb^-1 D_bw D_ww^-1 D_wb v
     DDRW_CUDA_CHECK(cudaMemsetAsync(F[1], 0, fb, ctx->stream));
     hop_between(ctx, DDRW_WHITE, F[0], F[1], nrhs);
-    if ((st = block_solve64(ctx, DDRW_WHITE, ms, F[1], F[2], nrhs, ctx->tol_block, ctx->maxiter, mixed, nullptr))) return st;
+    if ((st = block_solve64(ctx, DDRW_WHITE, ms, F[1], F[2], nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, nullptr))) return st;
     DDRW_CUDA_CHECK(cudaMemsetAsync(F[1], 0, fb, ctx->stream));
     hop_between(ctx, DDRW_BLACK, F[2], F[1], nrhs);
-    if ((st = block_solve64(ctx, DDRW_BLACK, ms, F[1], F[3], nrhs, ctx->tol_block, ctx->maxiter, mixed, nullptr))) return st;
+    if ((st = block_solve64(ctx, DDRW_BLACK, ms, F[1], F[3], nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, nullptr))) return st;
     GeomDev g = geom_dev(ctx);
     dim3 grid((unsigned)((ctx->V + 127) / 128), (unsigned)nrhs);
     DISPATCH_BL(ctx, k_delta, grid, 128, g, F[0], F[3], F[1], 12 * ctx->V);
@@ -638,7 +638,7 @@ ddrw_status ddrw_solve_block(ddrw_ctx *ctx, int colour, double m, const double *
     pack_spinor64(ctx, (const double *)din, F[0], nrhs);
     DDRW_CUDA_CHECK(cudaMemsetAsync(F[1], 0, sizeof(double2) * 12 * ctx->V * nrhs, ctx->stream));
     SolveStats stats;
-    st = block_solve64(ctx, colour, ms, F[0], F[1], nrhs, ctx->tol_block, ctx->maxiter, ctx->prec != DDRW_FP64, &stats);
+    st = block_solve64(ctx, colour, ms, F[0], F[1], nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, &stats);
     if (st && st != DDRW_ENOCONV) return st;
     ddrw_status conv = st;
     unpack_spinor64(ctx, F[1], (double *)dout, nrhs);

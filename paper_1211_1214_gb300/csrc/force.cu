@@ -473,7 +473,7 @@ extern "C" ddrw_status ddrw_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64
     // two mass slots (m1: v = eta, m2: v = y) of the four block solves
     auto bsolve = [&](int colour, const double2 *b, double2 *x) -> ddrw_status {
         DDRW_CUDA_CHECK(cudaMemsetAsync(x, 0, f2, ctx->stream));
-        ddrw_status s2 = block_solve64(ctx, colour, m12, b, x, R2, ctx->tol_block, ctx->maxiter, mixed, &stats);
+        ddrw_status s2 = block_solve64(ctx, colour, m12, b, x, R2, ctx->tol_block, ctx->maxiter, ctx->prec, &stats);
         if (s2 == DDRW_ENOCONV) conv = s2;
         else if (s2) return s2;
         return DDRW_OK;

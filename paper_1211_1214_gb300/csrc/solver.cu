@@ -15,11 +15,13 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
 #include "blas.cuh"
 #include "ctx.h"
+#include "lowprec.cuh"
 
 namespace ddrw {
 
@@ -49,8 +51,12 @@ __global__ void k_bicg_cond(cudaGraphConditionalHandle h, const KScal *sc, int n
 
 template <class P> void stencil(ddrw_ctx *ctx, const DslashCall &c)
 {
-    if constexpr (sizeof(typename P::R) == 8) dslash64(ctx, c);
-    else dslash32(ctx, c);
+    switch (P::ID) {
+    case 64: dslash64(ctx, c); break;
+    case 32: dslash32(ctx, c); break;
+    case 16: dslash16(ctx, c); break;
+    default: dslashb16(ctx, c); break;
+    }
 }
 
 template <class P> DslashCall base_call(const ddrw_ctx *ctx, const MassSet &ms, int nrhs, long rs)
@@ -61,8 +67,7 @@ template <class P> DslashCall base_call(const ddrw_ctx *ctx, const MassSet &ms, 
     c.nmass = ms.n;
     for (int k = 0; k < ms.n; k++) {
         c.masses[k] = ms.m[k];
-        if constexpr (sizeof(typename P::R) == 8) c.Ainv[k] = ms.inv[k]->A64;
-        else c.Ainv[k] = ms.inv[k]->A32;
+        c.Ainv[k] = ainv_for(ms.inv[k], P::ID);
     }
     c.blk0 = 0;
     c.nblk = ctx->nblk;
@@ -100,14 +105,14 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
                         const std::vector<double> &thresh, int maxiter, int *iters)
 {
     using E = typename P::SElem;
-    const long rs = (long)P::SPLANES * ctx->V;
+    const long rs = P::field_elems(ctx->V);
     const size_t fb = sizeof(E) * rs * nrhs;
     const char *names[6] = {"eo_r", "eo_rh", "eo_p", "eo_v", "eo_t", "eo_tmp"};
     void *w[6];
     ddrw_status st;
     for (int k = 0; k < 6; k++) {
         char nm[32];
-        snprintf(nm, sizeof nm, "%s%d", names[k], (int)sizeof(typename P::R));
+        snprintf(nm, sizeof nm, "%s%d", names[k], P::ID);
         if ((st = workspace(ctx, nm, fb, &w[k]))) return st;
     }
     E *r = (E *)w[0], *rh = (E *)w[1], *p = (E *)w[2], *v = (E *)w[3], *t = (E *)w[4], *tmp = (E *)w[5];
@@ -176,7 +181,7 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
         int *count;
         if ((st = workspace(ctx, "eo_graph_count", sizeof(int), (void **)&count))) return st;
         std::array<uintptr_t, 24> key{};
-        key[0] = sizeof(typename P::R);
+        key[0] = P::ID;
         key[1] = (uintptr_t)nrhs;
         key[2] = (uintptr_t)maxiter;
         const void *ptrs[9] = {r, rh, p, v, t, tmp, x, sc, count};
@@ -186,7 +191,7 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
         for (int k = 0; k < ms.n && k < 5; k++) {
             double mk = ms.m[k];
             memcpy(&key[13 + 2 * k], &mk, sizeof(double));
-            key[14 + 2 * k] = sizeof(typename P::R) == 8 ? (uintptr_t)ms.inv[k]->A64 : (uintptr_t)ms.inv[k]->A32;
+            key[14 + 2 * k] = (uintptr_t)ainv_for(ms.inv[k], P::ID);
         }
         if (ms.n > 5) return set_error(ctx, DDRW_EINVAL, "graph key holds up to 5 masses");
         auto git = ctx->graphs.find(key);
@@ -279,30 +284,54 @@ ddrw_status full_norms(ddrw_ctx *ctx, const double2 *f, int nrhs, std::vector<do
 
 }  // namespace
 
+// One inner solve of the defect correction in storage policy P: e = D^-1 rhs (rhs scaled by
+// scale_d[r] into P's storage, the solution scaled back by scale_d[nrhs + r] and added to x, which
+// is zeroed first on the first cycle).
+template <class P>
+static ddrw_status inner_solve(ddrw_ctx *ctx, const MassSet &ms, const double2 *rhs, double2 *x, bool first, int nrhs,
+                               const double *scale_d, const std::vector<double> &th, int maxiter, int *iters)
+{
+    using E = typename P::SElem;
+    const long V = ctx->V, rsl = P::field_elems(V);
+    const size_t fl = sizeof(E) * rsl * nrhs;
+    char nb[32], ne[32];
+    snprintf(nb, sizeof nb, "full_b%d", P::ID);
+    snprintf(ne, sizeof ne, "full_e%d", P::ID);
+    void *bl, *el;
+    ddrw_status st;
+    if ((st = workspace(ctx, nb, fl, &bl))) return st;
+    if ((st = workspace(ctx, ne, fl, &el))) return st;
+    VecRange all{V, 0, V, 12 * V, nrhs};
+    to_low<P>(ctx, all, rsl, rhs, (E *)bl, scale_d);
+    if ((st = eo_bicgstab<P>(ctx, ms, (const E *)bl, (E *)el, nrhs, th, maxiter, iters))) return st;
+    if (first) DDRW_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double2) * 12 * V * nrhs, ctx->stream));
+    add_low<P>(ctx, all, rsl, (const E *)el, x, scale_d + nrhs);
+    return DDRW_OK;
+}
+
 ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, double2 *x, int nrhs, double tol,
                          int maxiter, ddrw_prec prec, SolveStats *stats)
 {
-    const long V = ctx->V, rs64 = 12 * V, rs32 = 6 * V;
-    const size_t f64 = sizeof(double2) * rs64 * nrhs, f32 = sizeof(float4) * rs32 * nrhs;
+    const long V = ctx->V, rs64 = 12 * V;
+    const size_t f64 = sizeof(double2) * rs64 * nrhs;
     const bool mixed = prec != DDRW_FP64;
+    // deepest relative residual an inner solve is asked for: what its storage reliably reaches
+    const double floor = prec == DDRW_MIXED_FP32 ? 1e-6 : prec == DDRW_MIXED_FP16 ? 1e-3 : 5e-3;
     ddrw_status st;
     std::vector<double> bb, rr;
     if ((st = full_norms(ctx, b, nrhs, bb))) return st;
     for (int r = 0; r < nrhs; r++)
         if (!std::isfinite(bb[r])) return set_error(ctx, DDRW_ENUMERIC, "non-finite right-hand side");
     double2 *res, *e64 = nullptr;
-    float4 *b32 = nullptr, *e32 = nullptr;
     double *scale_d = nullptr;
     if ((st = workspace(ctx, "full_res", f64, (void **)&res))) return st;
     if (mixed) {
-        if ((st = workspace(ctx, "full_b32", f32, (void **)&b32))) return st;
-        if ((st = workspace(ctx, "full_e32", f32, (void **)&e32))) return st;
         if ((st = workspace(ctx, "full_scale", sizeof(double) * 2 * nrhs, (void **)&scale_d))) return st;
     } else if ((st = workspace(ctx, "full_e64", f64, (void **)&e64))) {
         return st;
     }
     // inner target per right-hand side and cycle: what is still missing to reach tol, with a
-    // margin of 2, but no deeper than an FP32 solve reliably goes (1e-6)
+    // margin of 2, but no deeper than the inner storage reliably goes (floor)
     const double2 *rhs = b;
     bool first = true;
     std::vector<double> scale(nrhs), unscale(nrhs), ones(nrhs, 1.0);
@@ -318,17 +347,16 @@ ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, dou
             DDRW_CUDA_CHECK(cudaMemcpyAsync(scale_d, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
             DDRW_CUDA_CHECK(cudaMemcpyAsync(scale_d + nrhs, unscale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice,
                                             ctx->stream));
-            VecRange all{V, 0, V, rs64, nrhs};
-            to32(ctx, all, rs32, rhs, b32, scale_d);
             std::vector<double> th(nrhs);
             for (int r = 0; r < nrhs; r++) {
                 double need = nr[r] > 0 ? 0.5 * tol * std::sqrt(bb[r] / nr[r]) : 1.0;
-                double ti = std::max(1e-6, std::min(need, 0.5));
+                double ti = std::max(floor, std::min(need, 0.5));
                 th[r] = nr[r] > 0 ? ti * ti : 0.0;
             }
-            if ((st = eo_bicgstab<PrecS>(ctx, ms, b32, e32, nrhs, th, maxiter, &iters))) return st;
-            if (first) DDRW_CUDA_CHECK(cudaMemsetAsync(x, 0, f64, ctx->stream));
-            add32(ctx, all, rs32, e32, x, scale_d + nrhs);
+            if (prec == DDRW_MIXED_FP32) st = inner_solve<PrecS>(ctx, ms, rhs, x, first, nrhs, scale_d, th, maxiter, &iters);
+            else if (prec == DDRW_MIXED_FP16) st = inner_solve<PrecH>(ctx, ms, rhs, x, first, nrhs, scale_d, th, maxiter, &iters);
+            else st = inner_solve<PrecB>(ctx, ms, rhs, x, first, nrhs, scale_d, th, maxiter, &iters);
+            if (st) return st;
         } else {
             double2 *target = first ? x : e64;
             std::vector<double> th(nrhs);

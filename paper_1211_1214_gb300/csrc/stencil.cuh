@@ -128,6 +128,108 @@ __device__ __forceinline__ void hop_dir_multi(const GeomDev &g, const Site<BL> &
     }
 }
 
+// ---- rolled form: the forward and backward hops of a direction share one body
+//
+// The projector sign sg (-1 forward, +1 backward) and the boundary phase enter as FMA
+// coefficients, and the backward hop's U^dag is formed in registers, so the four direction
+// bodies serve both signs: half the code of the unrolled form at nearly the same instruction
+// count (the stencil is large enough that instruction fetch limits it otherwise).
+
+// h = psi_u + sg e_mu psi_d
+template <int MU, typename R>
+__device__ __forceinline__ void project_sg(const Spinor<R> &p, R sg, Half<R> &h)
+{
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        cpx<R> d0 = p.v[2][c], d1 = p.v[3][c];
+        cpx<R> e0, e1;  // e_mu psi_d
+        if (MU == 0) { e0 = -d0; e1 = -d1; }
+        else if (MU == 1) { e0 = timesMinusI(d1); e1 = timesMinusI(d0); }
+        else if (MU == 2) { e0 = -d1; e1 = d0; }
+        else { e0 = timesMinusI(d0); e1 = timesI(d1); }
+        h.v[0][c] = {p.v[0][c].re + sg * e0.re, p.v[0][c].im + sg * e0.im};
+        h.v[1][c] = {p.v[1][c].re + sg * e1.re, p.v[1][c].im + sg * e1.im};
+    }
+}
+
+// acc += ph (w, sg e_mu^dag w)
+template <int MU, typename R>
+__device__ __forceinline__ void reconstruct_sg(Spinor<R> &acc, const Half<R> &w, R ph, R sgph)
+{
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        cpx<R> w0 = w.v[0][c], w1 = w.v[1][c];
+        cpx<R> f0, f1;  // e_mu^dag w
+        if (MU == 0) { f0 = -w0; f1 = -w1; }
+        else if (MU == 1) { f0 = timesI(w1); f1 = timesI(w0); }
+        else if (MU == 2) { f0 = w1; f1 = -w0; }
+        else { f0 = timesI(w0); f1 = timesMinusI(w1); }
+        acc.v[0][c] = {acc.v[0][c].re + ph * w0.re, acc.v[0][c].im + ph * w0.im};
+        acc.v[1][c] = {acc.v[1][c].re + ph * w1.re, acc.v[1][c].im + ph * w1.im};
+        acc.v[2][c] = {acc.v[2][c].re + sgph * f0.re, acc.v[2][c].im + sgph * f0.im};
+        acc.v[3][c] = {acc.v[3][c].re + sgph * f1.re, acc.v[3][c].im + sgph * f1.im};
+    }
+}
+
+template <typename R> __device__ __forceinline__ void dagger(Link<R> &L)
+{
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        L.m[a][a].im = -L.m[a][a].im;
+#pragma unroll
+        for (int b = a + 1; b < 3; b++) {
+            cpx<R> t = L.m[a][b];
+            L.m[a][b] = {L.m[b][a].re, -L.m[b][a].im};
+            L.m[b][a] = {t.re, -t.im};
+        }
+    }
+}
+
+// one direction, sign given at run time (dir +1: forward, -1: backward), NR right-hand sides
+template <class P, int BL, int HOPSEL, int MU, int NR>
+__device__ __forceinline__ void hop_dir_sg(const GeomDev &g, const Site<BL> &st, int s, int dir,
+                                           const typename P::SElem *in, long rstride,
+                                           const typename P::UElem *__restrict__ U,
+                                           Spinor<typename P::R> (&acc)[NR])
+{
+    using R = typename P::R;
+    bool cross;
+    int phi;
+    const int sn = neighbour<BL>(st, MU, dir, g, &cross, &phi);
+    if (!(HOPSEL == 0 || (HOPSEL == 1 && !cross) || (HOPSEL == 2 && cross))) return;
+    Link<R> L;
+    P::load_link(U, g.V, MU, dir > 0 ? s : sn, L);
+    if (dir < 0) dagger(L);
+    const R sg = dir > 0 ? R(-1) : R(1);  // (1 - g_mu) forward, (1 + g_mu) backward
+    const R ph = phi < 0 ? R(-1) : R(1);
+    const R sgph = sg * ph;
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        Spinor<R> p;
+        P::load_spinor(in + r * rstride, (int)g.V, sn, p);
+        Half<R> h, w;
+        project_sg<MU>(p, sg, h);
+        link_mul(L, h, w);
+        reconstruct_sg<MU>(acc[r], w, ph, sgph);
+    }
+}
+
+template <class P, int BL, int HOPSEL, int NR>
+__device__ __forceinline__ void hop_multi_rolled(const GeomDev &g, const Site<BL> &st, int s,
+                                                 const typename P::SElem *in, long rstride,
+                                                 const typename P::UElem *__restrict__ U,
+                                                 Spinor<typename P::R> (&acc)[NR])
+{
+#pragma unroll 1
+    for (int k = 0; k < 2; k++) {
+        const int dir = 1 - 2 * k;
+        hop_dir_sg<P, BL, HOPSEL, 0, NR>(g, st, s, dir, in, rstride, U, acc);
+        hop_dir_sg<P, BL, HOPSEL, 1, NR>(g, st, s, dir, in, rstride, U, acc);
+        hop_dir_sg<P, BL, HOPSEL, 2, NR>(g, st, s, dir, in, rstride, U, acc);
+        hop_dir_sg<P, BL, HOPSEL, 3, NR>(g, st, s, dir, in, rstride, U, acc);
+    }
+}
+
 // v <- (diag + H_ch) v on both chirality blocks, H from a packed clover-format array
 template <class P>
 __device__ __forceinline__ void clover_apply(const typename P::CElem *__restrict__ Cl, long V, long s,

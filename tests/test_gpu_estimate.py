@@ -144,7 +144,8 @@ def test_zero_mass_shift():
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", [binding.MIXED_FP32])
+@pytest.mark.parametrize("prec", [binding.MIXED_FP32, binding.MIXED_FP16, binding.MIXED_BF16],
+                         ids=["fp32", "fp16", "bf16"])
 def test_mixed_precision_estimate_matches_fp64(case, prec):
     ctx = case["ctx"]
     nhit = min(case["nhit"], 4)
@@ -153,6 +154,26 @@ def test_mixed_precision_estimate_matches_fp64(case, prec):
     try:
         e, lw, _, info = ctx.estimate(nhit, seed=2)
     finally:
+        ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+    for j in range(nhit):
+        assert close(e[j], e64[j]), (j, e[j], e64[j])
+    assert close(lw, lw64)
+    assert info["true_rel_residual"] <= 1e-10
+
+
+@pytest.mark.parametrize("prec", [binding.MIXED_FP32, binding.MIXED_FP16], ids=["fp32", "fp16"])
+@pytest.mark.parametrize("cfg", [(1, 128, 1, 1), (4, 64, 1, 0), (2, 64, 2, 1)], ids=["r1", "u4", "r2w2"])
+def test_mixed_estimate_under_pinned_stencil_configs(case, prec, cfg):
+    """The low-precision stencils in each pinned launch configuration lead to the FP64 result."""
+    ctx = case["ctx"]
+    nhit = min(case["nhit"], 4)
+    e64, lw64, _, _ = ctx.estimate(nhit, seed=3)
+    ctx.set_solver(prec, tol_outer=1e-10, tol_block=1e-12)
+    ctx.stencil_config(*cfg)
+    try:
+        e, lw, _, info = ctx.estimate(nhit, seed=3)
+    finally:
+        ctx.stencil_config(0)
         ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
     for j in range(nhit):
         assert close(e[j], e64[j]), (j, e[j], e64[j])

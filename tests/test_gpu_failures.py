@@ -55,7 +55,7 @@ def test_bad_arguments(ctx):
         c.solve_block(2, 0.045, b, np.zeros_like(b))  # colour must be black or white
     assert ei.value.status == 1
     with pytest.raises(binding.DDRWError) as ei:
-        c.set_solver(binding.MIXED_FP16)  # reserved precision
+        c.set_solver(9)  # no such precision
     assert ei.value.status == 1
     with pytest.raises(binding.DDRWError) as ei:
         c.estimate_interp(9, 2)  # at most 8 interpolation steps

@@ -101,15 +101,17 @@ def test_c5_force_against_finite_differences(c5, prec):
 def test_mixed_force_matches_fp64(c5):
     ctx, U, dims = c5
     outs = []
-    for prec, tol in ((binding.FP64, (1e-13, 1e-14)), (binding.MIXED_FP32, (1e-10, 1e-12))):
+    for prec, tol in ((binding.FP64, (1e-13, 1e-14)), (binding.MIXED_FP32, (1e-10, 1e-12)),
+                      (binding.MIXED_FP16, (1e-10, 1e-12))):
         ctx.set_solver(prec, tol_outer=tol[0], tol_block=tol[1])
         dU = torch.zeros((ctx.V, 4, 8), dtype=torch.float64, device="cuda")
         e, dm2, _ = ctx.force(2, seed=5, dU=dU)
         outs.append((e, dm2, dU.cpu().numpy()))
-    (e0, m0, F0), (e1, m1, F1) = outs
-    assert np.allclose(e1, e0, rtol=1e-8)
-    assert np.allclose(m1, m0, rtol=1e-7)
-    assert np.linalg.norm(F1 - F0) <= 1e-7 * np.linalg.norm(F0)
+    e0, m0, F0 = outs[0]
+    for e1, m1, F1 in outs[1:]:
+        assert np.allclose(e1, e0, rtol=1e-8)
+        assert np.allclose(m1, m0, rtol=1e-7)
+        assert np.linalg.norm(F1 - F0) <= 1e-7 * np.linalg.norm(F0)
 
 
 def test_autograd_function(c5):

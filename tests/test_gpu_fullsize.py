@@ -38,9 +38,10 @@ def test_operator_full_lattice(full):
     assert rel(y.cpu().numpy(), lat.apply(M2, x)) < 1e-12
 
 
-def test_solves_reach_their_true_residual(full):
+@pytest.mark.parametrize("prec", [binding.MIXED_FP32, binding.MIXED_FP16], ids=["fp32", "fp16"])
+def test_solves_reach_their_true_residual(full, prec):
     ctx, lat = full
-    ctx.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-10)
+    ctx.set_solver(prec, tol_outer=1e-10, tol_block=1e-10)
     b = synth.spinor_field(DIMS, seed=72)
     bt = torch.from_numpy(b).cuda()
     x = torch.zeros_like(bt)
@@ -56,11 +57,12 @@ def test_solves_reach_their_true_residual(full):
     assert np.linalg.norm(res) / np.linalg.norm(bc) <= 1e-10
 
 
-def test_mixed_estimate_matches_fp64_at_full_size(full):
+@pytest.mark.parametrize("prec", [binding.MIXED_FP32, binding.MIXED_FP16], ids=["fp32", "fp16"])
+def test_mixed_estimate_matches_fp64_at_full_size(full, prec):
     ctx, lat = full
     ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
     e64, lw64, _, _ = ctx.estimate(1, seed=2, hit_offset=0)
-    ctx.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-10)
+    ctx.set_solver(prec, tol_outer=1e-10, tol_block=1e-10)
     e32, lw32, _, info = ctx.estimate(1, seed=2, hit_offset=0)
     assert abs(e32[0] - e64[0]) <= 1e-8 * max(abs(e64[0]), 1.0)
     assert abs(lw32 - lw64) <= 1e-8 * max(abs(lw64), 1.0)

@@ -69,6 +69,23 @@ def test_apply_D_double_single(setup, m):
         assert rel(y[r], lat.apply(m, x[r])) < 1e-12
 
 
+@pytest.mark.parametrize("nr,nt,nw,roll", [(1, 64, 1, 0), (1, 64, 1, 1), (2, 128, 1, 0), (2, 128, 2, 1),
+                                           (4, 32, 2, 0), (4, 256, 1, 1), (1, 32, 8, 1)])
+def test_every_stencil_configuration(setup, nr, nt, nw, roll):
+    """Each pinned launch configuration of the all-hop stencil (right-hand sides per thread, CTA
+    shape, unrolled or rolled hop code) gives the oracle's operator on 4 right-hand sides."""
+    ctx, lat, dims = setup
+    x = synth.spinor_field(dims, seed=9, nrhs=4)
+    y = np.zeros_like(x)
+    ctx.stencil_config(nr, nt, nw, roll)
+    try:
+        ctx.apply_D(0.07, x, y, nrhs=4)
+    finally:
+        ctx.stencil_config(0)
+    for r in range(4):
+        assert rel(y[r], lat.apply(0.07, x[r])) < 1e-12
+
+
 @pytest.mark.parametrize("rows,cols", [(0, 0), (1, 1), (0, 1), (1, 0), (2, 0), (1, 2)])
 def test_apply_block(setup, rows, cols):
     ctx, lat, dims = setup
