@@ -215,15 +215,17 @@ ddrw_status ddrw_use_graphs(ddrw_ctx *ctx, int enable, long *graph_launches);
 
 /* Autotuner of the stencil launches: on the first launch of each shape (precision, block length,
  * parities, right-hand sides, diagonal/post modes) it times right-hand sides per thread {1,2,4},
- * sites per CTA row {64,128,256}, right-hand-side rows per CTA {1,2} and unrolled or rolled hop
- * code with CUDA events and keeps the fastest.  enable = 0 uses a fixed choice; either call
+ * sites per CTA row {64,128,256}, right-hand-side rows per CTA {1,2} and the hop code form
+ * (unrolled, rolled, batched loads) with CUDA events and keeps the fastest.  enable = 0 uses a fixed choice; either call
  * clears the tuned table.  The report lists the tuned shapes, one per line. */
 ddrw_status ddrw_autotune(ddrw_ctx *ctx, int enable);
 ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
 
 /* Pins the configuration of every tunable stencil launch (overrides the autotuner): nr
  * right-hand sides per thread (1, 2 or 4), nt sites per CTA row (32 .. 256, a multiple of 32),
- * nw right-hand-side rows per CTA (nt * nw <= 256), roll 0 / 1 (unrolled / rolled hop code).
+ * nw right-hand-side rows per CTA (nt * nw <= 256), roll 0 / 1 (unrolled / rolled hop code),
+ * 2 / 3 (the loads of 4 / 8 hops issued ahead of their arithmetic) or 4 / 5 (unrolled with at
+ * most 85 / 64 registers per thread); roll >= 2 needs nr = 1.
  * A launch whose right-hand sides per mass slot are not a multiple of nr * nw runs with nr = nw = 1.
  * nr = 0 returns to autotuning.  DDRW_EINVAL for values outside these ranges. */
 ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll);
@@ -240,6 +242,10 @@ ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll)
  * returns in *launches the number of kernel launches of every kind since the last reset.  ddrw_profile(ctx, enable) resets the counters. */
 ddrw_status ddrw_profile(ddrw_ctx *ctx, int enable);
 ddrw_status ddrw_profile_read(ddrw_ctx *ctx, int kind, long *launches, double *ms, double *bytes);
+
+/* Site updates (output sites x right-hand sides) summed over the timed launches of a stencil
+ * class (0-3, 7-9) since the last ddrw_profile call; other classes report 0. */
+ddrw_status ddrw_profile_units(ddrw_ctx *ctx, int kind, double *site_updates);
 
 #ifdef __cplusplus
 }

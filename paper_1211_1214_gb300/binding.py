@@ -25,7 +25,7 @@ EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", 
            "ddrw_set_params", "ddrw_set_solver", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
-           "ddrw_autotune", "ddrw_autotune_report", "ddrw_stencil_config", "ddrw_force", "ddrw_use_graphs",
+           "ddrw_autotune", "ddrw_autotune_report", "ddrw_stencil_config", "ddrw_profile_units", "ddrw_force", "ddrw_use_graphs",
            "ddrw_estimate_interp", "ddrw_apply_D_ds"]
 
 #: kernel classes of ddrw_profile_read
@@ -91,6 +91,7 @@ def load(path: str | None = None):
         "ddrw_profile": (st, [vp, ctypes.c_int]),
         "ddrw_autotune": (st, [vp, ctypes.c_int]),
         "ddrw_stencil_config": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "ddrw_profile_units": (st, [vp, ctypes.c_int, dp]),
         "ddrw_use_graphs": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long)]),
         "ddrw_estimate_interp": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp, dp, dp,
                                       dp, ctypes.POINTER(SolveInfo)]),
@@ -266,6 +267,12 @@ class Context:
 
     def profile(self, enable=True):
         self._check(self.L.ddrw_profile(self._h, int(enable)), "ddrw_profile")
+
+    def profile_units(self, kind):
+        """Site updates (sites x right-hand sides) of the timed launches of a stencil class."""
+        u = ctypes.c_double(0)
+        self._check(self.L.ddrw_profile_units(self._h, int(kind), ctypes.byref(u)), "ddrw_profile_units")
+        return u.value
 
     def profile_read(self, kind):
         """(launches, summed device ms, summed compulsory bytes) of one kernel class."""

@@ -238,7 +238,7 @@ static cudaEvent_t pool_event(ddrw_ctx *ctx)
     return e;
 }
 
-ProfScope::ProfScope(ddrw_ctx *c, int k, double b) : ctx(c), kind(k), bytes(b)
+ProfScope::ProfScope(ddrw_ctx *c, int k, double b, double u) : ctx(c), kind(k), bytes(b), units(u)
 {
     if (!ctx->prof_on) return;
     // launches captured into a graph are not timed (graph bodies hold no event nodes)
@@ -254,7 +254,7 @@ ProfScope::~ProfScope()
     if (!a) return;
     cudaEvent_t b = pool_event(ctx);
     cudaEventRecord(b, ctx->stream);
-    ctx->prof_pending.push_back({a, b, kind, bytes});
+    ctx->prof_pending.push_back({a, b, kind, bytes, units});
 }
 
 static void prof_collect(ddrw_ctx *ctx)
@@ -267,6 +267,7 @@ static void prof_collect(ddrw_ctx *ctx)
         ctx->prof_count[r.kind] += 1;
         ctx->prof_ms[r.kind] += ms;
         ctx->prof_bytes[r.kind] += r.bytes;
+        ctx->prof_units[r.kind] += r.units;
         ctx->prof_pool.push_back(r.a);
         ctx->prof_pool.push_back(r.b);
     }
@@ -287,6 +288,7 @@ ddrw_status ddrw_profile(ddrw_ctx *ctx, int enable)
         ctx->prof_count[k] = 0;
         ctx->prof_ms[k] = 0;
         ctx->prof_bytes[k] = 0;
+        ctx->prof_units[k] = 0;
     }
     ctx->prof_on = enable != 0;
     ctx->launches = 0;
@@ -314,6 +316,14 @@ ddrw_status ddrw_profile_read(ddrw_ctx *ctx, int kind, long *launches, double *m
     if (launches) *launches = ctx->prof_count[kind];
     if (ms) *ms = ctx->prof_ms[kind];
     if (bytes) *bytes = ctx->prof_bytes[kind];
+    return DDRW_OK;
+}
+
+ddrw_status ddrw_profile_units(ddrw_ctx *ctx, int kind, double *site_updates)
+{
+    if (!ctx || !site_updates || kind < 0 || kind >= PROF_NKIND) return DDRW_EINVAL;
+    prof_collect(ctx);
+    *site_updates = ctx->prof_units[kind];
     return DDRW_OK;
 }
 

@@ -128,12 +128,12 @@ struct ddrw_ctx {
     struct ProfRec {
         cudaEvent_t a, b;
         int kind;
-        double bytes;
+        double bytes, units;
     };
     std::vector<ProfRec> prof_pending;
     std::vector<cudaEvent_t> prof_pool;
     long prof_count[16] = {0};
-    double prof_ms[16] = {0}, prof_bytes[16] = {0};
+    double prof_ms[16] = {0}, prof_bytes[16] = {0}, prof_units[16] = {0};
 
     std::string err;
 };
@@ -160,9 +160,9 @@ enum {
 struct ProfScope {
     ddrw_ctx *ctx;
     int kind;
-    double bytes;
+    double bytes, units;  // algorithmic bytes and site updates (sites x right-hand sides) of the launch
     cudaEvent_t a = nullptr;
-    ProfScope(ddrw_ctx *c, int k, double b);
+    ProfScope(ddrw_ctx *c, int k, double b, double u = 0.0);
     ~ProfScope();
 };
 

@@ -301,6 +301,34 @@ struct PrecD {
             L.m[k / 3][k % 3] = {v.x, v.y};
         }
     }
+    // raw loads (all issued before any decode) for the batched hop form
+    struct SRaw {
+        double2 e[12];
+    };
+    struct URaw {
+        double2 e[9];
+    };
+    __device__ static __forceinline__ void load_raw(const SElem *__restrict__ f, int stride, int s, SRaw &r)
+    {
+#pragma unroll
+        for (int k = 0; k < 12; k++) r.e[k] = __ldg(f + (k * stride + s));
+    }
+    __device__ static __forceinline__ void decode(const SRaw &r, Spinor<R> &p)
+    {
+#pragma unroll
+        for (int k = 0; k < 12; k++) p.v[k / 3][k % 3] = {r.e[k].x, r.e[k].y};
+    }
+    __device__ static __forceinline__ void load_link_raw(const UElem *__restrict__ U, int V, int mu, int s, URaw &r)
+    {
+        const UElem *b = U + (long)mu * 9 * V;
+#pragma unroll
+        for (int k = 0; k < 9; k++) r.e[k] = __ldg(b + (k * V + s));
+    }
+    __device__ static __forceinline__ void decode_link(const URaw &r, Link<R> &L)
+    {
+#pragma unroll
+        for (int k = 0; k < 9; k++) L.m[k / 3][k % 3] = {r.e[k].x, r.e[k].y};
+    }
     // reals 0..35 of chirality block ch
     __device__ static __forceinline__ void load_clover(const CElem *__restrict__ Cl, int V, int s, int ch, R *c)
     {
@@ -384,6 +412,42 @@ struct PrecS {
         L.m[1][0] = {a1.z, a1.w};
         L.m[1][1] = {a2.x, a2.y};
         L.m[1][2] = {a2.z, a2.w};
+        reconstruct_row2(L);
+    }
+    struct SRaw {
+        float4 e[6];
+    };
+    struct URaw {
+        float4 e[3];
+    };
+    __device__ static __forceinline__ void load_raw(const SElem *__restrict__ f, int stride, int s, SRaw &r)
+    {
+#pragma unroll
+        for (int k = 0; k < 6; k++) r.e[k] = __ldg(f + (k * stride + s));
+    }
+    __device__ static __forceinline__ void decode(const SRaw &r, Spinor<R> &p)
+    {
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            p.v[(2 * k) / 3][(2 * k) % 3] = {r.e[k].x, r.e[k].y};
+            p.v[(2 * k + 1) / 3][(2 * k + 1) % 3] = {r.e[k].z, r.e[k].w};
+        }
+    }
+    __device__ static __forceinline__ void load_link_raw(const UElem *__restrict__ U, int V, int mu, int s, URaw &r)
+    {
+        const UElem *b = U + (long)mu * 3 * V;
+        r.e[0] = __ldg(b + s);
+        r.e[1] = __ldg(b + (V + s));
+        r.e[2] = __ldg(b + (2 * V + s));
+    }
+    __device__ static __forceinline__ void decode_link(const URaw &r, Link<R> &L)
+    {
+        L.m[0][0] = {r.e[0].x, r.e[0].y};
+        L.m[0][1] = {r.e[0].z, r.e[0].w};
+        L.m[0][2] = {r.e[1].x, r.e[1].y};
+        L.m[1][0] = {r.e[1].z, r.e[1].w};
+        L.m[1][1] = {r.e[2].x, r.e[2].y};
+        L.m[1][2] = {r.e[2].z, r.e[2].w};
         reconstruct_row2(L);
     }
     __device__ static __forceinline__ void reconstruct_row2(Link<R> &L)

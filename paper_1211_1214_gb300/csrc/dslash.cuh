@@ -42,8 +42,10 @@ template <class P> struct DsArgs {
     const typename P::CElem *Ainv[MAXM];  // A(m)^-1 per slot
 };
 
+// ROLL selects the hop code form: 0 unrolled, 1 rolled, 2 / 3 batched loads of 4 / 8 hops,
+// 4 / 5 unrolled compiled for at least 3 / 4 CTAs of 256 threads per SM (<= 85 / 64 registers)
 template <class P, int BL, int HOPSEL, int NR, int ROLL = 0>
-__global__ void __launch_bounds__(256) k_dslash(GeomDev g, DsArgs<P> a)
+__global__ void __launch_bounds__(256, ROLL == 4 ? 3 : ROLL == 5 ? 4 : 1) k_dslash(GeomDev g, DsArgs<P> a)
 {
     using R = typename P::R;
     // groups of NR right-hand sides; a CTA holds blockDim.y groups (one per row of threads) of
@@ -66,7 +68,10 @@ __global__ void __launch_bounds__(256) k_dslash(GeomDev g, DsArgs<P> a)
     for (int r = 0; r < NR; r++) zero(acc[r]);
     if (a.beta != R(0)) {
         const typename P::SElem *in = a.in + roff;
-        if constexpr (ROLL) {
+        if constexpr (ROLL == 2 || ROLL == 3) {  // batched loads, one right-hand side: 2 -> 4 hops, 3 -> 8 hops per batch
+            static_assert(NR == 1, "batched hops take one right-hand side per thread");
+            hop_batched<P, BL, HOPSEL, ROLL == 2 ? 4 : 8>(g, st, (int)s, in, a.U, acc[0]);
+        } else if constexpr (ROLL == 1) {
             hop_multi_rolled<P, BL, HOPSEL, NR>(g, st, (int)s, in, a.rstride, a.U, acc);
         } else {
             hop_dir_multi<P, BL, HOPSEL, 0, NR>(g, st, s, in, a.rstride, a.U, acc);
@@ -124,7 +129,9 @@ struct DsConfig {
     int nr = 1;    // right-hand sides per thread
     int nt = 128;  // sites per CTA (threads per CTA row)
     int nw = 1;    // CTA rows: groups of nr right-hand sides per CTA (nt * nw <= 256)
-    int roll = 0;  // 1: forward and backward hops share the direction bodies (smaller code)
+    int roll = 0;  // 1: forward and backward hops share the direction bodies (smaller code);
+                   // 2 / 3: batched loads of 4 / 8 hops before their arithmetic; 4 / 5: unrolled
+                   // with at most 85 / 64 registers (more warps per SM); forms 2-5 take nr = 1
 };
 
 template <class P, int BL>
@@ -173,12 +180,16 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
         else k_dslash<P, BL, 2, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
     } else {
         if (c.hopsel == 0) {
-            switch (cfg.nr * 2 + cfg.roll) {
-            case 8: k_dslash<P, BL, 0, 4><<<grid, blk, 0, ctx->stream>>>(g, a); break;
-            case 9: k_dslash<P, BL, 0, 4, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
-            case 4: k_dslash<P, BL, 0, 2><<<grid, blk, 0, ctx->stream>>>(g, a); break;
-            case 5: k_dslash<P, BL, 0, 2, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
-            case 3: k_dslash<P, BL, 0, 1, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            switch (cfg.roll * 8 + cfg.nr) {
+            case 4: k_dslash<P, BL, 0, 4><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 2: k_dslash<P, BL, 0, 2><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 12: k_dslash<P, BL, 0, 4, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 10: k_dslash<P, BL, 0, 2, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 9: k_dslash<P, BL, 0, 1, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 17: k_dslash<P, BL, 0, 1, 2><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 25: k_dslash<P, BL, 0, 1, 3><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 33: k_dslash<P, BL, 0, 1, 4><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 41: k_dslash<P, BL, 0, 1, 5><<<grid, blk, 0, ctx->stream>>>(g, a); break;
             default: k_dslash<P, BL, 0, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
             }
         } else if (c.hopsel == 1) {
@@ -225,7 +236,7 @@ void launch_bl(ddrw_ctx *ctx, const DslashCall &c)
     int kind = split ? PROF_DSLASH_DS
                      : P::ID < 32 ? PROF_DSLASH16 + (c.hopsel != 0)
                                   : (sizeof(R) == 8 ? PROF_DSLASH64 : PROF_DSLASH32) + (c.hopsel != 0 ? 2 : 0);
-    ProfScope ps(ctx, kind, compulsory_bytes<P>(c, n));
+    ProfScope ps(ctx, kind, compulsory_bytes<P>(c, n), (double)n * c.nrhs);
     launch_cfg<P, BL>(ctx, c, make_args<P, BL>(ctx, c), cfg);
 }
 

@@ -5,7 +5,9 @@
 // configuration -- right-hand sides per thread NR in {1, 2, 4} (dividing the right-hand sides per
 // mass slot), sites per CTA row in {64, 128, 256}, CTA rows (groups of NR right-hand sides of the
 // same sites, sharing links and clover terms in L1) in {1, 2}, at most 256 threads per CTA, and
-// unrolled or rolled hop bodies -- with CUDA events on the context's stream, keeps the fastest,
+// the hop code form (unrolled, rolled, with the loads of 4 or 8 hops batched ahead of their
+// arithmetic, or unrolled under a register cap for more warps per SM; the last three with one
+// right-hand side per thread) -- with CUDA events on the context's stream, keeps the fastest,
 // and reuses it for every later launch of that shape.  The candidates run on the real
 // arguments: a stencil launch never reads its own output sites, so repeating it is harmless.
 // While the stream is being captured into a graph nothing is timed and the default is used.
@@ -45,9 +47,11 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
     DsConfig best = def;
     float best_ms = 1e30f;
     const int nrs[3] = {1, 2, 4}, nts[3] = {64, 128, 256}, nws[2] = {1, 2};
-    for (int roll = 0; roll < 2; roll++)
+    for (int roll = 0; roll < 6; roll++)
     for (int nr : nrs) {
-        if (c.nrhs % nr || rpm % nr) continue;
+        // the batched and register-capped forms are for 32- and 16-bit storage: with FP64 data
+        // they spill
+        if (c.nrhs % nr || rpm % nr || (roll >= 2 && (nr != 1 || prec == 64))) continue;
         for (int nw : nws)
         for (int nt : nts) {
             if ((c.nrhs / nr) % nw || nt * nw > 256) continue;
@@ -93,8 +97,8 @@ ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll)
         ctx->pinned_nr = 0;
         return DDRW_OK;
     }
-    if ((nr != 1 && nr != 2 && nr != 4) || nt < 32 || nt > 256 || nt % 32 || nw < 1 || nt * nw > 256 ||
-        (roll != 0 && roll != 1))
+    if ((nr != 1 && nr != 2 && nr != 4) || nt < 32 || nt > 256 || nt % 32 || nw < 1 || nt * nw > 256 || roll < 0 ||
+        roll > 5 || (roll >= 2 && nr != 1))
         return set_error(ctx, DDRW_EINVAL, "bad stencil configuration");
     ctx->pinned_nr = nr;
     ctx->pinned_nt = nt;

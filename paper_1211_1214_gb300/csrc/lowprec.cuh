@@ -169,6 +169,51 @@ template <bool BF> struct PrecLow {
             c[4 * k + 3] = hi.y;
         }
     }
+    struct SRaw {
+        uint4 e[3];
+        float n;
+    };
+    struct URaw {
+        uint2 e[3];
+    };
+    __device__ static __forceinline__ void load_raw(const SElem *__restrict__ f, int stride, int s, SRaw &r)
+    {
+        r.n = __ldg(reinterpret_cast<const float *>(f + 3 * stride) + s);
+#pragma unroll
+        for (int k = 0; k < 3; k++) r.e[k] = __ldg(f + (k * stride + s));
+    }
+    __device__ static __forceinline__ void decode(const SRaw &r, Spinor<R> &p)
+    {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            p.v[(4 * k) / 3][(4 * k) % 3] = cx(r.e[k].x, r.n);
+            p.v[(4 * k + 1) / 3][(4 * k + 1) % 3] = cx(r.e[k].y, r.n);
+            p.v[(4 * k + 2) / 3][(4 * k + 2) % 3] = cx(r.e[k].z, r.n);
+            p.v[(4 * k + 3) / 3][(4 * k + 3) % 3] = cx(r.e[k].w, r.n);
+        }
+    }
+    __device__ static __forceinline__ void load_link_raw(const UElem *__restrict__ U, int V, int mu, int s, URaw &r)
+    {
+        const UElem *b = U + (long)mu * 3 * V;
+        r.e[0] = __ldg(b + s);
+        r.e[1] = __ldg(b + (V + s));
+        r.e[2] = __ldg(b + (2 * V + s));
+    }
+    __device__ static __forceinline__ void decode_link(const URaw &r, Link<R> &L)
+    {
+        L.m[0][0] = cx(r.e[0].x, 1.f);
+        L.m[0][1] = cx(r.e[0].y, 1.f);
+        L.m[0][2] = cx(r.e[1].x, 1.f);
+        L.m[1][0] = cx(r.e[1].y, 1.f);
+        L.m[1][1] = cx(r.e[2].x, 1.f);
+        L.m[1][2] = cx(r.e[2].y, 1.f);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            int i = (c + 1) % 3, j = (c + 2) % 3;
+            cpx<R> t = cmul(L.m[0][i], L.m[1][j]) - cmul(L.m[0][j], L.m[1][i]);
+            L.m[2][c] = {t.re, -t.im};
+        }
+    }
     // BLAS access: the whole site as one chunk
     __device__ static __forceinline__ void ld_chunk(const SElem *f, long V, long s, int, cpx<R> *c)
     {

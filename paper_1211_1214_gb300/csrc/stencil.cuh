@@ -230,6 +230,93 @@ __device__ __forceinline__ void hop_multi_rolled(const GeomDev &g, const Site<BL
     }
 }
 
+// ---- batched form (one right-hand side): the loads of G hops are all issued before any of them
+// is used, so a site waits for memory 8 / G times instead of 8.  Hop k = 0..7 is direction
+// mu = k / 2, forward for even k, backward for odd k.
+
+template <class P, int BL, int HOPSEL, int K> struct HopK {
+    using R = typename P::R;
+    static constexpr int MU = K / 2;
+    static constexpr int DIR = (K & 1) ? -1 : 1;
+    __device__ static __forceinline__ bool issue(const GeomDev &g, const Site<BL> &st, int s,
+                                                 const typename P::SElem *in,
+                                                 const typename P::UElem *__restrict__ U,
+                                                 typename P::SRaw &sr, typename P::URaw &ur, int &ph)
+    {
+        bool cross;
+        const int sn = neighbour<BL>(st, MU, DIR, g, &cross, &ph);
+        if (!(HOPSEL == 0 || (HOPSEL == 1 && !cross) || (HOPSEL == 2 && cross))) return false;
+        P::load_raw(in, (int)g.V, sn, sr);
+        P::load_link_raw(U, (int)g.V, MU, DIR > 0 ? s : sn, ur);
+        return true;
+    }
+    __device__ static __forceinline__ void compute(const typename P::SRaw &sr, const typename P::URaw &ur, int ph,
+                                                   Spinor<R> &acc)
+    {
+        Spinor<R> p;
+        P::decode(sr, p);
+        Link<R> L;
+        P::decode_link(ur, L);
+        Half<R> h, w;
+        project<MU, -DIR>(p, h);
+        if (DIR > 0) link_mul(L, h, w);
+        else link_dag_mul(L, h, w);
+        if (ph < 0)
+#pragma unroll
+            for (int a = 0; a < 2; a++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) w.v[a][c] = -w.v[a][c];
+        reconstruct_add<MU, -DIR>(acc, w);
+    }
+};
+
+template <class P, int BL, int HOPSEL, int K0, int G> struct HopBatch {
+    using R = typename P::R;
+    __device__ static __forceinline__ void run(const GeomDev &g, const Site<BL> &st, int s,
+                                               const typename P::SElem *in,
+                                               const typename P::UElem *__restrict__ U, Spinor<R> &acc)
+    {
+        typename P::SRaw sr[G];
+        typename P::URaw ur[G];
+        int ph[G];
+        bool act[G];
+        issue_all<0>(g, st, s, in, U, sr, ur, ph, act);
+        compute_all<0>(sr, ur, ph, act, acc);
+    }
+    template <int J>
+    __device__ static __forceinline__ void issue_all(const GeomDev &g, const Site<BL> &st, int s,
+                                                     const typename P::SElem *in,
+                                                     const typename P::UElem *__restrict__ U, typename P::SRaw *sr,
+                                                     typename P::URaw *ur, int *ph, bool *act)
+    {
+        if constexpr (J < G) {
+            act[J] = HopK<P, BL, HOPSEL, K0 + J>::issue(g, st, s, in, U, sr[J], ur[J], ph[J]);
+            issue_all<J + 1>(g, st, s, in, U, sr, ur, ph, act);
+        }
+    }
+    template <int J>
+    __device__ static __forceinline__ void compute_all(const typename P::SRaw *sr, const typename P::URaw *ur,
+                                                       const int *ph, const bool *act, Spinor<R> &acc)
+    {
+        if constexpr (J < G) {
+            if (act[J]) HopK<P, BL, HOPSEL, K0 + J>::compute(sr[J], ur[J], ph[J], acc);
+            compute_all<J + 1>(sr, ur, ph, act, acc);
+        }
+    }
+};
+
+template <class P, int BL, int HOPSEL, int G>
+__device__ __forceinline__ void hop_batched(const GeomDev &g, const Site<BL> &st, int s, const typename P::SElem *in,
+                                            const typename P::UElem *__restrict__ U, Spinor<typename P::R> &acc)
+{
+    HopBatch<P, BL, HOPSEL, 0, G>::run(g, st, s, in, U, acc);
+    if constexpr (G < 8) HopBatch<P, BL, HOPSEL, G, G>::run(g, st, s, in, U, acc);
+    if constexpr (G < 4) {
+        HopBatch<P, BL, HOPSEL, 2 * G, G>::run(g, st, s, in, U, acc);
+        HopBatch<P, BL, HOPSEL, 3 * G, G>::run(g, st, s, in, U, acc);
+    }
+}
+
 // v <- (diag + H_ch) v on both chirality blocks, H from a packed clover-format array
 template <class P>
 __device__ __forceinline__ void clover_apply(const typename P::CElem *__restrict__ Cl, long V, long s,
