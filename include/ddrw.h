@@ -225,7 +225,7 @@ ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
  * right-hand sides per thread (1, 2 or 4), nt sites per CTA row (32 .. 256, a multiple of 32),
  * nw right-hand-side rows per CTA (nt * nw <= 256), roll 0 / 1 (unrolled / rolled hop code),
  * 2 / 3 (the loads of 4 / 8 hops issued ahead of their arithmetic) or 4 / 5 (unrolled with at
- * most 85 / 64 registers per thread); roll >= 2 needs nr = 1.
+ * most 85 / 128 registers per thread); roll 2-4 need nr = 1, roll 5 nr <= 2.
  * A launch whose right-hand sides per mass slot are not a multiple of nr * nw runs with nr = nw = 1.
  * nr = 0 returns to autotuning.  DDRW_EINVAL for values outside these ranges. */
 ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll);

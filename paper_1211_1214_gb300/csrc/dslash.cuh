@@ -43,9 +43,9 @@ template <class P> struct DsArgs {
 };
 
 // ROLL selects the hop code form: 0 unrolled, 1 rolled, 2 / 3 batched loads of 4 / 8 hops,
-// 4 / 5 unrolled compiled for at least 3 / 4 CTAs of 256 threads per SM (<= 85 / 64 registers)
+// 4 / 5 unrolled compiled for at least 3 / 2 CTAs of 256 threads per SM (<= 85 / 128 registers)
 template <class P, int BL, int HOPSEL, int NR, int ROLL = 0>
-__global__ void __launch_bounds__(256, ROLL == 4 ? 3 : ROLL == 5 ? 4 : 1) k_dslash(GeomDev g, DsArgs<P> a)
+__global__ void __launch_bounds__(256, ROLL == 4 ? 3 : ROLL == 5 ? 2 : 1) k_dslash(GeomDev g, DsArgs<P> a)
 {
     using R = typename P::R;
     // groups of NR right-hand sides; a CTA holds blockDim.y groups (one per row of threads) of
@@ -130,8 +130,8 @@ struct DsConfig {
     int nt = 128;  // sites per CTA (threads per CTA row)
     int nw = 1;    // CTA rows: groups of nr right-hand sides per CTA (nt * nw <= 256)
     int roll = 0;  // 1: forward and backward hops share the direction bodies (smaller code);
-                   // 2 / 3: batched loads of 4 / 8 hops before their arithmetic; 4 / 5: unrolled
-                   // with at most 85 / 64 registers (more warps per SM); forms 2-5 take nr = 1
+                   // 2 / 3: batched loads of 4 / 8 hops before their arithmetic (nr = 1); 4 / 5:
+                   // unrolled with at most 85 / 128 registers, more warps per SM (nr = 1 / nr <= 2)
 };
 
 template <class P, int BL>
@@ -190,6 +190,7 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
             case 25: k_dslash<P, BL, 0, 1, 3><<<grid, blk, 0, ctx->stream>>>(g, a); break;
             case 33: k_dslash<P, BL, 0, 1, 4><<<grid, blk, 0, ctx->stream>>>(g, a); break;
             case 41: k_dslash<P, BL, 0, 1, 5><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 42: k_dslash<P, BL, 0, 2, 5><<<grid, blk, 0, ctx->stream>>>(g, a); break;
             default: k_dslash<P, BL, 0, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
             }
         } else if (c.hopsel == 1) {

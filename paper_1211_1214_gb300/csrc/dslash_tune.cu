@@ -6,8 +6,8 @@
 // mass slot), sites per CTA row in {64, 128, 256}, CTA rows (groups of NR right-hand sides of the
 // same sites, sharing links and clover terms in L1) in {1, 2}, at most 256 threads per CTA, and
 // the hop code form (unrolled, rolled, with the loads of 4 or 8 hops batched ahead of their
-// arithmetic, or unrolled under a register cap for more warps per SM; the last three with one
-// right-hand side per thread) -- with CUDA events on the context's stream, keeps the fastest,
+// arithmetic, or unrolled under a register cap of 85 or 128 for more warps per SM) -- with CUDA
+// events on the context's stream, keeps the fastest,
 // and reuses it for every later launch of that shape.  The candidates run on the real
 // arguments: a stencil launch never reads its own output sites, so repeating it is harmless.
 // While the stream is being captured into a graph nothing is timed and the default is used.
@@ -51,7 +51,9 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
     for (int nr : nrs) {
         // the batched and register-capped forms are for 32- and 16-bit storage: with FP64 data
         // they spill
-        if (c.nrhs % nr || rpm % nr || (roll >= 2 && (nr != 1 || prec == 64))) continue;
+        if (c.nrhs % nr || rpm % nr || (roll >= 2 && prec == 64) || (roll >= 2 && roll <= 4 && nr != 1) ||
+            (roll == 5 && nr > 2))
+            continue;
         for (int nw : nws)
         for (int nt : nts) {
             if ((c.nrhs / nr) % nw || nt * nw > 256) continue;
@@ -98,7 +100,7 @@ ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll)
         return DDRW_OK;
     }
     if ((nr != 1 && nr != 2 && nr != 4) || nt < 32 || nt > 256 || nt % 32 || nw < 1 || nt * nw > 256 || roll < 0 ||
-        roll > 5 || (roll >= 2 && nr != 1))
+        roll > 5 || (roll >= 2 && roll <= 4 && nr != 1) || (roll == 5 && nr > 2))
         return set_error(ctx, DDRW_EINVAL, "bad stencil configuration");
     ctx->pinned_nr = nr;
     ctx->pinned_nt = nt;

@@ -71,7 +71,8 @@ def test_apply_D_double_single(setup, m):
 
 @pytest.mark.parametrize("nr,nt,nw,roll", [(1, 64, 1, 0), (1, 64, 1, 1), (2, 128, 1, 0), (2, 128, 2, 1),
                                            (4, 32, 2, 0), (4, 256, 1, 1), (1, 32, 8, 1), (1, 128, 1, 2),
-                                           (1, 64, 2, 3), (1, 256, 1, 4), (1, 128, 2, 5)])
+                                           (1, 64, 2, 3), (1, 256, 1, 4), (1, 128, 2, 5),
+                                           (2, 128, 1, 5)])
 def test_every_stencil_configuration(setup, nr, nt, nw, roll):
     """Each pinned launch configuration of the all-hop stencil (right-hand sides per thread, CTA
     shape, unrolled or rolled hop code) gives the oracle's operator on 4 right-hand sides."""
