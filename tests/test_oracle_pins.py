@@ -400,3 +400,63 @@ def test_mass_interpolation_telescopes():
         tot += np.linalg.slogdet(Mi.conj().T @ Mi)[1]
     one = od.ratio_matrix(lat, m1, m2)
     assert abs(tot - np.linalg.slogdet(one.conj().T @ one)[1]) < 1e-9
+
+
+# ---- block determinants of Eq. 7 (oracle/blockdet.py)
+
+def test_block_determinants_factorise_det_D(c1):
+    """Sum over the blocks of one colour of log|det D_k| is log|det D_bb| (D_ww), and with the
+    Schur complement they give log|det D| (Sec. 1) -- every determinant of D_k real (Eq. 7 uses
+    det D_k^2)."""
+    from oracle import blockdet as ob
+    for m in (0.2, -0.3):
+        ld, sg = ob.block_logdets(c1, m)
+        blocks = ob.block_list(c1)
+        nb = len(blocks) // 2
+        assert all(c == 0 for c, _ in blocks[:nb]) and all(c == 1 for c, _ in blocks[nb:])
+        Dbb, _, _, Dww = od.blocks(c1, m)
+        sb, lb = od.logdet(Dbb)
+        sw, lw = od.logdet(Dww)
+        assert abs(ld[:nb].sum() - lb) < 1e-9 * max(1.0, abs(lb))
+        assert abs(ld[nb:].sum() - lw) < 1e-9 * max(1.0, abs(lw))
+        s, lD = od.logdet(od.dense_D(c1, m))
+        _, lS = od.logdet(od.schur(c1, m))
+        assert abs(ld.sum() + lS - lD) < 1e-8 * max(1.0, abs(lD))
+        assert np.all(np.abs(np.imag(sg)) < 1e-9)
+
+
+def test_single_site_blocks_reduce_to_the_site_term():
+    """With l = 1 every block is one site and D_k = A(x) = (4 + m) + C(x): its determinant is the
+    determinant of the 12x12 site matrix, read from the oracle's clover routine."""
+    from oracle import blockdet as ob
+    dims = (2, 2, 2, 2)
+    U = synth.gauge_field(dims, 0.4, seed=17)
+    lat = oc.Lattice(dims, (1, 1, 1, 1), U, 1.3)
+    m = 0.11
+    ld, sg = ob.block_logdets(lat, m)
+    for k, (_, o) in enumerate(ob.block_list(lat)):
+        x = ((o[0] * dims[1] + o[1]) * dims[2] + o[2]) * dims[3] + o[3]
+        s, l = np.linalg.slogdet(lat.clover(x) + (4 + m) * np.eye(12))
+        assert abs(ld[k] - l) < 1e-12 and abs(sg[k] - s) < 1e-12
+
+
+def test_block_determinants_are_gauge_invariant():
+    """A gauge transformation acts on each block operator as a similarity transform, so every
+    block determinant is unchanged; a wrong link index or a missing conjugate breaks this."""
+    from oracle import blockdet as ob
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.4, seed=21)
+    g = synth.gauge_transform(dims, seed=23)
+    X = coords(dims)
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        Y = X.copy()
+        Y[:, mu] = (Y[:, mu] + 1) % dims[mu]
+        ym = ((Y[:, 0] * dims[1] + Y[:, 1]) * dims[2] + Y[:, 2]) * dims[3] + Y[:, 3]
+        Ug[:, mu] = g @ U[:, mu] @ g[ym].conj().transpose(0, 2, 1)
+    ld0, _ = ob.block_logdets(oc.Lattice(dims, (2, 2, 2, 2), U, csw=1.2), 0.07)
+    ld1, _ = ob.block_logdets(oc.Lattice(dims, (2, 2, 2, 2), Ug, csw=1.2), 0.07)
+    assert np.max(np.abs(ld1 - ld0)) < 1e-10
+    # and they do change when the links change (the test is not vacuous)
+    ld2, _ = ob.block_logdets(oc.Lattice(dims, (2, 2, 2, 2), synth.gauge_field(dims, 0.4, seed=22), csw=1.2), 0.07)
+    assert np.max(np.abs(ld2 - ld0)) > 1e-3
