@@ -230,6 +230,23 @@ ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
  * nr = 0 returns to autotuning.  DDRW_EINVAL for values outside these ranges. */
 ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll);
 
+/* The exact block factor of Eq. 7: W = W_gl prod_k det D_k^2(m2) / det D_k^2(m1), k over the black
+ * and the white blocks, D_k the block Dirac operators on the diagonal of D_bb and D_ww (Eq. 1).
+ * ddrw_block_logdet writes log |det D_k(m)| and the sign of det D_k(m) (real by g5-hermiticity)
+ * for every block, in the library's block numbering: black blocks first, then white, each in
+ * lexicographic order of the block coordinates (t slowest); logdet and sign hold nblk = V / l^4
+ * doubles, host or device (sign may be null).  ddrw_block_factor writes
+ * log prod_k det D_k^2(m2) / det D_k^2(m1) for the m1, m2 of ddrw_set_params (two flavours).
+ * Method: det D_k = det A_oo det S_k with S_k = A_ee - D_eo A_oo^-1 D_oe the block's even-odd
+ * Schur complement (dimension 6 l^4), assembled by the FP64 block stencil and factorised by a
+ * batched LU with partial pivoting in FP64 (one CTA per block).  The paper calls the exact block
+ * determinants feasible for l^4 <= 6^4; l > 6 returns DDRW_EINVAL, and blocks are processed in
+ * batches that fit 60 % of the free device memory (DDRW_ENOMEM if one matrix does not fit).
+ * Cost: (6 l^4)^3 / 3 complex FP64 multiply-adds per block and mass -- about a second per block
+ * at l = 4 on one SM, minutes per block at l = 6. */
+ddrw_status ddrw_block_logdet(ddrw_ctx *ctx, double m, double *logdet, double *sign);
+ddrw_status ddrw_block_factor(ddrw_ctx *ctx, double *log_w_blk);
+
 /* Kernel timing for measurement (not part of the method): with profiling enabled, CUDA events
  * bracket every launch of the instrumented kernel classes on the context's stream, and
  * ddrw_profile_read returns, per class, the number of launches, their summed device time (ms) and

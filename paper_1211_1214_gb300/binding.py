@@ -25,7 +25,8 @@ EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", 
            "ddrw_set_params", "ddrw_set_solver", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
-           "ddrw_autotune", "ddrw_autotune_report", "ddrw_stencil_config", "ddrw_profile_units", "ddrw_force", "ddrw_use_graphs",
+           "ddrw_autotune", "ddrw_autotune_report", "ddrw_stencil_config", "ddrw_profile_units",
+           "ddrw_block_logdet", "ddrw_block_factor", "ddrw_force", "ddrw_use_graphs",
            "ddrw_estimate_interp", "ddrw_apply_D_ds"]
 
 #: kernel classes of ddrw_profile_read
@@ -92,6 +93,8 @@ def load(path: str | None = None):
         "ddrw_autotune": (st, [vp, ctypes.c_int]),
         "ddrw_stencil_config": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "ddrw_profile_units": (st, [vp, ctypes.c_int, dp]),
+        "ddrw_block_logdet": (st, [vp, ctypes.c_double, dp, dp]),
+        "ddrw_block_factor": (st, [vp, dp]),
         "ddrw_use_graphs": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long)]),
         "ddrw_estimate_interp": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp, dp, dp,
                                       dp, ctypes.POINTER(SolveInfo)]),
@@ -255,6 +258,20 @@ class Context:
 
     def autotune(self, enable=True):
         self._check(self.L.ddrw_autotune(self._h, int(enable)), "ddrw_autotune")
+
+    def block_logdet(self, m):
+        """log |det D_k(m)| and sign for every block (Eq. 7), library block numbering."""
+        nb = self.V // (self.block[0] * self.block[1] * self.block[2] * self.block[3])
+        ld = np.zeros(nb)
+        sg = np.zeros(nb)
+        self._check(self.L.ddrw_block_logdet(self._h, float(m), _ptr(ld), _ptr(sg)), "ddrw_block_logdet")
+        return ld, sg
+
+    def block_factor(self):
+        """log prod_k det D_k^2(m2) / det D_k^2(m1) for the current m1, m2 (Eq. 7)."""
+        v = ctypes.c_double(0)
+        self._check(self.L.ddrw_block_factor(self._h, ctypes.byref(v)), "ddrw_block_factor")
+        return v.value
 
     def stencil_config(self, nr=0, nt=128, nw=1, roll=0):
         """Pin the stencil launch configuration (nr = 0: back to the autotuner)."""

@@ -54,6 +54,16 @@ ddrw_status workspace(ddrw_ctx *ctx, const char *name, size_t bytes, void **out)
     return DDRW_OK;
 }
 
+void release_workspace(ddrw_ctx *ctx, const char *name)
+{
+    auto it = ctx->ws.find(name);
+    if (it == ctx->ws.end()) return;
+    clear_graphs(ctx);
+    cudaStreamSynchronize(ctx->stream);
+    if (it->second.p) cudaFree(it->second.p);
+    ctx->ws.erase(it);
+}
+
 GeomDev geom_dev(const ddrw_ctx *ctx)
 {
     GeomDev g;

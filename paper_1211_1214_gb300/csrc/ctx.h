@@ -174,6 +174,8 @@ void clear_graphs(ddrw_ctx *ctx);
 
 // device workspace of at least `bytes`, reused across calls under `name`
 ddrw_status workspace(ddrw_ctx *ctx, const char *name, size_t bytes, void **out);
+// frees a workspace (after the stream has drained); for large one-off buffers
+void release_workspace(ddrw_ctx *ctx, const char *name);
 
 GeomDev geom_dev(const ddrw_ctx *ctx);
 
