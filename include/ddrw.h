@@ -242,8 +242,9 @@ ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll)
  * batched LU with partial pivoting in FP64 (one CTA per block).  The paper calls the exact block
  * determinants feasible for l^4 <= 6^4; l > 6 returns DDRW_EINVAL, and blocks are processed in
  * batches that fit 60 % of the free device memory (DDRW_ENOMEM if one matrix does not fit).
- * Cost: (6 l^4)^3 / 3 complex FP64 multiply-adds per block and mass -- about a second per block
- * at l = 4 on one SM, minutes per block at l = 6. */
+ * Cost: (6 l^4)^3 / 3 complex FP64 multiply-adds per block and mass, one SM per block: 16^4
+ * with l = 4 takes about 9 s for both masses (256 blocks), 12^4 with l = 6 about 4 minutes per
+ * mass (16 blocks, 16 SMs busy). */
 ddrw_status ddrw_block_logdet(ddrw_ctx *ctx, double m, double *logdet, double *sign);
 ddrw_status ddrw_block_factor(ddrw_ctx *ctx, double *log_w_blk);
 

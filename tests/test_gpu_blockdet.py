@@ -69,8 +69,8 @@ def test_block_factor_is_gauge_invariant_and_vanishes_at_equal_masses():
 
 
 def test_block_determinants_refuse_large_blocks():
-    ctx = binding.Context((16, 8, 8, 8), (8, 8, 8, 8))
-    ctx.load_gauge(synth.gauge_field((16, 8, 8, 8), 0.2, seed=1))
+    ctx = binding.Context((16, 16, 16, 16), (8, 8, 8, 8))
+    ctx.load_gauge(synth.gauge_field((16, 16, 16, 16), 0.2, seed=1))
     ctx.set_params(1.0, 0.1, 0.09)
     with pytest.raises(binding.DDRWError) as ei:
         ctx.block_factor()
