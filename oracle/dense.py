@@ -10,6 +10,10 @@ mirror the paper's statements:
 * Eq. 3   the Gaussian integral 1/det(M^dag M) and its estimator exp(-eta^dag (M^dag M - 1) eta);
 * Eq. 4   sigma_s^2 = 1/det(2 M^dag M - 1) - 1/det(M^dag M)^2;
 * Eq. 5/6 det M^-1 = prod lambda/(lambda + dm), lambda(M) = 1 + dm lambda(D^-1(m2)).
+* Sec. 2   the other operators whose ratio the estimator can sample (Fig. 1's variants): the total
+          operator, M = D(m2)^-1 D(m1), and the even-odd Schur complement
+          S = A_ee - D_eo A_oo^-1 D_oe (the block Schur complement for blocks of one site),
+          M = S(m2)^-1 S(m1); supports in lexicographic site order.
 """
 from __future__ import annotations
 
@@ -65,6 +69,31 @@ def schur_on_P(lat, m) -> np.ndarray:
 def ratio_matrix(lat, m1, m2) -> np.ndarray:
     """Mhat = A(m2)^-1 A(m1) on supp P (Eq. 8 with N = 1, restricted to the support of P)."""
     return np.linalg.solve(schur_on_P(lat, m2), schur_on_P(lat, m1))
+
+
+def ratio_matrix_total(lat, m1, m2) -> np.ndarray:
+    """M = D(m2)^-1 D(m1) on all 12 V components (lexicographic site order)."""
+    return np.linalg.solve(dense_D(lat, m2), dense_D(lat, m1))
+
+
+def even_components(lat) -> np.ndarray:
+    """Component indices (into 12 V) of the even sites (t + x + y + z even), ascending."""
+    X = np.stack(np.unravel_index(np.arange(lat.V), lat.dims), -1)
+    even = np.nonzero(X.sum(1) % 2 == 0)[0]
+    return (even[:, None] * 12 + np.arange(12)[None, :]).reshape(-1)
+
+
+def schur_eo(lat, m) -> np.ndarray:
+    """S(m) = D_ee - D_eo D_oo^-1 D_oe on the even components (D_ee = A_ee, D_oo = A_oo)."""
+    D = dense_D(lat, m)
+    e = even_components(lat)
+    o = np.setdiff1d(np.arange(12 * lat.V), e)
+    return D[np.ix_(e, e)] - D[np.ix_(e, o)] @ np.linalg.solve(D[np.ix_(o, o)], D[np.ix_(o, e)])
+
+
+def ratio_matrix_eo(lat, m1, m2) -> np.ndarray:
+    """M = S(m2)^-1 S(m1) on the even components."""
+    return np.linalg.solve(schur_eo(lat, m2), schur_eo(lat, m1))
 
 
 def exponent(Mh: np.ndarray, eta_packed: np.ndarray) -> np.ndarray:

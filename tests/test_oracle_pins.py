@@ -460,3 +460,27 @@ def test_block_determinants_are_gauge_invariant():
     # and they do change when the links change (the test is not vacuous)
     ld2, _ = ob.block_logdets(oc.Lattice(dims, (2, 2, 2, 2), synth.gauge_field(dims, 0.4, seed=22), csw=1.2), 0.07)
     assert np.max(np.abs(ld2 - ld0)) > 1e-3
+
+
+# ---- the operators of Fig. 1's comparison (oracle/dense.py): total, even-odd, block Schur
+
+def test_estimator_operators_factorise_the_determinant_ratio(c1):
+    """det D = det A_oo det S (even-odd) and det D = det Dhat det D_bb det D_ww (Sec. 1), so the
+    three ratio matrices carry the same determinant ratio up to exactly known site and block
+    factors: log det M_total = log det M_eo + log det A_oo(m1) - log det A_oo(m2)
+                             = log det Mh + sum_k [log det D_k(m1) - log det D_k(m2)]   (Eq. 7)."""
+    from oracle import blockdet as ob
+    m1, m2 = 0.20, 0.15
+    st, lt = od.logdet(od.ratio_matrix_total(c1, m1, m2))
+    se, le = od.logdet(od.ratio_matrix_eo(c1, m1, m2))
+    sh, lh = od.logdet(od.ratio_matrix(c1, m1, m2))
+    # det A_oo(m): product over odd sites of det((4 + m) + C(x)) from the oracle's clover matrix
+    X = np.stack(np.unravel_index(np.arange(c1.V), c1.dims), -1)
+    odd = np.nonzero(X.sum(1) % 2 == 1)[0]
+    lA = lambda m: sum(np.linalg.slogdet(c1.clover(x) + (4 + m) * np.eye(12))[1] for x in odd)
+    assert abs(lt - (le + lA(m1) - lA(m2))) < 1e-9
+    b1, _ = ob.block_logdets(c1, m1)
+    b2, _ = ob.block_logdets(c1, m2)
+    assert abs(lt - (lh + b1.sum() - b2.sum())) < 1e-9
+    # the ratio matrices differ (the estimator's variance depends on the choice, Fig. 1)
+    assert abs(lt - lh) > 1e-3
