@@ -104,6 +104,41 @@ def stencil_one_rhs(ctx, w, prec, key, hbm, tol_block):
             "what": "same stencil kernel, 1 right-hand side per launch (links and clover not amortised)"}
 
 
+def fig1(args):
+    """Synthetic analogue of Fig. 1 (Sec. 2): the relative stochastic variance sigma^2(W)/W^2 of the
+    interpolated two-flavour estimate against the number of interpolation steps N at a fixed
+    number of solves N * N_hit, for the total operator, the even-odd Schur complement (blocks of one
+    site) and the block Schur complement with several block lengths, one synthetic configuration.
+    sigma^2(W)/W^2 = prod_i (1 + v_i / N_hit) - 1 with v_i the sample variance of exp(-e_ij) over
+    its squared mean in factor i (independent factors, each a mean of N_hit samples)."""
+    import torch
+    from paper_1211_1214_gb300 import binding, synth
+    dims, eps, csw, m1, m2, total = (16, 16, 16, 16), 0.25, 1.5, 0.05, 0.02, 96
+    U = torch.from_numpy(synth.gauge_field(dims, eps, seed=1)).cuda()
+    V = int(np.prod(dims))
+    variants = [("total", 0, 4), ("even-odd (l=1)", 1, 4)] + [(f"blocks l={l}", 2, l) for l in (2, 4, 8)]
+    rows = []
+    t0 = time.perf_counter()
+    for name, var, l in variants:
+        ctx = binding.Context(dims, (l,) * 4)
+        ctx.load_gauge(U)
+        ctx.set_params(csw, m1, m2)
+        ctx.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-10)
+        pts = []
+        for N in (1, 2, 4, 8):
+            nhit = total // N
+            e, lw, rv, dim, _ = ctx.estimate_variant(var, N, nhit, seed=2)
+            rel = float(np.prod(1.0 + rv / nhit) - 1.0)
+            pts.append({"N": N, "N_hit": nhit, "rel_var": rel, "logW": lw})
+        rows.append({"operator": name, "dim_over_12V": dim / (12.0 * V), "points": pts})
+        ctx.close()
+    print(json.dumps({"metric": "relative stochastic variance sigma^2(W)/W^2 vs N at N*N_hit = %d" % total,
+                      "config": {"lattice": list(dims), "eps": eps, "csw": csw, "m1": m1, "m2": m2,
+                                 "precision": "FP32 inner solves, FP64 defect correction, residual 1e-10"},
+                      "data": "synthetic (U = exp(i eps H), seed 1; Philox noise, seed 2)",
+                      "variants": rows, "seconds": time.perf_counter() - t0}), flush=True)
+
+
 def describe(name, w, prec):
     return (f"{name} lattice, {w['l']}^4 blocks, U=exp(i {w['eps']} H) seed 1, csw {w['csw']}, m1 {w['m1']}, "
             f"m2 in {list(w['m2s'])}, N_hit {w['nhit']}, {prec} inner solves, FP64 defect correction, "
@@ -271,6 +306,8 @@ def main():
     ap.add_argument("--fp64-hits", type=int, default=2, help="noise vectors of the FP64-path comparison (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fig1", action="store_true",
+                    help="run the synthetic Fig. 1 analogue (variance vs interpolation steps per operator) instead")
     ap.add_argument("--stencil-config", default=None,
                     help="pin the stencil launch form nr,nt,nw,roll (ddrw_stencil_config) instead of autotuning")
     args = ap.parse_args()
@@ -279,6 +316,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, w, name)
+        return
+    if args.fig1:
+        fig1(args)
         return
 
     import torch

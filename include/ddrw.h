@@ -152,6 +152,22 @@ ddrw_status ddrw_noise(ddrw_ctx *ctx, uint64_t seed, uint64_t hit_offset, int nh
 ddrw_status ddrw_estimate(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64_t hit_offset, const double *eta,
                           double *exponents, double *logW, double *rel_var, double *delta, ddrw_solve_info *info);
 
+/* The global factor of Eq. 8 (mass interpolation, N steps, nhit noise vectors per factor) for the
+ * operators Fig. 1 compares (Sec. 2): variant 0 the total operator, Mh_i = D(m_i)^-1 D(m_{i-1}) on
+ * all 12 V components; variant 1 the even-odd Schur complement S = A_ee - D_eo A_oo^-1 D_oe (the
+ * block Schur complement for blocks of one site), Mh_i = S(m_i)^-1 S(m_{i-1}) on the 6 V
+ * components of the even sites; variant 2 the block Schur complement of this context (as
+ * ddrw_estimate_interp).  m_i = (i/N) m2 + ((N-i)/N) m1.  exponents[N][nhit] (optional) =
+ * eta^dag (Mh_i^dag Mh_i - 1) eta, *logW (optional) = sum_i log((1/nhit) sum_j exp(-e_ij)),
+ * rel_var[N] (optional) = per-factor sample variance of exp(-e_ij) over its squared mean, *dim
+ * (optional) = the dimension of the support (12 V, 6 V or 12 dim P).  Noise: eta (variants 0 and
+ * 1 only; packed [N][nhit][dim] complex, sites of the support in lexicographic order, 12
+ * components each) or Philox (seed, hit hit_offset + i nhit + j, component index in that packed
+ * order).  1 <= N <= 8. */
+ddrw_status ddrw_estimate_variant(ddrw_ctx *ctx, int variant, int N, int nhit, uint64_t seed, uint64_t hit_offset,
+                                  const double *eta, double *exponents, double *logW, double *rel_var, long *dim,
+                                  ddrw_solve_info *info);
+
 /* The estimate for several target masses in one batched call (the mass sweep of a reweighting
  * study): right-hand side k * nhit + j carries m2[k] and noise vector j (the same noise vectors for
  * every mass), all in one multi-right-hand-side pass.  exponents[nmass * nhit], logW[nmass] and

@@ -26,7 +26,7 @@ EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", 
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
            "ddrw_autotune", "ddrw_autotune_report", "ddrw_stencil_config", "ddrw_profile_units",
-           "ddrw_block_logdet", "ddrw_block_factor", "ddrw_force", "ddrw_use_graphs",
+           "ddrw_block_logdet", "ddrw_block_factor", "ddrw_estimate_variant", "ddrw_force", "ddrw_use_graphs",
            "ddrw_estimate_interp", "ddrw_apply_D_ds"]
 
 #: kernel classes of ddrw_profile_read
@@ -95,6 +95,8 @@ def load(path: str | None = None):
         "ddrw_profile_units": (st, [vp, ctypes.c_int, dp]),
         "ddrw_block_logdet": (st, [vp, ctypes.c_double, dp, dp]),
         "ddrw_block_factor": (st, [vp, dp]),
+        "ddrw_estimate_variant": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                       dp, dp, dp, dp, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(SolveInfo)]),
         "ddrw_use_graphs": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long)]),
         "ddrw_estimate_interp": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp, dp, dp,
                                       dp, ctypes.POINTER(SolveInfo)]),
@@ -266,6 +268,21 @@ class Context:
         sg = np.zeros(nb)
         self._check(self.L.ddrw_block_logdet(self._h, float(m), _ptr(ld), _ptr(sg)), "ddrw_block_logdet")
         return ld, sg
+
+    def estimate_variant(self, variant, N, nhit, seed=2, hit_offset=0, eta=None):
+        """Fig. 1's operator variants (0 total, 1 even-odd, 2 blocks) of the interpolated estimate:
+        returns (exponents [N, nhit], log W, rel_var [N], support dimension, solve info)."""
+        e = np.zeros((N, nhit))
+        rv = np.zeros(N)
+        lw = ctypes.c_double(0)
+        dim = ctypes.c_long(0)
+        info = SolveInfo()
+        ep = None if eta is None else np.ascontiguousarray(eta, dtype=np.complex128)
+        st = self.L.ddrw_estimate_variant(self._h, int(variant), int(N), int(nhit), int(seed), int(hit_offset),
+                                          None if ep is None else _ptr(ep), _ptr(e), ctypes.byref(lw), _ptr(rv),
+                                          ctypes.byref(dim), ctypes.byref(info))
+        self._check(st, "ddrw_estimate_variant")
+        return e, lw.value, rv, dim.value, info.as_dict()
 
     def block_factor(self):
         """log prod_k det D_k^2(m2) / det D_k^2(m1) for the current m1, m2 (Eq. 7)."""

@@ -132,6 +132,84 @@ static void noise_launch(ddrw_ctx *ctx, uint64_t seed, uint64_t hit0, int nhit, 
                                            (uint32_t)(seed >> 32), hit0, nhit, nrep, field, packed);
 }
 
+// ---- supports of the operator variants of Fig. 1's comparison (ddrw_estimate_variant)
+
+// idx[i] = internal index of the i-th site of the support in lexicographic order: every site
+// (even_only = 0) or the even sites (t + x + y + z even; Z even, so every z-row holds Z/2 of them)
+template <int BL>
+__global__ void k_support(GeomDev g, int even_only, long n, int *idx)
+{
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int t, x, y, z;
+    if (even_only) {
+        const int zh = g.L[3] / 2;
+        long row = i / zh;
+        int j = (int)(i - row * zh);
+        y = (int)(row % g.L[2]);
+        row /= g.L[2];
+        x = (int)(row % g.L[1]);
+        t = (int)(row / g.L[1]);
+        z = 2 * j + ((t + x + y) & 1);
+    } else {
+        long r = i;
+        z = (int)(r % g.L[3]);
+        r /= g.L[3];
+        y = (int)(r % g.L[2]);
+        r /= g.L[2];
+        x = (int)(r % g.L[1]);
+        t = (int)(r / g.L[1]);
+    }
+    idx[i] = (int)internal_index<BL>(g, t, x, y, z);
+}
+
+// caller's packed noise (nhit vectors of 12 n complex components, support order) -> fields
+__global__ void k_scatter_packed(const int *__restrict__ idx, long n, const double *__restrict__ packed, long V,
+                                 double2 *field)
+{
+    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 12 * n) return;
+    const int h = blockIdx.y;
+    const long j = k / 12;
+    const int comp = (int)(k - j * 12);
+    const double *p = packed + ((long)h * 12 * n + k) * 2;
+    field[((long)h * 12 + comp) * V + idx[j]] = make_double2(p[0], p[1]);
+}
+
+// out_e = S(m) in_e with S = A_ee - 1/4 H_eo A_oo^-1 H_oe (FP64, all blocks; tmp holds A_oo^-1 H_oe in)
+static ddrw_status apply_schur_eo64(ddrw_ctx *ctx, double m, const double2 *in, double2 *out, double2 *tmp,
+                                    int nrhs)
+{
+    MassInv *mi;
+    ddrw_status st = mass_inverse(ctx, m, &mi);
+    if (st) return st;
+    DslashCall c;
+    c.in = in;
+    c.out = tmp;
+    c.rstride = 12 * ctx->V;
+    c.nrhs = nrhs;
+    c.masses[0] = m;
+    c.Ainv[0] = mi->A64;
+    c.beta = 1.0;
+    c.post = 1;
+    c.par0 = 1;
+    c.npar = 1;
+    c.blk0 = 0;
+    c.nblk = ctx->nblk;
+    dslash64(ctx, c);
+    DslashCall d = c;
+    d.in = tmp;
+    d.x = in;
+    d.out = out;
+    d.alpha = 1.0;
+    d.beta = -0.25;
+    d.diag = 1;
+    d.post = 0;
+    d.par0 = 0;
+    dslash64(ctx, d);
+    return DDRW_OK;
+}
+
 // hop between blocks: out (colour rows) = -1/2 H_{rows <- other colour} in ; other rows untouched
 static void hop_between(ddrw_ctx *ctx, int rows, const double2 *in, double2 *out, int nrhs)
 {
@@ -510,6 +588,108 @@ ddrw_status ddrw_estimate_interp(ddrw_ctx *ctx, int N, int nhit, uint64_t seed, 
         logW[2] = sg;        // sign of W_1f
         logW[3] = 0.5 * l2;  // root trick: log sqrt(W_gl)
     }
+    fill_info(info, stats, elapsed(t0));
+    for (double v : e)
+        if (!(v == v)) return set_error(ctx, DDRW_ENUMERIC, "NaN exponent");
+    return conv;
+}
+
+ddrw_status ddrw_estimate_variant(ddrw_ctx *ctx, int variant, int N, int nhit, uint64_t seed, uint64_t hit_offset,
+                                  const double *eta, double *exponents, double *logW, double *rel_var, long *dim,
+                                  ddrw_solve_info *info)
+{
+    if (!ctx) return DDRW_EINVAL;
+    if (variant < 0 || variant > 2) return set_error(ctx, DDRW_EINVAL, "variant 0 (total), 1 (even-odd) or 2 (blocks)");
+    if (N < 1 || N > MAXM || nhit <= 0) return set_error(ctx, DDRW_EINVAL, "1 <= N <= 8 interpolation steps, nhit > 0");
+    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
+    cudaSetDevice(ctx->device);
+    if (variant == 2) {
+        if (eta) return set_error(ctx, DDRW_EINVAL, "the block variant draws its own noise (ddrw_estimate_interp)");
+        double lw[4];
+        if (dim) *dim = 12 * ctx->nP;
+        ddrw_status st = ddrw_estimate_interp(ctx, N, nhit, seed, hit_offset, exponents, nullptr, lw, nullptr,
+                                              rel_var, info);
+        if (logW) *logW = lw[0];
+        return st;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    const long V = ctx->V, nsites = variant == 0 ? V : ctx->vh;
+    if (dim) *dim = 12 * nsites;
+    ddrw_status st;
+    int *idx;
+    if ((st = workspace(ctx, "var_idx", sizeof(int) * nsites, (void **)&idx))) return st;
+    DISPATCH_BL(ctx, k_support, (unsigned)((nsites + 255) / 256), 256, geom_dev(ctx), variant == 1 ? 1 : 0, nsites,
+                idx);
+    ++ctx->launches;
+    std::vector<double> ma(N), mb(N);
+    for (int i = 1; i <= N; i++) {
+        ma[i - 1] = ((double)(i - 1) * ctx->m2 + (double)(N - i + 1) * ctx->m1) / N;
+        mb[i - 1] = ((double)i * ctx->m2 + (double)(N - i) * ctx->m1) / N;
+    }
+    const int budget = std::max(1, (ctx->max_rhs > 0 ? ctx->max_rhs : rhs_budget(ctx)) / 2);
+    const int hper = std::min(nhit, budget);
+    double2 *F[4];
+    if ((st = fields(ctx, "var_f", 4, hper, F))) return st;
+    double *nd;
+    if ((st = workspace(ctx, "var_nd", sizeof(double) * 3 * hper, (void **)&nd))) return st;
+    std::vector<double> e((size_t)N * nhit), h(3 * (size_t)hper);
+    SolveStats stats;
+    ddrw_status conv = DDRW_OK;
+    const size_t fb = sizeof(double2) * 12 * (size_t)V;
+    for (int i = 0; i < N; i++) {
+        MassSet mbs;
+        if ((st = make_massset(ctx, 1, &mb[i], &mbs))) return st;
+        const double dm = ma[i] - mb[i];
+        for (int j0 = 0; j0 < nhit; j0 += hper) {
+            const int jn = std::min(hper, nhit - j0);
+            DDRW_CUDA_CHECK(cudaMemsetAsync(F[0], 0, fb * jn, ctx->stream));
+            ++ctx->launches;
+            dim3 grid((unsigned)((12 * nsites + 255) / 256), (unsigned)jn);
+            if (eta)
+                k_scatter_packed<<<grid, 256, 0, ctx->stream>>>(idx, nsites, eta + 2 * 12 * nsites * ((size_t)i * nhit + j0),
+                                                                V, F[0]);
+            else
+                k_noise<<<grid, 256, 0, ctx->stream>>>(V, nsites, idx, (uint32_t)(seed & 0xffffffffu),
+                                                       (uint32_t)(seed >> 32), hit_offset + (uint64_t)i * nhit + j0, jn,
+                                                       1, F[0], nullptr);
+            const double2 *rhs = F[0];
+            if (variant == 1) {
+                // rhs_e = (S(m_{i-1}) - S(m_i)) eta_e, odd sites zero; the solution's even part is
+                // S(m_i)^-1 rhs_e = delta (the full solve with b_o = 0)
+                if ((st = apply_schur_eo64(ctx, ma[i], F[0], F[2], F[1], jn))) return st;
+                DDRW_CUDA_CHECK(cudaMemsetAsync(F[3], 0, fb * jn, ctx->stream));
+                if ((st = apply_schur_eo64(ctx, mb[i], F[0], F[3], F[1], jn))) return st;
+                Blas<PrecD>::axpby(ctx, VecRange{V, 0, ctx->vh, 12 * V, jn}, 1.0, F[2], -1.0, F[3]);
+                rhs = F[3];
+            }
+            SolveStats s1;
+            st = full_solve64(ctx, mbs, rhs, F[1], jn, ctx->tol_outer, ctx->maxiter, ctx->prec, &s1);
+            if (st == DDRW_ENOCONV) conv = st;
+            else if (st) return st;
+            stats.outer_iters += s1.outer_iters;
+            stats.outer_cycles = std::max(stats.outer_cycles, s1.outer_cycles);
+            stats.fp64_dslash_full += s1.fp64_dslash_full;
+            stats.outer_rel_residual = std::max(stats.outer_rel_residual, s1.outer_rel_residual);
+            // total: delta = dm x, e = dm^2 |x|^2 + 2 dm Re <eta, x>;  even-odd: delta = x_e
+            const long n_range = variant == 0 ? V : ctx->vh;
+            if ((st = Blas<PrecD>::norm_dot(ctx, VecRange{V, 0, n_range, 12 * V, jn}, F[1], F[0], nd))) return st;
+            DDRW_CUDA_CHECK(cudaMemcpyAsync(h.data(), nd, sizeof(double) * 3 * jn, cudaMemcpyDeviceToHost, ctx->stream));
+            DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+            for (int j = 0; j < jn; j++) {
+                const double a = h[3 * j], b = h[3 * j + 1];
+                e[(size_t)i * nhit + j0 + j] = variant == 0 ? dm * dm * a + 2.0 * dm * b : a + 2.0 * b;
+            }
+        }
+    }
+    double l2 = 0;
+    for (int i = 0; i < N; i++) {
+        double lf, rv;
+        two_flavour_factor(e.data() + (size_t)i * nhit, nhit, &lf, &rv);
+        l2 += lf;
+        if (rel_var) rel_var[i] = rv;
+    }
+    if (exponents) std::copy(e.begin(), e.end(), exponents);
+    if (logW) *logW = l2;
     fill_info(info, stats, elapsed(t0));
     for (double v : e)
         if (!(v == v)) return set_error(ctx, DDRW_ENUMERIC, "NaN exponent");
