@@ -113,7 +113,9 @@ def fig1(args):
     its squared mean in factor i (independent factors, each a mean of N_hit samples)."""
     import torch
     from paper_1211_1214_gb300 import binding, synth
-    dims, eps, csw, m1, m2, total = (16, 16, 16, 16), 0.25, 1.5, 0.05, 0.02, 96
+    # dm = 0.006: the exponents of the total operator spread by O(1) at N = 1 (the fluctuations
+    # grow like dm^2 V), the regime of Fig. 1 where the variance estimates are meaningful
+    dims, eps, csw, m1, m2, total = (16, 16, 16, 16), 0.25, 1.5, 0.05, 0.044, 192
     U = torch.from_numpy(synth.gauge_field(dims, eps, seed=1)).cuda()
     V = int(np.prod(dims))
     variants = [("total", 0, 4), ("even-odd (l=1)", 1, 4)] + [(f"blocks l={l}", 2, l) for l in (2, 4, 8)]
@@ -129,7 +131,8 @@ def fig1(args):
             nhit = total // N
             e, lw, rv, dim, _ = ctx.estimate_variant(var, N, nhit, seed=2)
             rel = float(np.prod(1.0 + rv / nhit) - 1.0)
-            pts.append({"N": N, "N_hit": nhit, "rel_var": rel, "logW": lw})
+            pts.append({"N": N, "N_hit": nhit, "rel_var": rel, "logW": lw,
+                        "std_e_per_factor": float(np.mean(np.std(e, axis=1, ddof=1)))})
         rows.append({"operator": name, "dim_over_12V": dim / (12.0 * V), "points": pts})
         ctx.close()
     print(json.dumps({"metric": "relative stochastic variance sigma^2(W)/W^2 vs N at N*N_hit = %d" % total,
