@@ -142,6 +142,21 @@ def fig1(args):
                       "variants": rows, "seconds": time.perf_counter() - t0}), flush=True)
 
 
+def variance_check(E, RV, m2s, nhit):
+    """Per target mass: the sample relative variance of exp(-e_j) (Eq. 4 estimated from the
+    samples) beside its small-dm expansion.  With X = Mh^dag Mh - 1, Eq. 4 gives
+    sigma^2/W^2 = det(M^dag M)^2 / det(2 M^dag M - 1) - 1 = exp(tr X^2 + O(X^3)) - 1, and for complex
+    Gaussian noise with E|eta|^2 = 1 the exponent e = eta^dag X eta has variance tr X^2, so the
+    expansion is exp(Var e) - 1 with Var e the sample variance of the exponents."""
+    E = np.asarray(E, dtype=np.float64).reshape(len(m2s), nhit)
+    out = []
+    for k, m2 in enumerate(m2s):
+        ve = float(np.var(E[k], ddof=1))
+        out.append({"m2": m2, "rel_var_samples": float(RV[k]), "expansion_exp_var_e_minus_1": float(np.expm1(ve)),
+                    "var_e": ve})
+    return out
+
+
 def describe(name, w, prec):
     return (f"{name} lattice, {w['l']}^4 blocks, U=exp(i {w['eps']} H) seed 1, csw {w['csw']}, m1 {w['m1']}, "
             f"m2 in {list(w['m2s'])}, N_hit {w['nhit']}, {prec} inner solves, FP64 defect correction, "
@@ -463,6 +478,7 @@ def main():
                       "block_iters_max": infos[-1]["block_iters_max"],
                       "true_rel_residual": infos[-1]["true_rel_residual"]},
            "logW": [float(x) for x in LW], "wall_s_timed": wall,
+           "variance_check": variance_check(E, RV, m2s, nhit),
            "autotune": ctx.autotune_report().strip().splitlines(),
            "graph_launches_total": graphs_timed}
 
