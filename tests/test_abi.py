@@ -48,3 +48,19 @@ def test_create_rejects_bad_geometry_without_touching_the_gpu(lib):
     for dims, blk in bad:
         st = L.ddrw_create(ctypes.byref(h), (ctypes.c_int * 4)(*dims), (ctypes.c_int * 4)(*blk), 0, None)
         assert st == 1, (dims, blk)
+
+
+@pytest.mark.parametrize("dims,block", [
+    ((256, 256, 256, 16), 8),   # 2^28 sites: above the 2^27 limit of the kernels' 32-bit in-field offsets
+    ((8, 8, 8, 8), 8),          # one block per direction (blocks must alternate in colour: >= 2, even)
+    ((12, 12, 12, 12), 4),      # three blocks per direction (odd)
+    ((6, 6, 6, 6), 3),          # block length 3 (2, 4, 6, 8 are built)
+    ((8, 8, 8, 8), (4, 4, 2, 2)),  # non-hypercubic blocks
+    ((8, 8, 0, 8), 2),          # empty lattice
+])
+def test_geometry_is_validated_before_any_device_call(lib, dims, block):
+    """ddrw_create rejects a geometry the kernels do not support with DDRW_EINVAL before it touches
+    the device (so this runs without a GPU)."""
+    with pytest.raises(binding.DDRWError) as ei:
+        binding.Context(dims, block)
+    assert ei.value.status == 1

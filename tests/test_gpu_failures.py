@@ -72,3 +72,32 @@ def test_calls_before_a_gauge_field_are_refused():
         c.apply_D(0.1, b, np.zeros_like(b))
     assert ei.value.status == 7  # DDRW_ESTATE
     c.close()
+
+
+def test_empty_and_oversized_requests_are_refused(ctx):
+    c, dims = ctx
+    b = synth.spinor_field(dims, seed=86)
+    assert c.L.ddrw_apply_D(c._h, 0.1, b.ctypes.data, b.ctypes.data, 0) == 1      # nrhs = 0
+    with pytest.raises(binding.DDRWError) as ei:
+        c.estimate(0)                                                            # no noise vectors
+    assert ei.value.status == 1
+    with pytest.raises(binding.DDRWError) as ei:
+        c.estimate_masses([0.04] * 9, 2)                                         # at most 8 mass slots
+    assert ei.value.status == 1
+    with pytest.raises(binding.DDRWError) as ei:
+        c.estimate_variant(3, 1, 2)                                              # no such operator variant
+    assert ei.value.status == 1
+
+
+def test_eight_mass_slots_in_one_pass(ctx):
+    """The largest batch of target masses (8 slots) agrees with single-mass estimates."""
+    c, dims = ctx
+    c.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+    m2s = [0.045 - 0.002 * k for k in range(8)]
+    e, lw, _, _ = c.estimate_masses(m2s, 2, seed=4)
+    e = np.asarray(e).reshape(8, 2)
+    for k in (0, 7):
+        c.set_params(1.5, 0.05, m2s[k])
+        e1, _, _, _ = c.estimate(2, seed=4)
+        assert np.all(np.abs(e[k] - e1) <= 1e-8 * np.maximum(np.abs(e1), 1.0))
+    c.set_params(1.5, 0.05, 0.045)
