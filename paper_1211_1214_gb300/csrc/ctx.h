@@ -115,7 +115,7 @@ struct ddrw_ctx {
     // CUDA graphs of the outer Krylov loop, by launch shape and buffers
     bool use_graphs = true;
     long graph_launches = 0;
-    std::map<std::array<uintptr_t, 24>, ddrw::GraphEntry> graphs;
+    std::map<std::array<uintptr_t, 13 + 2 * ddrw::MAXM>, ddrw::GraphEntry> graphs;
 
     // stencil autotuner (dslash_tune.cu); pinned_nr > 0 overrides it with the pinned configuration
     bool autotune = true;

@@ -8,6 +8,9 @@
 // double-length arithmetic with a fused multiply-add).  Every operation is written with the
 // round-to-nearest intrinsics, which the compiler never contracts or reassociates.
 //
+// Sums of products (link and clover multiplies) use accumulated pairs normalised once per result
+// (dd_acc below).
+//
 // Storage: a "split" field holds one complex number per 16-byte element (re.hi, re.lo, im.hi,
 // im.lo), the same bytes as an FP64 field; links (9 complex per direction) and the clover term
 // (72 reals per site) are split once per configuration, the stencil input once per residual, and
@@ -53,6 +56,98 @@ __device__ __forceinline__ dd operator*(dd a, dd b)
     return dd(h, __fsub_rn(e, __fsub_rn(h, p)));
 }
 __device__ __forceinline__ bool operator!=(dd a, dd b) { return a.hi != b.hi || a.lo != b.lo; }
+
+// ---- accumulated products.  A sum of products sum_k x_k y_k is kept as an unnormalised pair:
+// each product's leading part enters the leading word through a two-sum, its rounding error and
+// the two-sum's error collect in the trailing word, and the pair is normalised once at the end
+// (12 FP32 operations per product instead of 18 for a normalised product plus a normalised sum).
+struct dd_acc {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void mac(dd x, dd y)  // += x y
+    {
+        float p = __fmul_rn(x.hi, y.hi);
+        float e = __fmaf_rn(x.hi, y.hi, -p);
+        e = __fmaf_rn(x.hi, y.lo, e);
+        e = __fmaf_rn(x.lo, y.hi, e);
+        float s = __fadd_rn(hi, p);
+        float v = __fsub_rn(s, hi);
+        float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(t, e));
+    }
+    __device__ __forceinline__ void msub(dd x, dd y) { mac(x, dd(-y.hi, -y.lo)); }  // -= x y
+    __device__ __forceinline__ dd get() const
+    {
+        float h = __fadd_rn(hi, lo);
+        return dd(h, __fsub_rn(lo, __fsub_rn(h, hi)));
+    }
+};
+
+// w = U h and w = U^dag h on the two spin components of a half spinor, in accumulated form
+template <> __device__ __forceinline__ void link_mul<dd>(const Link<dd> &U, const Half<dd> &h, Half<dd> &w)
+{
+#pragma unroll
+    for (int s = 0; s < 2; s++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            dd_acc re, im;
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                re.mac(U.m[a][b].re, h.v[s][b].re);
+                re.msub(U.m[a][b].im, h.v[s][b].im);
+                im.mac(U.m[a][b].re, h.v[s][b].im);
+                im.mac(U.m[a][b].im, h.v[s][b].re);
+            }
+            w.v[s][a] = cpx<dd>{re.get(), im.get()};
+        }
+}
+template <> __device__ __forceinline__ void link_dag_mul<dd>(const Link<dd> &U, const Half<dd> &h, Half<dd> &w)
+{
+#pragma unroll
+    for (int s = 0; s < 2; s++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            dd_acc re, im;
+#pragma unroll
+            for (int b = 0; b < 3; b++) {  // conj(U[b][a]) h[b]
+                re.mac(U.m[b][a].re, h.v[s][b].re);
+                re.mac(U.m[b][a].im, h.v[s][b].im);
+                im.mac(U.m[b][a].re, h.v[s][b].im);
+                im.msub(U.m[b][a].im, h.v[s][b].re);
+            }
+            w.v[s][a] = cpx<dd>{re.get(), im.get()};
+        }
+}
+
+// out = (diag + H) v for a packed Hermitian 6x6 H (layout of herm6_mul), in accumulated form
+template <> __device__ __forceinline__ void herm6_mul<dd>(const dd *c, dd diag, const cpx<dd> *v, cpx<dd> *out)
+{
+    dd_acc re[6], im[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        const dd d = diag + c[i];
+        re[i].mac(d, v[i].re);
+        im[i].mac(d, v[i].im);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; i++)
+#pragma unroll
+        for (int j = i + 1; j < 6; j++) {
+            const int o = 6 + 2 * herm_off(i, j);
+            const dd hr = c[o], hi = c[o + 1];
+            // out_i += h_ij v_j ; out_j += conj(h_ij) v_i
+            re[i].mac(hr, v[j].re);
+            re[i].msub(hi, v[j].im);
+            im[i].mac(hr, v[j].im);
+            im[i].mac(hi, v[j].re);
+            re[j].mac(hr, v[i].re);
+            re[j].mac(hi, v[i].im);
+            im[j].mac(hr, v[i].im);
+            im[j].msub(hi, v[i].re);
+        }
+#pragma unroll
+    for (int i = 0; i < 6; i++) out[i] = cpx<dd>{re[i].get(), im[i].get()};
+}
 
 // Storage policy of the double-single stencil: split spinors, links and clover in, FP64 out.
 struct PrecDD {

@@ -180,7 +180,7 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
         // iterations and the condition kernel; no host round trip until convergence or the cap
         int *count;
         if ((st = workspace(ctx, "eo_graph_count", sizeof(int), (void **)&count))) return st;
-        std::array<uintptr_t, 24> key{};
+        std::array<uintptr_t, 13 + 2 * MAXM> key{};
         key[0] = P::ID;
         key[1] = (uintptr_t)nrhs;
         key[2] = (uintptr_t)maxiter;
@@ -188,12 +188,11 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
         for (int k = 0; k < 9; k++) key[3 + k] = (uintptr_t)ptrs[k];
         key[12] = (uintptr_t)ms.n;
         // masses and the device arrays of their inverses are baked into the captured launches
-        for (int k = 0; k < ms.n && k < 5; k++) {
+        for (int k = 0; k < ms.n; k++) {  // at most MAXM slots (make_massset)
             double mk = ms.m[k];
             memcpy(&key[13 + 2 * k], &mk, sizeof(double));
             key[14 + 2 * k] = (uintptr_t)ainv_for(ms.inv[k], P::ID);
         }
-        if (ms.n > 5) return set_error(ctx, DDRW_EINVAL, "graph key holds up to 5 masses");
         auto git = ctx->graphs.find(key);
         cudaGraphExec_t exec = nullptr;
         if (git != ctx->graphs.end()) {
