@@ -144,7 +144,10 @@ __device__ __noinline__ Dot3<typename P::R> site_even(const GeomDev &g, long s, 
 }
 
 template <class P, int BL, int NT>
-__global__ void __launch_bounds__(NT) k_block_solve(GeomDev g, BlkArgs<P> a)
+// 32-bit arithmetic: at least two 256-thread (three 128-thread) CTAs per SM, i.e. at most 128 (170)
+// registers, so the register allocation keeps the occupancy of the out-of-line site functions
+__global__ void __launch_bounds__(NT, sizeof(typename P::R) == 4 ? (NT >= 256 ? 2 : NT >= 128 ? 3 : 1) : 1)
+    k_block_solve(GeomDev g, BlkArgs<P> a)
 {
     using R = typename P::R;
     using E = typename P::SElem;
