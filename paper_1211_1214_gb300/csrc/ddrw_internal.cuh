@@ -156,6 +156,11 @@ template <typename R> __device__ __forceinline__ void cmacc(cpx<R> &acc, cpx<R> 
     acc.re = fmad(a.re, b.re, fmad(a.im, b.im, acc.re));
     acc.im = fmad(a.re, b.im, fmad(-a.im, b.re, acc.im));
 }
+template <typename R> __device__ __forceinline__ void cmsub(cpx<R> &acc, cpx<R> a, cpx<R> b)  // acc -= a b
+{
+    acc.re = fmad(-a.re, b.re, fmad(a.im, b.im, acc.re));
+    acc.im = fmad(-a.re, b.im, fmad(-a.im, b.re, acc.im));
+}
 template <typename R> __device__ __forceinline__ cpx<R> timesI(cpx<R> a) { return {-a.im, a.re}; }
 template <typename R> __device__ __forceinline__ cpx<R> timesMinusI(cpx<R> a) { return {a.im, -a.re}; }
 
@@ -470,7 +475,8 @@ struct PrecS {
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             int i = (c + 1) % 3, j = (c + 2) % 3;
-            cpx<R> t = cmul(L.m[0][i], L.m[1][j]) - cmul(L.m[0][j], L.m[1][i]);
+            cpx<R> t = cmul(L.m[0][i], L.m[1][j]);
+            cmsub(t, L.m[0][j], L.m[1][i]);
             L.m[2][c] = {t.re, -t.im};
         }
     }

@@ -152,7 +152,8 @@ template <bool BF> struct PrecLow {
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             int i = (c + 1) % 3, j = (c + 2) % 3;
-            cpx<R> t = cmul(L.m[0][i], L.m[1][j]) - cmul(L.m[0][j], L.m[1][i]);
+            cpx<R> t = cmul(L.m[0][i], L.m[1][j]);
+            cmsub(t, L.m[0][j], L.m[1][i]);
             L.m[2][c] = {t.re, -t.im};
         }
     }
@@ -210,7 +211,8 @@ template <bool BF> struct PrecLow {
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             int i = (c + 1) % 3, j = (c + 2) % 3;
-            cpx<R> t = cmul(L.m[0][i], L.m[1][j]) - cmul(L.m[0][j], L.m[1][i]);
+            cpx<R> t = cmul(L.m[0][i], L.m[1][j]);
+            cmsub(t, L.m[0][j], L.m[1][i]);
             L.m[2][c] = {t.re, -t.im};
         }
     }
