@@ -350,6 +350,40 @@ def test_estimator_mean_and_variance():
         assert abs(res["e"] - e[j]) < 1e-10 * max(abs(e[j]), 1.0)
 
 
+def test_variance_expansion_and_hutchinson_moments():
+    """Eq. 4 at small dm, the form the large-volume check uses.  With A = Mh^dag Mh and X = A - 1:
+    det(A)^2 / det(2A - 1) = det(1 + X^2 (1 + 2X)^-1) exactly, so sigma_s^2/W^2 = exp(tr X^2 + O(X^3)) - 1;
+    for complex Gaussian noise (E|eta|^2 = 1) the exponent e = eta^dag X eta has mean tr X and
+    variance tr X^2 (Hutchinson).  Both sides are checked on the dense 4^4 ratio matrix."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, seed=1)
+    lat = oc.Lattice(dims, (2, 2, 2, 2), U, csw=1.0)
+    m1 = 0.20
+    prev = None
+    for m2 in (0.199, 0.198):
+        Mh = od.ratio_matrix(lat, m1, m2)
+        A = Mh.conj().T @ Mh
+        n = A.shape[0]
+        X = A - np.eye(n)
+        W = od.inv_det_MdagM(Mh)
+        rel = od.stochastic_variance(Mh) / W ** 2           # Eq. 4 divided by W^2
+        trX, trX2 = np.real(np.trace(X)), np.real(np.trace(X @ X))
+        # the exact rewrite and its leading order
+        _, ld = np.linalg.slogdet(np.eye(n) + X @ X @ np.linalg.inv(np.eye(n) + 2 * X))
+        assert abs(np.expm1(ld) - rel) < 1e-10 * rel
+        assert abs(np.expm1(trX2) - rel) < 0.05 * rel
+        # Hutchinson: sample mean and variance of the exponents
+        ns = 20000
+        eta = oc.noise_packed(seed=91, hit0=0, nhit=ns, n=n)
+        e = od.exponent(Mh, eta)
+        assert abs(e.mean() - trX) < 5 * np.sqrt(trX2 / ns)
+        assert abs(e.var() / trX2 - 1) < 0.1
+        # the fluctuations grow like dm^2
+        if prev is not None:
+            assert abs(trX2 / prev - 4.0) < 0.1
+        prev = trX2
+
+
 # ----------------------------------------------------------------------------- one flavour (Eq. 11, Eq. 12), interpolation (Eq. 8)
 
 def test_one_flavour_integral_and_variance():
