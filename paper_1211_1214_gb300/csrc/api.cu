@@ -26,19 +26,95 @@ ddrw_status set_cuda_error(ddrw_ctx *ctx, cudaError_t e, const char *what, const
 // every graph is destroyed before any such buffer is freed or moved.
 void clear_graphs(ddrw_ctx *ctx)
 {
-    if (ctx->graphs.empty()) return;
+    ctx->est_seen.clear();
+    if (ctx->graphs.empty() && ctx->est_graphs.empty()) return;
     cudaStreamSynchronize(ctx->stream);
     for (auto &kv : ctx->graphs) {
         cudaGraphExecDestroy(kv.second.exec);
         cudaGraphDestroy(kv.second.graph);
     }
     ctx->graphs.clear();
+    for (auto &kv : ctx->est_graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        cudaGraphDestroy(kv.second.graph);
+    }
+    ctx->est_graphs.clear();
+}
+
+// arms a loop: its condition is 1 when the loop node is reached (each time, also inside an outer loop)
+static __global__ void k_arm_loop(cudaGraphConditionalHandle h) { cudaGraphSetConditional(h, 1u); }
+
+ddrw_status capture_while(ddrw_ctx *ctx, const void *cond_fn,
+                          const std::function<ddrw_status(cudaGraphConditionalHandle, int)> &body)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    DDRW_CUDA_CHECK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &graph, &deps, &ed, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return set_error(ctx, DDRW_ESTATE, "loop capture outside a stream capture");
+    if (ctx->cap_depth >= 4 || ctx->dc_loops >= DC_LOOPS)
+        return set_error(ctx, DDRW_EINVAL, "too many nested or captured loops");
+    cudaGraphConditionalHandle h;
+    DDRW_CUDA_CHECK(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+    // a kernel node in front of the loop sets its condition to 1: the default applies only at graph
+    // launch, and a loop nested in another loop's body must start afresh on every outer pass
+    ++ctx->launches;
+    k_arm_loop<<<1, 1, 0, ctx->stream>>>(h);
+    DDRW_CUDA_CHECK(cudaStreamGetCaptureInfo(ctx->stream, &cs, nullptr, &graph, &deps, &ed, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    DDRW_CUDA_CHECK(cudaGraphAddNode(&node, graph, deps, ed, nd, &cp));
+    DDRW_CUDA_CHECK(cudaStreamUpdateCaptureDependencies(ctx->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+    cudaStream_t &side = ctx->cap_streams[ctx->cap_depth];
+    if (!side) DDRW_CUDA_CHECK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    DDRW_CUDA_CHECK(cudaStreamBeginCaptureToGraph(side, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    cudaStream_t saved = ctx->stream;
+    ctx->stream = side;
+    const int slot = ctx->dc_loops++;
+    const long l0 = ctx->launches;
+    ctx->cap_depth++;
+    ctx->cap_nested[ctx->cap_depth] = 0;
+    ddrw_status st = body(h, slot);
+    const long inner = ctx->cap_nested[ctx->cap_depth];
+    ctx->cap_depth--;
+    ctx->stream = saved;
+    cudaGraph_t g2 = nullptr;
+    cudaError_t e = cudaStreamEndCapture(side, &g2);
+    if (st) return st;
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "cudaStreamEndCapture(loop body)", __FILE__, __LINE__);
+    // the launches of this body, without those of loops nested in it (counted per their own runs)
+    const long all = ctx->launches - l0;
+    ctx->cap_loop_launches.push_back({slot, all - inner});
+    ctx->cap_nested[ctx->cap_depth] += all;
+    // the body must contain its condition kernel, or the loop would never end
+    size_t nn = 0;
+    DDRW_CUDA_CHECK(cudaGraphGetNodes(bodyg, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) DDRW_CUDA_CHECK(cudaGraphGetNodes(bodyg, nodes.data(), &nn));
+    bool found = false;
+    for (auto n : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(n, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        if (cudaGraphKernelNodeGetParams(n, &kp) == cudaSuccess && kp.func == cond_fn) found = true;
+    }
+    if (!found) return set_error(ctx, DDRW_ECUDA, "a captured loop body lacks its condition kernel");
+    return DDRW_OK;
 }
 
 ddrw_status workspace(ddrw_ctx *ctx, const char *name, size_t bytes, void **out)
 {
     DevBuf &b = ctx->ws[name];
     if (b.bytes < bytes) {
+        // a graph capture must find every buffer allocated (allocating would end the capture)
+        if (ctx->devctl) return set_error(ctx, DDRW_ESTATE, std::string("workspace allocation during capture: ") + name);
         clear_graphs(ctx);
         if (b.p) cudaFree(b.p);
         b.p = nullptr;
@@ -483,6 +559,8 @@ void ddrw_destroy(ddrw_ctx *ctx)
     clear_graphs(ctx);
     for (auto e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    for (auto &sd : ctx->cap_streams)
+        if (sd) cudaStreamDestroy(sd);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }

@@ -81,7 +81,8 @@ static ddrw_status colour_norms(ddrw_ctx *ctx, int colour, const double2 *f, int
 // solution, scaled back by scale_d[nrhs + r], is added to x (zeroed first on the first cycle).
 template <class P>
 static ddrw_status low_cycle(ddrw_ctx *ctx, int colour, const MassSet &ms, const double2 *rhs, double2 *x, bool first,
-                             int nrhs, void *const *w, const double *scale_d, double tol_inner, int maxiter, int *stat)
+                             int nrhs, void *const *w, const double *scale_d, double tol_inner, int maxiter, int *stat,
+                             const double *tol2_dev = nullptr)
 {
     using E = typename P::SElem;
     const long rs64 = 12 * ctx->V, rsl = P::field_elems(ctx->V);
@@ -100,6 +101,7 @@ static ddrw_status low_cycle(ddrw_ctx *ctx, int colour, const MassSet &ms, const
     a.rpm = (nrhs + std::max(ms.n, 1) - 1) / std::max(ms.n, 1);
     fill_args(ctx, a, ms, colour);
     a.tol2 = tol_inner * tol_inner;
+    a.tol2_dev = tol2_dev;
     a.maxiter = maxiter;
     a.stat = stat;
     launch_block(ctx, a, nrhs);
@@ -108,11 +110,182 @@ static ddrw_status low_cycle(ddrw_ctx *ctx, int colour, const MassSet &ms, const
     return DDRW_OK;
 }
 
+// out = -D_cc(ms) x on the sites of colour c (the stencil part of the residual b - D_cc x)
+static DslashCall residual_call(const ddrw_ctx *ctx, const MassSet &ms, int colour, const double2 *x, double2 *out,
+                                int nrhs)
+{
+    DslashCall c;
+    c.in = x;
+    c.x = x;
+    c.out = out;
+    c.rstride = 12 * ctx->V;
+    c.nrhs = nrhs;
+    c.nmass = ms.n;
+    for (int k = 0; k < ms.n; k++) {
+        c.masses[k] = ms.m[k];
+        c.Ainv[k] = ms.inv[k]->A64;
+    }
+    c.alpha = -1.0;
+    c.beta = 0.5;
+    c.diag = 1;
+    c.hopsel = 1;
+    c.par0 = 0;
+    c.npar = 2;
+    c.blk0 = colour == DDRW_BLACK ? 0 : ctx->nblk_c;
+    c.nblk = ctx->nblk_c;
+    return c;
+}
+
+// ---- device-controlled form (the estimate captured as one graph): the same cycles, with the
+// host's decisions taken by a one-thread control kernel on device norms
+
+// mode 0, before the first cycle: inner settings from nr = bb.  mode 1, after a cycle: statistics,
+// the continue decision (handle), then the next inner settings from nr = rr.  Norms come per
+// parity (2 nrhs values: parity 0 then parity 1).  ctl[0] counts the cycles.
+__global__ void k_blk_ctl(int mode, int nrhs, const double *bb2, const double *rr2, double tol, double floor, int mixed,
+                          const int *stat, double *scale, double *tol2, int *ctl, DcStats *dc, int slot,
+                          cudaGraphConditionalHandle h)
+{
+    const double *nr2 = mode == 0 ? bb2 : rr2;
+    if (mode == 1) {
+        const int cyc = ++ctl[0];
+        dc->loop_iters[slot] += 1;
+        dc->block_cycles += 1;
+        dc->fp64_dslash_half += 1;
+        dc->block_iters_max = max(dc->block_iters_max, stat[0]);
+        double worst = 0.0;
+        bool nan = false;
+        for (int r = 0; r < nrhs; r++) {
+            const double b = bb2[r] + bb2[nrhs + r], q = rr2[r] + rr2[nrhs + r];
+            if (!isfinite(q)) nan = true;
+            else if (b > 0) worst = fmax(worst, sqrt(q / b));
+        }
+        dc->block_rel_residual = fmax(dc->block_rel_residual, worst);
+        unsigned cont = 1;
+        if (nan) {
+            dc->nan = 1;
+            cont = 0;
+        } else if (worst <= tol) {
+            cont = 0;
+        } else if (cyc >= 50 || (!mixed && stat[1] > 0 && cyc >= 4)) {
+            dc->noconv = 1;
+            cont = 0;
+        }
+        cudaGraphSetConditional(h, cont);
+    } else {
+        ctl[0] = 0;
+    }
+    double need = 1.0;
+    for (int r = 0; r < nrhs; r++) {
+        const double b = bb2[r] + bb2[nrhs + r], q = nr2[r] + nr2[nrhs + r];
+        if (q > 0) need = fmin(need, 0.5 * tol * sqrt(b / q));
+        scale[r] = q > 0 ? 1.0 / sqrt(q) : 0.0;
+        scale[nrhs + r] = sqrt(q);
+    }
+    const double ti = mixed ? fmax(floor, fmin(need, 0.5)) : 0.5 * tol;
+    *tol2 = ti * ti;
+}
+
+__global__ void k_zero_ints(int *p, int n)  // (a kernel node: loop bodies hold kernels only)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0;
+}
+
+static ddrw_status colour_norms_dev(ddrw_ctx *ctx, int colour, const double2 *f, int nrhs, double *out2)
+{
+    ddrw_status st;
+    for (int p = 0; p < 2; p++)
+        if ((st = Blas<PrecD>::norm2(ctx, colour_range(ctx, colour, p, nrhs, 12 * ctx->V), f, out2 + p * nrhs))) return st;
+    return DDRW_OK;
+}
+
+// device buffers of the controlled form (allocated before a capture)
+ddrw_status block_solve_dc_prepare(ddrw_ctx *ctx, int nrhs)
+{
+    void *p;
+    ddrw_status st;
+    if ((st = workspace(ctx, "dcb_norms", sizeof(double) * 4 * nrhs, &p))) return st;
+    if ((st = workspace(ctx, "dcb_scale", sizeof(double) * 2 * nrhs, &p))) return st;
+    if ((st = workspace(ctx, "dcb_ctl", sizeof(double) * 2, &p))) return st;
+    if ((st = workspace(ctx, "blk_e64", sizeof(double2) * 12 * ctx->V * nrhs, &p))) return st;
+    return DDRW_OK;
+}
+
+static ddrw_status block_solve_dc(ddrw_ctx *ctx, int colour, const MassSet &ms, const double2 *b, double2 *x, int nrhs,
+                                  double tol, int maxiter, ddrw_prec prec)
+{
+    const bool mixed = prec != DDRW_FP64;
+    const long V = ctx->V, rs64 = 12 * V;
+    const size_t f64 = sizeof(double2) * rs64 * nrhs, f32 = sizeof(float4) * 6 * V * nrhs;
+    const double floor = prec == DDRW_MIXED_FP32 ? 1e-6 : prec == DDRW_MIXED_FP16 ? 1e-3 : 5e-3;
+    ddrw_status st;
+    int *stat;
+    double2 *res64, *e64;
+    double *norms, *scale, *ctlbuf;
+    if ((st = workspace(ctx, "blk_stat", sizeof(int) * 2, (void **)&stat))) return st;
+    if ((st = workspace(ctx, "blk_res64", f64, (void **)&res64))) return st;
+    if ((st = workspace(ctx, "blk_e64", f64, (void **)&e64))) return st;
+    if ((st = workspace(ctx, "dcb_norms", sizeof(double) * 4 * nrhs, (void **)&norms))) return st;
+    if ((st = workspace(ctx, "dcb_scale", sizeof(double) * 2 * nrhs, (void **)&scale))) return st;
+    if ((st = workspace(ctx, "dcb_ctl", sizeof(double) * 2, (void **)&ctlbuf))) return st;
+    double *bb2 = norms, *rr2 = norms + 2 * nrhs, *tol2 = ctlbuf;
+    int *cyc = (int *)(ctlbuf + 1);
+    void *w[6];
+    const char *names64[6] = {"blk_r", "blk_rh", "blk_p", "blk_v", "blk_t", "blk_tmp"};
+    const char *names32[6] = {"blk32_r", "blk32_rh", "blk32_p", "blk32_v", "blk32_t", "blk32_tmp"};
+    for (int k = 0; k < 6; k++)
+        if ((st = workspace(ctx, mixed ? names32[k] : names64[k], mixed ? f32 : f64, &w[k]))) return st;
+
+    if ((st = colour_norms_dev(ctx, colour, b, nrhs, bb2))) return st;
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(res64, b, f64, cudaMemcpyDeviceToDevice, ctx->stream));
+    zero_colour64(ctx, x, colour, nrhs);
+    ++ctx->launches;
+    k_blk_ctl<<<1, 1, 0, ctx->stream>>>(0, nrhs, bb2, rr2, tol, floor, mixed, stat, scale, tol2, cyc, ctx->dc, 0, 0);
+    return capture_while(ctx, (const void *)k_blk_ctl, [&](cudaGraphConditionalHandle h, int slot) -> ddrw_status {
+        ddrw_status s2;
+        ++ctx->launches;
+        k_zero_ints<<<1, 32, 0, ctx->stream>>>(stat, 2);
+        if (mixed) {  // the solution is added to x (zeroed above)
+            if (prec == DDRW_MIXED_FP32)
+                s2 = low_cycle<PrecS>(ctx, colour, ms, res64, x, false, nrhs, w, scale, 1.0, maxiter, stat, tol2);
+            else if (prec == DDRW_MIXED_FP16)
+                s2 = low_cycle<PrecH>(ctx, colour, ms, res64, x, false, nrhs, w, scale, 1.0, maxiter, stat, tol2);
+            else
+                s2 = low_cycle<PrecB>(ctx, colour, ms, res64, x, false, nrhs, w, scale, 1.0, maxiter, stat, tol2);
+            if (s2) return s2;
+        } else {
+            BlkArgs<PrecD> a;
+            a.b = res64;
+            a.x = e64;
+            a.r = (double2 *)w[0]; a.rh = (double2 *)w[1]; a.p = (double2 *)w[2];
+            a.v = (double2 *)w[3]; a.t = (double2 *)w[4]; a.tmp = (double2 *)w[5];
+            a.rstride = rs64;
+            a.rpm = (nrhs + std::max(ms.n, 1) - 1) / std::max(ms.n, 1);
+            fill_args(ctx, a, ms, colour);
+            a.tol2 = 0.0;
+            a.tol2_dev = tol2;
+            a.maxiter = maxiter;
+            a.stat = stat;
+            launch_block(ctx, a, nrhs);
+            for (int p = 0; p < 2; p++)
+                Blas<PrecD>::axpby(ctx, colour_range(ctx, colour, p, nrhs, rs64), 1.0, e64, 1.0, x);
+        }
+        DslashCall c = residual_call(ctx, ms, colour, x, res64, nrhs);
+        if ((s2 = residual_stencil(ctx, c, mixed))) return s2;
+        for (int p = 0; p < 2; p++) Blas<PrecD>::axpby(ctx, colour_range(ctx, colour, p, nrhs, rs64), 1.0, b, 1.0, res64);
+        if ((s2 = colour_norms_dev(ctx, colour, res64, nrhs, rr2))) return s2;
+        ++ctx->launches;
+        k_blk_ctl<<<1, 1, 0, ctx->stream>>>(1, nrhs, bb2, rr2, tol, floor, mixed, stat, scale, tol2, cyc, ctx->dc, slot, h);
+        return DDRW_OK;
+    });
+}
+
 // x = D_cc(ms)^-1 b on the sites of colour c (FP64 fields, full-field layout, nrhs rhs).
 // Sites of the other colour in x are left untouched.
 ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const double2 *b, double2 *x, int nrhs,
                           double tol, int maxiter, ddrw_prec prec, SolveStats *stats)
 {
+    if (ctx->devctl) return block_solve_dc(ctx, colour, ms, b, x, nrhs, tol, maxiter, prec);
     const bool mixed = prec != DDRW_FP64;
     const long V = ctx->V, rs64 = 12 * V;
     // the inner Krylov vectors: FP64 fields, or the largest low-precision field (FP32)
@@ -191,25 +364,7 @@ ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const do
         int hstat[2];
         DDRW_CUDA_CHECK(cudaMemcpyAsync(hstat, stat, sizeof(hstat), cudaMemcpyDeviceToHost, ctx->stream));
         // true residual res = b - D_cc x in FP64
-        DslashCall c;
-        c.in = x;
-        c.x = x;
-        c.out = res64;
-        c.rstride = rs64;
-        c.nrhs = nrhs;
-        c.nmass = ms.n;
-        for (int k = 0; k < ms.n; k++) {
-            c.masses[k] = ms.m[k];
-            c.Ainv[k] = ms.inv[k]->A64;
-        }
-        c.alpha = -1.0;
-        c.beta = 0.5;
-        c.diag = 1;
-        c.hopsel = 1;
-        c.par0 = 0;
-        c.npar = 2;
-        c.blk0 = colour == DDRW_BLACK ? 0 : ctx->nblk_c;
-        c.nblk = ctx->nblk_c;
+        DslashCall c = residual_call(ctx, ms, colour, x, res64, nrhs);
         if ((st = residual_stencil(ctx, c, mixed))) return st;
         if (stats) stats->fp64_dslash_half += 1;
         for (int p = 0; p < 2; p++) Blas<PrecD>::axpby(ctx, colour_range(ctx, colour, p, nrhs, rs64), 1.0, b, 1.0, res64);

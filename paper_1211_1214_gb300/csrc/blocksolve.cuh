@@ -22,6 +22,7 @@ template <class P> struct BlkArgs {
     const typename P::CElem *Ainv[MAXM];
     int blk0;
     double tol2;
+    const double *tol2_dev = nullptr;  // if set, the tolerance is read from device memory (captured graphs)
     int maxiter;
     int *stat;  // [0] max iterations, [1] blocks that missed the tolerance
 };
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(NT, sizeof(typename P::R) == 4 ? (NT >= 256 ? 
     cta_sum<3, NT>(red, sm);
     double rr = red[0];
     double2 rho = make_double2(rr, 0.0);
-    const double thresh = a.tol2 * bb;
+    const double thresh = (a.tol2_dev ? *a.tol2_dev : a.tol2) * bb;
     int it = 0;
     bool ok = rr <= thresh;
     while (!ok && it < a.maxiter) {

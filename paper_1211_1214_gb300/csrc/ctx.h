@@ -6,6 +6,7 @@
 #include <array>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -40,6 +41,25 @@ inline const void *ainv_for(const MassInv *m, int id)
 struct GraphEntry {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
+};
+
+// Device-side record of a graph-captured estimate: written by the loops' control kernels, read by
+// the host after the replay (estimate.cu, blocksolve.cu, solver.cu).
+constexpr int DC_LOOPS = 32;
+struct DcStats {
+    int block_iters_max, block_cycles, outer_iters, outer_cycles;
+    int fp64_dslash_half, fp64_dslash_full;
+    int nan, noconv;
+    double block_rel_residual, outer_rel_residual;
+    int loop_iters[DC_LOOPS];  // executions of each captured loop body (launch accounting)
+};
+
+// a captured whole-estimate graph
+struct EstGraph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    long top_launches;                              // kernel launches outside the loops
+    std::vector<std::pair<int, long>> loop_launches;  // (loop slot, launches per body execution)
 };
 
 // a tuned stencil launch configuration
@@ -116,6 +136,16 @@ struct ddrw_ctx {
     bool use_graphs = true;
     long graph_launches = 0;
     std::map<std::array<uintptr_t, 13 + 2 * ddrw::MAXM>, ddrw::GraphEntry> graphs;
+    // whole-estimate graphs (estimate.cu): captured on the second call of a shape, replayed after
+    std::map<std::array<uintptr_t, 24>, ddrw::EstGraph> est_graphs;
+    std::map<std::array<uintptr_t, 24>, int> est_seen;
+    // device-side loop control while an estimate is captured
+    bool devctl = false;                  // capturing: solvers use their device-controlled forms
+    ddrw::DcStats *dc = nullptr;          // device record of the capture being built / replayed
+    cudaStream_t cap_streams[4] = {};     // side streams that capture nested loop bodies
+    int cap_depth = 0, dc_loops = 0;
+    long cap_nested[5] = {0};             // launches of nested bodies, per capture depth
+    std::vector<std::pair<int, long>> cap_loop_launches;
 
     // stencil autotuner (dslash_tune.cu); pinned_nr > 0 overrides it with the pinned configuration
     bool autotune = true;
@@ -169,8 +199,17 @@ struct ProfScope {
 ddrw_status set_error(ddrw_ctx *ctx, ddrw_status st, const std::string &msg);
 ddrw_status set_cuda_error(ddrw_ctx *ctx, cudaError_t e, const char *what, const char *file, int line);
 
-// destroy the captured Krylov-loop graphs (before any buffer they reference is freed or moved)
+// destroy the captured Krylov-loop and estimate graphs (before any buffer they reference is freed
+// or moved)
 void clear_graphs(ddrw_ctx *ctx);
+
+// While the estimate is being captured on ctx->stream: appends a while-loop node whose body is
+// captured from body(handle, slot) with ctx->stream switched to a capturing side stream.  The body
+// must end with a kernel that sets the loop's condition handle (cudaGraphSetConditional) and
+// counts its executions in dc->loop_iters[slot]; the helper checks, before anything runs, that the
+// captured body contains the kernel cond_fn.
+ddrw_status capture_while(ddrw_ctx *ctx, const void *cond_fn,
+                          const std::function<ddrw_status(cudaGraphConditionalHandle, int)> &body);
 
 // device workspace of at least `bytes`, reused across calls under `name`
 ddrw_status workspace(ddrw_ctx *ctx, const char *name, size_t bytes, void **out);
@@ -257,9 +296,13 @@ void split64(ddrw_ctx *ctx, const double2 *in, float4 *out, long V, long vh, lon
 ddrw_status residual_stencil(ddrw_ctx *ctx, DslashCall c, bool ds);
 
 // x = D_cc(ms)^-1 b on the sites of colour c (persistent block solver + FP64 defect correction)
+// device buffers of the device-controlled block solve (to allocate before a capture)
+ddrw_status block_solve_dc_prepare(ddrw_ctx *ctx, int nrhs);
 ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const double2 *b, double2 *x, int nrhs,
                           double tol, int maxiter, ddrw_prec prec, SolveStats *stats);
 // x = D(ms)^-1 b on the full lattice (even-odd BiCGStab + FP64 defect correction)
+// device buffers of the device-controlled outer solve (to allocate before a capture)
+ddrw_status full_solve_dc_prepare(ddrw_ctx *ctx, int nrhs);
 ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, double2 *x, int nrhs, double tol,
                          int maxiter, ddrw_prec prec, SolveStats *stats);
 // mass set from a list of masses (builds the inverses on first use)

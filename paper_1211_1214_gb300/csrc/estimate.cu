@@ -40,12 +40,18 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
 }
 
 // eta for packed component k of hit h -> internal field (and optionally the packed output)
+// (dparams, if given: {seed, hit offset} read from device memory, so that a replayed graph draws new noise)
 __global__ void k_noise(long V, long nP, const int *__restrict__ idx, uint32_t k0, uint32_t k1, uint64_t hit0,
-                        int nhit, int nrep, double2 *field, double *packed)
+                        int nhit, int nrep, double2 *field, double *packed, const uint64_t *dparams = nullptr)
 {
     long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= 12 * nP) return;
     int h = blockIdx.y;
+    if (dparams) {
+        k0 = (uint32_t)(dparams[0] & 0xffffffffu);
+        k1 = (uint32_t)(dparams[0] >> 32);
+        hit0 = dparams[1];
+    }
     uint32_t c[4] = {(uint32_t)k, (uint32_t)(hit0 + (uint64_t)h), 0u, 0u};
     philox4x32_10(c, k0, k1);
     double u1 = ((double)c[0] + 1.0) * (1.0 / 4294967296.0);
@@ -124,12 +130,13 @@ __global__ void k_delta(GeomDev g, const double2 *r, const double2 *x, double2 *
     default: KERNEL<8><<<GRID, BLOCK, 0, (ctx)->stream>>>(__VA_ARGS__); break;                            \
     }
 
-static void noise_launch(ddrw_ctx *ctx, uint64_t seed, uint64_t hit0, int nhit, int nrep, double2 *field, double *packed)
+static void noise_launch(ddrw_ctx *ctx, uint64_t seed, uint64_t hit0, int nhit, int nrep, double2 *field, double *packed,
+                         const uint64_t *dparams = nullptr)
 {
     dim3 grid((unsigned)((12 * ctx->nP + 255) / 256), (unsigned)nhit);
     ++ctx->launches;
     k_noise<<<grid, 256, 0, ctx->stream>>>(ctx->V, ctx->nP, ctx->d_suppP, (uint32_t)(seed & 0xffffffffu),
-                                           (uint32_t)(seed >> 32), hit0, nhit, nrep, field, packed);
+                                           (uint32_t)(seed >> 32), hit0, nhit, nrep, field, packed, dparams);
 }
 
 // ---- supports of the operator variants of Fig. 1's comparison (ddrw_estimate_variant)
@@ -269,9 +276,11 @@ static ddrw_status apply_dA_fields(ddrw_ctx *ctx, const MassSet &m2s, const Mass
     if ((st = block_solve64(ctx, DDRW_BLACK, m1s, u, r, nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, stats))) return st;
     double *dm;
     if ((st = workspace(ctx, "est_dm", sizeof(double) * MAXM, (void **)&dm))) return st;
-    double hdm[MAXM];
-    for (int k = 0; k < MAXM; k++) hdm[k] = k < m2s.n ? m1s.m[k < m1s.n ? k : 0] - m2s.m[k] : 0.0;
-    DDRW_CUDA_CHECK(cudaMemcpyAsync(dm, hdm, sizeof(hdm), cudaMemcpyHostToDevice, ctx->stream));
+    if (!ctx->devctl) {  // a captured estimate finds the mass differences written before the capture
+        double hdm[MAXM];
+        for (int k = 0; k < MAXM; k++) hdm[k] = k < m2s.n ? m1s.m[k < m1s.n ? k : 0] - m2s.m[k] : 0.0;
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(dm, hdm, sizeof(hdm), cudaMemcpyHostToDevice, ctx->stream));
+    }
     GeomDev g = geom_dev(ctx);
     int rpm = (nrhs + m2s.n - 1) / m2s.n;
     dim3 grid((unsigned)((ctx->V + 127) / 128), (unsigned)nrhs);
@@ -306,6 +315,160 @@ static ddrw_status fields(ddrw_ctx *ctx, const char *prefix, int n, int nrhs, do
     return DDRW_OK;
 }
 
+// ---- the whole estimate chunk as one CUDA graph
+//
+// With ctx->use_graphs, Philox noise and no delta output, the first call of a chunk shape runs
+// eagerly (it tunes the stencil and allocates every buffer), the second captures the chunk with
+// the solvers' device-controlled forms (every defect-correction cycle and Krylov loop a
+// conditional while-node whose condition a one-thread kernel sets from device norms, each with an
+// iteration cap), and later calls replay it: the noise seed and hit offset go in through device
+// memory, the exponents and the statistics come back after one synchronisation.
+
+using EstKey = std::array<uintptr_t, 24>;
+
+static EstKey est_key(const ddrw_ctx *ctx, int nmass, const double *ma, const double *m2, int nhit, bool distinct)
+{
+    EstKey k{};
+    k[0] = (uintptr_t)nmass;
+    k[1] = (uintptr_t)nhit;
+    k[2] = distinct;
+    k[3] = (uintptr_t)ctx->prec;
+    k[4] = (uintptr_t)ctx->maxiter;
+    memcpy(&k[5], &ctx->tol_block, sizeof(double));
+    memcpy(&k[6], &ctx->tol_outer, sizeof(double));
+    for (int i = 0; i < nmass && i < MAXM; i++) {
+        memcpy(&k[7 + 2 * i], &ma[i], sizeof(double));
+        memcpy(&k[8 + 2 * i], &m2[i], sizeof(double));
+    }
+    return k;
+}
+
+static ddrw_status apply_dA_fields(ddrw_ctx *ctx, const MassSet &m2s, const MassSet &m1s, const double2 *eta,
+                                   double2 *r, double2 *const *f, int nrhs, SolveStats *stats);
+static ddrw_status solve_schur_fields(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, double2 *delta,
+                                      double2 *const *f, int nrhs, SolveStats *stats);
+
+// the device work of one chunk (the same calls as the eager chunk, noise parameters from device)
+static ddrw_status chunk_body(ddrw_ctx *ctx, int nmass, int nhit, bool distinct, const MassSet &m2s,
+                              const MassSet &m1s, double2 *const *F, const uint64_t *dparams, double *red)
+{
+    const int nrhs = nmass * nhit;
+    double2 *eta = F[0], *r = F[1], *delta = F[2];
+    double2 *work[3] = {F[3], F[4], F[2]};
+    double2 *w2[2] = {F[3], F[4]};
+    DDRW_CUDA_CHECK(cudaMemsetAsync(eta, 0, sizeof(double2) * 12 * ctx->V * nrhs, ctx->stream));
+    if (distinct) noise_launch(ctx, 0, 0, nrhs, 1, eta, nullptr, dparams);
+    else noise_launch(ctx, 0, 0, nhit, nmass, eta, nullptr, dparams);
+    ddrw_status st;
+    if ((st = apply_dA_fields(ctx, m2s, m1s, eta, r, work, nrhs, nullptr))) return st;
+    st = solve_schur_fields(ctx, m2s, r, delta, w2, nrhs, nullptr);
+    if (st && st != DDRW_ENOCONV) return st;
+    long vbh = (long)ctx->l * ctx->l * ctx->l * ctx->l / 2, nc = (long)ctx->nblk_c * vbh;
+    for (int p = 0; p < 2; p++)
+        if ((st = Blas<PrecD>::norm_dot(ctx, VecRange{ctx->V, p * ctx->vh, nc, 12 * ctx->V, nrhs}, delta, eta,
+                                        red + 3 * p * nrhs)))
+            return st;
+    return DDRW_OK;
+}
+
+static ddrw_status chunk_capture(ddrw_ctx *ctx, int nmass, const double *ma, const double *m2, int nhit, bool distinct,
+                                 const MassSet &m2s, const MassSet &m1s, double2 *const *F, EstGraph &out)
+{
+    const int nrhs = nmass * nhit;
+    ddrw_status st;
+    void *p;
+    double *red, *dm;
+    uint64_t *dparams;
+    // every buffer the capture uses, allocated now
+    if ((st = block_solve_dc_prepare(ctx, nrhs))) return st;
+    if ((st = full_solve_dc_prepare(ctx, nrhs))) return st;
+    if ((st = workspace(ctx, "dc_stats", sizeof(DcStats), &p))) return st;
+    ctx->dc = (DcStats *)p;
+    if ((st = workspace(ctx, "dc_noise", sizeof(uint64_t) * 2, (void **)&dparams))) return st;
+    if ((st = workspace(ctx, "est_red", sizeof(double) * 6 * nrhs, (void **)&red))) return st;
+    if ((st = workspace(ctx, "est_dm", sizeof(double) * MAXM, (void **)&dm))) return st;
+    double hdm[MAXM];
+    for (int k = 0; k < MAXM; k++) hdm[k] = k < m2s.n ? m1s.m[k < m1s.n ? k : 0] - m2s.m[k] : 0.0;
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(dm, hdm, sizeof(hdm), cudaMemcpyHostToDevice, ctx->stream));
+    DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+
+    DDRW_CUDA_CHECK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed));
+    ctx->devctl = true;
+    ctx->dc_loops = 0;
+    ctx->cap_depth = 0;
+    ctx->cap_nested[0] = 0;
+    ctx->cap_loop_launches.clear();
+    const long l0 = ctx->launches;
+    cudaError_t em = cudaMemsetAsync(ctx->dc, 0, sizeof(DcStats), ctx->stream);
+    st = em == cudaSuccess ? chunk_body(ctx, nmass, nhit, distinct, m2s, m1s, F, dparams, red)
+                           : set_cuda_error(ctx, em, "cudaMemsetAsync(stats)", __FILE__, __LINE__);
+    ctx->devctl = false;
+    const long captured = ctx->launches - l0;
+    ctx->launches = l0;  // nothing ran yet
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (st || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st ? st : set_cuda_error(ctx, e, "cudaStreamEndCapture(estimate)", __FILE__, __LINE__);
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+    if (ei != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return set_cuda_error(ctx, ei, "cudaGraphInstantiate(estimate)", __FILE__, __LINE__);
+    }
+    out.graph = g;
+    out.exec = exec;
+    out.top_launches = captured - ctx->cap_nested[0];
+    out.loop_launches = ctx->cap_loop_launches;
+    return DDRW_OK;
+}
+
+static ddrw_status chunk_replay(ddrw_ctx *ctx, const EstGraph &eg, int nrhs, uint64_t seed, uint64_t hit0,
+                                double *exponents, double *e1, SolveStats &stats)
+{
+    ddrw_status st;
+    void *p;
+    double *red;
+    uint64_t *dparams;
+    if ((st = workspace(ctx, "dc_stats", sizeof(DcStats), &p))) return st;
+    if ((st = workspace(ctx, "dc_noise", sizeof(uint64_t) * 2, (void **)&dparams))) return st;
+    if ((st = workspace(ctx, "est_red", sizeof(double) * 6 * nrhs, (void **)&red))) return st;
+    const uint64_t prm[2] = {seed, hit0};
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(dparams, prm, sizeof(prm), cudaMemcpyHostToDevice, ctx->stream));
+    DDRW_CUDA_CHECK(cudaGraphLaunch(eg.exec, ctx->stream));
+    ++ctx->graph_launches;
+    std::vector<double> h(6 * nrhs);
+    DcStats d;
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(h.data(), red, sizeof(double) * 6 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(&d, p, sizeof(DcStats), cudaMemcpyDeviceToHost, ctx->stream));
+    if ((st = sync(ctx))) return st;
+    long launches = eg.top_launches;
+    for (auto &sl : eg.loop_launches) launches += sl.second * d.loop_iters[sl.first];
+    ctx->launches += launches;
+    stats.block_iters_max = std::max(stats.block_iters_max, d.block_iters_max);
+    stats.block_cycles += d.block_cycles;
+    stats.block_rel_residual = std::max(stats.block_rel_residual, d.block_rel_residual);
+    stats.fp64_dslash_half += d.fp64_dslash_half;
+    stats.outer_iters += d.outer_iters;
+    stats.outer_cycles = d.outer_cycles;
+    stats.fp64_dslash_full += d.fp64_dslash_full;
+    stats.outer_rel_residual = d.outer_rel_residual;
+    for (int rr = 0; rr < nrhs; rr++) {
+        double nn = h[3 * rr] + h[3 * nrhs + 3 * rr], dr = h[3 * rr + 1] + h[3 * nrhs + 3 * rr + 1];
+        double di = h[3 * rr + 2] + h[3 * nrhs + 3 * rr + 2];
+        exponents[rr] = nn + 2.0 * dr;
+        if (e1) {
+            e1[2 * rr] = dr;
+            e1[2 * rr + 1] = -di;
+        }
+    }
+    if (d.nan) return set_error(ctx, DDRW_ENUMERIC, "NaN in a solve of the captured estimate");
+    if (d.noconv) return set_error(ctx, DDRW_ENOCONV, "a solve of the captured estimate missed its tolerance");
+    return DDRW_OK;
+}
+
 // One chunk of the estimate: nmass target masses x nhit noise vectors as nrhs = nmass * nhit
 // right-hand sides; writes the FP64 exponents e[k * nhit + j].  eta_user (packed, nhit vectors)
 // or the Philox noise of hits hit0 .. hit0 + nhit - 1.
@@ -325,6 +488,20 @@ static ddrw_status estimate_chunk(ddrw_ctx *ctx, int nmass, const double *ma, co
     if ((st = make_massset(ctx, nmass, ma, &m1s))) return st;
     double2 *F[5];
     if ((st = fields(ctx, "est_f", 5, nrhs, F))) return st;
+    // the whole chunk as a graph: captured on the second call of this shape, replayed later
+    const bool graphable = ctx->use_graphs && !eta_user && !delta_user && !ctx->devctl;
+    EstKey key{};
+    if (graphable) {
+        key = est_key(ctx, nmass, ma, m2, nhit, distinct_noise);
+        auto it = ctx->est_graphs.find(key);
+        if (it == ctx->est_graphs.end() && ctx->est_seen.count(key)) {
+            EstGraph eg;
+            if ((st = chunk_capture(ctx, nmass, ma, m2, nhit, distinct_noise, m2s, m1s, F, eg))) return st;
+            it = ctx->est_graphs.emplace(key, eg).first;
+        }
+        if (it != ctx->est_graphs.end())
+            return chunk_replay(ctx, it->second, nrhs, seed, hit0, exponents, e1, stats);
+    }
     double2 *eta = F[0], *r = F[1], *delta = F[2];
     double2 *work[3] = {F[3], F[4], F[2]};
     const size_t pbytes = sizeof(double) * 24 * ctx->nP;
@@ -365,6 +542,7 @@ static ddrw_status estimate_chunk(ddrw_ctx *ctx, int nmass, const double *ma, co
         if ((st = finish_out(ctx, delta_user, dd, pbytes * nrhs, host))) return st;
     }
     if ((st = sync(ctx))) return st;
+    if (graphable) ctx->est_seen[key] = 1;  // after the eager run: its allocations clear the table
     for (int rr = 0; rr < nrhs; rr++) {
         // h: |delta|^2, Re sum conj(delta) eta, Im sum conj(delta) eta (two parities)
         double nn = h[3 * rr] + h[3 * nrhs + 3 * rr], dr = h[3 * rr + 1] + h[3 * nrhs + 3 * rr + 1];

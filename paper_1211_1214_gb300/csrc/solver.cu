@@ -98,6 +98,24 @@ void apply_mhat(ddrw_ctx *ctx, const MassSet &ms, int nrhs, long rs, const typen
     stencil<P>(ctx, d);
 }
 
+// One BiCGStab iteration on the even-odd operator for nrhs right-hand sides (scalars on the device)
+template <class P>
+static ddrw_status bicg_iteration(ddrw_ctx *ctx, const MassSet &ms, int nrhs, long rs, const VecRange &ev,
+                                  typename P::SElem *x, typename P::SElem *r, typename P::SElem *rh,
+                                  typename P::SElem *p, typename P::SElem *v, typename P::SElem *t,
+                                  typename P::SElem *tmp, KScal *sc)
+{
+    ddrw_status s2;
+    apply_mhat<P>(ctx, ms, nrhs, rs, p, tmp, v);
+    if ((s2 = Blas<P>::bicg_alpha(ctx, ev, rh, v, sc))) return s2;
+    Blas<P>::bicg_s(ctx, ev, r, v, sc);
+    apply_mhat<P>(ctx, ms, nrhs, rs, r, tmp, t);
+    if ((s2 = Blas<P>::bicg_omega(ctx, ev, t, r, sc))) return s2;
+    if ((s2 = Blas<P>::bicg_xr(ctx, ev, x, p, r, t, rh, sc))) return s2;
+    Blas<P>::bicg_p(ctx, ev, p, r, v, sc);
+    return DDRW_OK;
+}
+
 // Inner even-odd BiCGStab in policy P: solve D x = b (full fields) until the even-odd residual of
 // right-hand side r satisfies ||r||^2 <= thresh[r].  Adds iterations to *iters.
 template <class P>
@@ -150,17 +168,7 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
 
     KScal *hs = (KScal *)ctx->h_pinned;
     const int check = sizeof(typename P::R) == 8 ? 1 : 4;
-    auto iteration = [&]() -> ddrw_status {
-        ddrw_status s2;
-        apply_mhat<P>(ctx, ms, nrhs, rs, p, tmp, v);
-        if ((s2 = Blas<P>::bicg_alpha(ctx, ev, rh, v, sc))) return s2;
-        Blas<P>::bicg_s(ctx, ev, r, v, sc);
-        apply_mhat<P>(ctx, ms, nrhs, rs, r, tmp, t);
-        if ((s2 = Blas<P>::bicg_omega(ctx, ev, t, r, sc))) return s2;
-        if ((s2 = Blas<P>::bicg_xr(ctx, ev, x, p, r, t, rh, sc))) return s2;
-        Blas<P>::bicg_p(ctx, ev, p, r, v, sc);
-        return DDRW_OK;
-    };
+    auto iteration = [&]() -> ddrw_status { return bicg_iteration<P>(ctx, ms, nrhs, rs, ev, x, r, rh, p, v, t, tmp, sc); };
     int it = 0;
     bool done = false;
     // first iterations eagerly: they tune the stencil launches and create every workspace
@@ -308,9 +316,261 @@ static ddrw_status inner_solve(ddrw_ctx *ctx, const MassSet &ms, const double2 *
     return DDRW_OK;
 }
 
+// out = -D(ms) x over the whole lattice (the stencil part of the residual b - D x)
+static DslashCall outer_residual_call(const ddrw_ctx *ctx, const MassSet &ms, const double2 *x, double2 *out, int nrhs)
+{
+    DslashCall c;
+    c.in = x;
+    c.x = x;
+    c.out = out;
+    c.rstride = 12 * ctx->V;
+    c.nrhs = nrhs;
+    c.nmass = ms.n;
+    for (int k = 0; k < ms.n; k++) {
+        c.masses[k] = ms.m[k];
+        c.Ainv[k] = ms.inv[k]->A64;
+    }
+    c.alpha = -1.0;
+    c.beta = 0.5;
+    c.diag = 1;
+    c.blk0 = 0;
+    c.nblk = ctx->nblk;
+    c.par0 = 0;
+    c.npar = 2;
+    return c;
+}
+
+// ---- device-controlled forms (the estimate captured as one graph)
+
+// KScal of every right-hand side from device thresholds (the host form copies them)
+__global__ void k_kscal_init(KScal *sc, const double *th, int nrhs, int maxiter)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrhs) return;
+    KScal k = {};
+    k.thresh = th[r];
+    k.maxiter = maxiter;
+    sc[r] = k;
+}
+
+// loop condition of the captured Krylov loop (k_bicg_cond plus the body count of its loop)
+__global__ void k_bicg_cond_dc(cudaGraphConditionalHandle h, const KScal *sc, int nrhs, int *count, int step,
+                               int maxiter, int *body_count)
+{
+    int act = 0;
+    for (int r = 0; r < nrhs; r++) act |= sc[r].active;
+    int it = (*count += step);
+    *body_count += 1;
+    cudaGraphSetConditional(h, (act && it < maxiter) ? 1u : 0u);
+}
+
+__global__ void k_zero_count(int *c) { *c = 0; }
+
+// outer iterations of a finished Krylov loop: the most any right-hand side needed
+__global__ void k_iters_acc(const KScal *sc, int nrhs, int *acc)
+{
+    int m = 0;
+    for (int r = 0; r < nrhs; r++) m = max(m, sc[r].iters);
+    *acc += m;
+}
+
+template <class P>
+static ddrw_status eo_bicgstab_dc(ddrw_ctx *ctx, const MassSet &ms, const typename P::SElem *b, typename P::SElem *x,
+                                  int nrhs, const double *th, int maxiter)
+{
+    using E = typename P::SElem;
+    const long rs = P::field_elems(ctx->V);
+    const size_t fb = sizeof(E) * rs * nrhs;
+    const char *names[6] = {"eo_r", "eo_rh", "eo_p", "eo_v", "eo_t", "eo_tmp"};
+    void *w[6];
+    ddrw_status st;
+    for (int k = 0; k < 6; k++) {
+        char nm[32];
+        snprintf(nm, sizeof nm, "%s%d", names[k], P::ID);
+        if ((st = workspace(ctx, nm, fb, &w[k]))) return st;
+    }
+    E *r = (E *)w[0], *rh = (E *)w[1], *p = (E *)w[2], *v = (E *)w[3], *t = (E *)w[4], *tmp = (E *)w[5];
+    KScal *sc;
+    int *count;
+    if ((st = workspace(ctx, "eo_kscal", sizeof(KScal) * nrhs, (void **)&sc))) return st;
+    if ((st = workspace(ctx, "eo_graph_count", sizeof(int), (void **)&count))) return st;
+    DslashCall c = base_call<P>(ctx, ms, nrhs, rs);  // btil_e = b_e + 1/2 H_eo A_oo^-1 b_o
+    c.x = b;
+    c.out = tmp;
+    c.alpha = 1.0;
+    c.diag = 2;
+    c.post = 1;
+    c.par0 = 1;
+    stencil<P>(ctx, c);
+    DslashCall d = base_call<P>(ctx, ms, nrhs, rs);
+    d.in = tmp;
+    d.x = b;
+    d.out = r;
+    d.alpha = 1.0;
+    d.beta = 0.5;
+    d.diag = 2;
+    d.par0 = 0;
+    stencil<P>(ctx, d);
+    ++ctx->launches;
+    k_kscal_init<<<(nrhs + 63) / 64, 64, 0, ctx->stream>>>(sc, th, nrhs, maxiter);
+    VecRange ev{ctx->V, 0, ctx->vh, rs, nrhs};
+    if ((st = Blas<P>::bicg_init(ctx, ev, r, rh, p, x, sc))) return st;
+    ++ctx->launches;
+    k_zero_count<<<1, 1, 0, ctx->stream>>>(count);  // a kernel node: this may sit in an outer loop body
+    const int check = sizeof(typename P::R) == 8 ? 1 : 4;
+    st = capture_while(ctx, (const void *)k_bicg_cond_dc, [&](cudaGraphConditionalHandle h, int slot) -> ddrw_status {
+        ddrw_status s2;
+        for (int k = 0; k < check; k++)
+            if ((s2 = bicg_iteration<P>(ctx, ms, nrhs, rs, ev, x, r, rh, p, v, t, tmp, sc))) return s2;
+        ++ctx->launches;
+        k_bicg_cond_dc<<<1, 1, 0, ctx->stream>>>(h, sc, nrhs, count, check, maxiter, &ctx->dc->loop_iters[slot]);
+        return DDRW_OK;
+    });
+    if (st) return st;
+    ++ctx->launches;
+    k_iters_acc<<<1, 1, 0, ctx->stream>>>(sc, nrhs, &ctx->dc->outer_iters);
+    DslashCall e = base_call<P>(ctx, ms, nrhs, rs);  // x_o = A_oo^-1 (b_o + 1/2 H_oe x_e)
+    e.in = x;
+    e.x = b;
+    e.out = x;
+    e.alpha = 1.0;
+    e.beta = 0.5;
+    e.diag = 2;
+    e.post = 1;
+    e.par0 = 1;
+    stencil<P>(ctx, e);
+    return DDRW_OK;
+}
+
+// control of the outer defect correction: mode 0 before the first cycle (nr = bb), mode 1 after a
+// cycle (statistics, continue decision, then the next inner settings from nr = rr); ctl[0] counts
+// the cycles
+__global__ void k_full_ctl(int mode, int nrhs, const double *bb, const double *rr, double tol, double floor, int mixed,
+                           int maxiter, double *scale, double *th, int *ctl, DcStats *dc, int slot,
+                           cudaGraphConditionalHandle h)
+{
+    const double *nr = mode == 0 ? bb : rr;
+    if (mode == 1) {
+        const int cyc = ++ctl[0];
+        dc->loop_iters[slot] += 1;
+        dc->outer_cycles = cyc;
+        dc->fp64_dslash_full += 1;
+        double worst = 0.0;
+        bool nan = false;
+        for (int r = 0; r < nrhs; r++) {
+            if (!isfinite(rr[r])) nan = true;
+            else if (bb[r] > 0) worst = fmax(worst, sqrt(rr[r] / bb[r]));
+        }
+        dc->outer_rel_residual = worst;
+        unsigned cont = 1;
+        if (nan) {
+            dc->nan = 1;
+            cont = 0;
+        } else if (worst <= tol) {
+            cont = 0;
+        } else if (cyc >= 40 || dc->outer_iters >= 4 * maxiter) {
+            dc->noconv = 1;
+            cont = 0;
+        }
+        cudaGraphSetConditional(h, cont);
+    } else {
+        ctl[0] = 0;
+    }
+    for (int r = 0; r < nrhs; r++) {
+        const double q = nr[r];
+        scale[r] = q > 0 ? 1.0 / sqrt(q) : 0.0;
+        scale[nrhs + r] = sqrt(q);
+        if (mixed) {
+            const double need = q > 0 ? 0.5 * tol * sqrt(bb[r] / q) : 1.0;
+            const double ti = fmax(floor, fmin(need, 0.5));
+            th[r] = q > 0 ? ti * ti : 0.0;
+        } else {
+            th[r] = 0.25 * tol * tol * bb[r];
+        }
+    }
+}
+
+template <class P>
+static ddrw_status inner_solve_dc(ddrw_ctx *ctx, const MassSet &ms, const double2 *rhs, double2 *x, int nrhs,
+                                  const double *scale, const double *th, int maxiter)
+{
+    using E = typename P::SElem;
+    const long V = ctx->V, rsl = P::field_elems(V);
+    const size_t fl = sizeof(E) * rsl * nrhs;
+    char nb[32], ne[32];
+    snprintf(nb, sizeof nb, "full_b%d", P::ID);
+    snprintf(ne, sizeof ne, "full_e%d", P::ID);
+    void *bl, *el;
+    ddrw_status st;
+    if ((st = workspace(ctx, nb, fl, &bl))) return st;
+    if ((st = workspace(ctx, ne, fl, &el))) return st;
+    VecRange all{V, 0, V, 12 * V, nrhs};
+    to_low<P>(ctx, all, rsl, rhs, (E *)bl, scale);
+    if ((st = eo_bicgstab_dc<P>(ctx, ms, (const E *)bl, (E *)el, nrhs, th, maxiter))) return st;
+    add_low<P>(ctx, all, rsl, (const E *)el, x, scale + nrhs);
+    return DDRW_OK;
+}
+
+ddrw_status full_solve_dc_prepare(ddrw_ctx *ctx, int nrhs)
+{
+    void *p;
+    ddrw_status st;
+    if ((st = workspace(ctx, "dcf_norms", sizeof(double) * 2 * nrhs, &p))) return st;
+    if ((st = workspace(ctx, "dcf_scale", sizeof(double) * 3 * nrhs, &p))) return st;
+    if ((st = workspace(ctx, "dcf_ctl", sizeof(int), &p))) return st;
+    if ((st = workspace(ctx, "full_e64", sizeof(double2) * 12 * ctx->V * nrhs, &p))) return st;
+    if ((st = workspace(ctx, "eo_graph_count", sizeof(int), &p))) return st;
+    return DDRW_OK;
+}
+
+static ddrw_status full_solve_dc(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, double2 *x, int nrhs, double tol,
+                                 int maxiter, ddrw_prec prec)
+{
+    const long V = ctx->V, rs64 = 12 * V;
+    const size_t f64 = sizeof(double2) * rs64 * nrhs;
+    const bool mixed = prec != DDRW_FP64;
+    const double floor = prec == DDRW_MIXED_FP32 ? 1e-6 : prec == DDRW_MIXED_FP16 ? 1e-3 : 5e-3;
+    ddrw_status st;
+    double2 *res, *e64;
+    double *norms, *scale;
+    int *cyc;
+    if ((st = workspace(ctx, "full_res", f64, (void **)&res))) return st;
+    if ((st = workspace(ctx, "full_e64", f64, (void **)&e64))) return st;
+    if ((st = workspace(ctx, "dcf_norms", sizeof(double) * 2 * nrhs, (void **)&norms))) return st;
+    if ((st = workspace(ctx, "dcf_scale", sizeof(double) * 3 * nrhs, (void **)&scale))) return st;
+    if ((st = workspace(ctx, "dcf_ctl", sizeof(int), (void **)&cyc))) return st;
+    double *bb = norms, *rr = norms + nrhs, *th = scale + 2 * nrhs;
+    const VecRange all{V, 0, V, rs64, nrhs};
+    if ((st = Blas<PrecD>::norm2(ctx, all, b, bb))) return st;
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(res, b, f64, cudaMemcpyDeviceToDevice, ctx->stream));
+    DDRW_CUDA_CHECK(cudaMemsetAsync(x, 0, f64, ctx->stream));
+    ++ctx->launches;
+    k_full_ctl<<<1, 1, 0, ctx->stream>>>(0, nrhs, bb, rr, tol, floor, mixed, maxiter, scale, th, cyc, ctx->dc, 0, 0);
+    return capture_while(ctx, (const void *)k_full_ctl, [&](cudaGraphConditionalHandle h, int slot) -> ddrw_status {
+        ddrw_status s2;
+        if (mixed) {
+            if (prec == DDRW_MIXED_FP32) s2 = inner_solve_dc<PrecS>(ctx, ms, res, x, nrhs, scale, th, maxiter);
+            else if (prec == DDRW_MIXED_FP16) s2 = inner_solve_dc<PrecH>(ctx, ms, res, x, nrhs, scale, th, maxiter);
+            else s2 = inner_solve_dc<PrecB>(ctx, ms, res, x, nrhs, scale, th, maxiter);
+            if (s2) return s2;
+        } else {
+            if ((s2 = eo_bicgstab_dc<PrecD>(ctx, ms, res, e64, nrhs, th, maxiter))) return s2;
+            Blas<PrecD>::axpby(ctx, all, 1.0, e64, 1.0, x);
+        }
+        DslashCall c = outer_residual_call(ctx, ms, x, res, nrhs);
+        if ((s2 = residual_stencil(ctx, c, mixed))) return s2;
+        Blas<PrecD>::axpby(ctx, all, 1.0, b, 1.0, res);
+        if ((s2 = Blas<PrecD>::norm2(ctx, all, res, rr))) return s2;
+        ++ctx->launches;
+        k_full_ctl<<<1, 1, 0, ctx->stream>>>(1, nrhs, bb, rr, tol, floor, mixed, maxiter, scale, th, cyc, ctx->dc, slot, h);
+        return DDRW_OK;
+    });
+}
+
 ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, double2 *x, int nrhs, double tol,
                          int maxiter, ddrw_prec prec, SolveStats *stats)
 {
+    if (ctx->devctl) return full_solve_dc(ctx, ms, b, x, nrhs, tol, maxiter, prec);
     const long V = ctx->V, rs64 = 12 * V;
     const size_t f64 = sizeof(double2) * rs64 * nrhs;
     const bool mixed = prec != DDRW_FP64;
@@ -364,24 +624,7 @@ ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, dou
             if (!first) Blas<PrecD>::axpby(ctx, VecRange{V, 0, V, rs64, nrhs}, 1.0, e64, 1.0, x);
         }
         // res = b - D x in FP64
-        DslashCall c;
-        c.in = x;
-        c.x = x;
-        c.out = res;
-        c.rstride = rs64;
-        c.nrhs = nrhs;
-        c.nmass = ms.n;
-        for (int k = 0; k < ms.n; k++) {
-            c.masses[k] = ms.m[k];
-            c.Ainv[k] = ms.inv[k]->A64;
-        }
-        c.alpha = -1.0;
-        c.beta = 0.5;
-        c.diag = 1;
-        c.blk0 = 0;
-        c.nblk = ctx->nblk;
-        c.par0 = 0;
-        c.npar = 2;
+        DslashCall c = outer_residual_call(ctx, ms, x, res, nrhs);
         if ((st = residual_stencil(ctx, c, mixed))) return st;
         if (stats) stats->fp64_dslash_full += 1;
         Blas<PrecD>::axpby(ctx, VecRange{V, 0, V, rs64, nrhs}, 1.0, b, 1.0, res);

@@ -61,3 +61,28 @@ def test_autotuner_off_gives_the_same_numbers(ctx):
     c.autotune(True)
     # a different launch shape changes only the order of nothing: each site's arithmetic is the same
     assert np.allclose(e0, e1, rtol=1e-9)
+
+
+@pytest.mark.parametrize("prec", [binding.MIXED_FP32, binding.FP64, binding.MIXED_FP16], ids=["fp32", "fp64", "fp16"])
+def test_whole_estimate_graph_replays_the_eager_estimate(ctx, prec):
+    """The second call of a chunk shape captures the whole estimate (noise, the four block solves,
+    the outer solve, the reductions) as one graph with device-controlled loops; later calls replay
+    it.  Same seeds give bit-identical exponents to the host-controlled path, for fresh noise on
+    every replay, and the replay counts the kernels its loops ran."""
+    c, dims = ctx
+    c.set_solver(prec, tol_outer=1e-10, tol_block=1e-12)
+    m2s = [0.045, 0.04]
+    c.use_graphs(False)
+    ref = [c.estimate_masses(m2s, 3, seed=s)[0] for s in (11, 12, 13)]
+    c.use_graphs(True)
+    n0 = c.use_graphs()
+    c.profile(True)
+    got = [c.estimate_masses(m2s, 3, seed=s) for s in (11, 12, 13)]  # eager, capture + replay, replay
+    launches = c.profile_read(binding.PROF_LAUNCHES)[0]
+    c.profile(False)
+    assert c.use_graphs() >= n0 + 2  # two replays of the whole estimate (plus Krylov-loop graphs)
+    for (e, lw, rv, info), e_ref in zip(got, ref):
+        assert np.array_equal(np.asarray(e), np.asarray(e_ref))
+        assert info["true_rel_residual"] <= 1e-10
+    assert not np.array_equal(np.asarray(got[1][0]), np.asarray(got[2][0]))  # new noise per replay
+    assert launches > 1000
