@@ -232,7 +232,7 @@ ddrw_status ddrw_use_graphs(ddrw_ctx *ctx, int enable, long *graph_launches);
 /* Autotuner of the stencil launches: on the first launch of each shape (precision, block length,
  * parities, right-hand sides, diagonal/post modes) it times right-hand sides per thread {1,2,4},
  * sites per CTA row {64,128,256}, right-hand-side rows per CTA {1,2} and the hop code form
- * (unrolled, rolled, batched loads) with CUDA events and keeps the fastest.  enable = 0 uses a fixed choice; either call
+ * (unrolled, rolled, batched loads, register caps, neighbour table) with CUDA events and keeps the fastest.  enable = 0 uses a fixed choice; either call
  * clears the tuned table.  The report lists the tuned shapes, one per line. */
 ddrw_status ddrw_autotune(ddrw_ctx *ctx, int enable);
 ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
@@ -240,8 +240,10 @@ ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
 /* Pins the configuration of every tunable stencil launch (overrides the autotuner): nr
  * right-hand sides per thread (1, 2 or 4), nt sites per CTA row (32 .. 256, a multiple of 32),
  * nw right-hand-side rows per CTA (nt * nw <= 256), roll 0 / 1 (unrolled / rolled hop code),
- * 2 / 3 (the loads of 4 / 8 hops issued ahead of their arithmetic) or 4 / 5 (unrolled with at
- * most 85 / 128 registers per thread); roll 2-4 need nr = 1, roll 5 nr <= 2.
+ * 2 / 3 (the loads of 4 / 8 hops issued ahead of their arithmetic), 4 / 5 (unrolled with at
+ * most 85 / 128 registers per thread) or 6 / 7 (as 5 / 4, with the neighbour indices read from a
+ * table built at ddrw_create, 32 bytes per site, instead of computed from the block-major site
+ * order); roll 2-4 and 7 need nr = 1, roll 5 and 6 nr <= 2.
  * A launch whose right-hand sides per mass slot are not a multiple of nr * nw runs with nr = nw = 1.
  * nr = 0 returns to autotuning.  DDRW_EINVAL for values outside these ranges. */
 ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll);

@@ -155,6 +155,7 @@ GeomDev geom_dev(const ddrw_ctx *ctx)
     g.blk_org = ctx->d_blk_org;
     g.blk_index = ctx->d_blk_index;
     g.tsign = ctx->antiperiodic ? -1 : 1;
+    g.nbr = ctx->d_nbr;
     return g;
 }
 
@@ -511,6 +512,9 @@ ddrw_status ddrw_create(ddrw_ctx **out, const int dims[4], const int block[4], i
     cudaMemcpy(ctx->d_blk_org, org.data(), sizeof(int) * 4 * nb, cudaMemcpyHostToDevice);
     cudaMemcpy(ctx->d_blk_index, number.data(), sizeof(int) * nb, cudaMemcpyHostToDevice);
     if (!suppP.empty()) cudaMemcpy(ctx->d_suppP, suppP.data(), sizeof(int) * suppP.size(), cudaMemcpyHostToDevice);
+    if (cudaMalloc(&ctx->d_nbr, sizeof(int4) * 2 * (size_t)ctx->V) != cudaSuccess) return fail(DDRW_ENOMEM);
+    build_nbr_table(ctx);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return fail(DDRW_ECUDA);
 
     size_t V = ctx->V;
     if (cudaMalloc(&ctx->U64, sizeof(double2) * 36 * V) != cudaSuccess ||
@@ -540,6 +544,7 @@ void ddrw_destroy(ddrw_ctx *ctx)
     cudaFree(ctx->d_blk_org);
     cudaFree(ctx->d_blk_index);
     cudaFree(ctx->d_suppP);
+    cudaFree(ctx->d_nbr);
     cudaFree(ctx->U64);
     cudaFree(ctx->U32);
     cudaFree(ctx->C64);

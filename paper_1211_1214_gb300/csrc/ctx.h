@@ -98,6 +98,7 @@ struct ddrw_ctx {
     long V, vh;
     int nblk, nblk_c;
     int *d_blk_nb = nullptr, *d_blk_org = nullptr, *d_blk_index = nullptr;
+    int4 *d_nbr = nullptr;  // neighbour table of the stencil's table forms, [2][V]
     long nP = 0;
     int *d_suppP = nullptr;  // internal site index of the k-th supp-P site (lexicographic order)
 
@@ -217,6 +218,7 @@ ddrw_status workspace(ddrw_ctx *ctx, const char *name, size_t bytes, void **out)
 void release_workspace(ddrw_ctx *ctx, const char *name);
 
 GeomDev geom_dev(const ddrw_ctx *ctx);
+void build_nbr_table(ddrw_ctx *ctx);
 
 // mass-dependent inverse of A(m), built on first use
 ddrw_status mass_inverse(ddrw_ctx *ctx, double m, MassInv **out);

@@ -44,7 +44,16 @@ struct GeomDev {
     const int *blk_org; // [nblk][4]: coordinates of the block origin
     const int *blk_index; // [nblk]: block number of the block with lexicographic block index B
     int tsign;          // -1: antiperiodic in time, +1: periodic
+    const int4 *nbr;    // [2][V] neighbour table (see NBR_IDX), nullptr while not built
 };
+
+// Neighbour table: for site s, nbr[s] = (+0, -0, +1, -1) and nbr[V + s] = (+2, -2, +3, -3), each
+// entry the internal index of the neighbour in that direction (bits 0-29), bit 30 set when the hop
+// leaves the block, bit 31 (the sign bit) set when the hop crosses the time boundary of the lattice
+// (where antiperiodic fields change sign).  Built once per geometry by the same neighbour()
+// arithmetic the other kernels use.
+constexpr int NBR_IDX = 0x3fffffff;
+constexpr int NBR_CROSS = 0x40000000;
 
 template <int BL> struct BlockShape {
     static constexpr int VB = BL * BL * BL * BL;

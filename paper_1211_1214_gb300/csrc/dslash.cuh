@@ -43,9 +43,11 @@ template <class P> struct DsArgs {
 };
 
 // ROLL selects the hop code form: 0 unrolled, 1 rolled, 2 / 3 batched loads of 4 / 8 hops,
-// 4 / 5 unrolled compiled for at least 3 / 2 CTAs of 256 threads per SM (<= 85 / 128 registers)
+// 4 / 5 unrolled compiled for at least 3 / 2 CTAs of 256 threads per SM (<= 85 / 128 registers),
+// 6 / 7 as 5 / 4 with the neighbours read from the neighbour table instead of computed
 template <class P, int BL, int HOPSEL, int NR, int ROLL = 0>
-__global__ void __launch_bounds__(256, ROLL == 4 ? 3 : ROLL == 5 ? 2 : 1) k_dslash(GeomDev g, DsArgs<P> a)
+__global__ void __launch_bounds__(256, (ROLL == 4 || ROLL == 7) ? 3 : (ROLL == 5 || ROLL == 6) ? 2 : 1)
+    k_dslash(GeomDev g, DsArgs<P> a)
 {
     using R = typename P::R;
     // groups of NR right-hand sides; a CTA holds blockDim.y groups (one per row of threads) of
@@ -61,7 +63,12 @@ __global__ void __launch_bounds__(256, ROLL == 4 ? 3 : ROLL == 5 ? 2 : 1) k_dsla
     const int pp = (int)(i / nper);
     const long s = (long)(a.par0 + pp) * g.vh + (long)a.blk0 * BlockShape<BL>::VBH + (i - pp * nper);
     Site<BL> st;
-    decode_site<BL>(s, g, st);
+    int4 n0;
+    if constexpr (ROLL >= 6) {
+        n0 = g.nbr[s];
+    } else {
+        decode_site<BL>(s, g, st);
+    }
 
     Spinor<R> acc[NR];
 #pragma unroll
@@ -71,6 +78,12 @@ __global__ void __launch_bounds__(256, ROLL == 4 ? 3 : ROLL == 5 ? 2 : 1) k_dsla
         if constexpr (ROLL == 2 || ROLL == 3) {  // batched loads, one right-hand side: 2 -> 4 hops, 3 -> 8 hops per batch
             static_assert(NR == 1, "batched hops take one right-hand side per thread");
             hop_batched<P, BL, HOPSEL, ROLL == 2 ? 4 : 8>(g, st, (int)s, in, a.U, acc[0]);
+        } else if constexpr (ROLL >= 6) {
+            hop_tab<P, HOPSEL, 0, NR>(g, n0.x, n0.y, (int)s, in, a.rstride, a.U, acc);
+            hop_tab<P, HOPSEL, 1, NR>(g, n0.z, n0.w, (int)s, in, a.rstride, a.U, acc);
+            const int4 n1 = g.nbr[g.V + s];  // loaded here: fewer registers live over the first hops
+            hop_tab<P, HOPSEL, 2, NR>(g, n1.x, n1.y, (int)s, in, a.rstride, a.U, acc);
+            hop_tab<P, HOPSEL, 3, NR>(g, n1.z, n1.w, (int)s, in, a.rstride, a.U, acc);
         } else if constexpr (ROLL == 1) {
             hop_multi_rolled<P, BL, HOPSEL, NR>(g, st, (int)s, in, a.rstride, a.U, acc);
         } else {
@@ -131,7 +144,8 @@ struct DsConfig {
     int nw = 1;    // CTA rows: groups of nr right-hand sides per CTA (nt * nw <= 256)
     int roll = 0;  // 1: forward and backward hops share the direction bodies (smaller code);
                    // 2 / 3: batched loads of 4 / 8 hops before their arithmetic (nr = 1); 4 / 5:
-                   // unrolled with at most 85 / 128 registers, more warps per SM (nr = 1 / nr <= 2)
+                   // unrolled with at most 85 / 128 registers, more warps per SM (nr = 1 / nr <= 2);
+                   // 6 / 7: 5 / 4 with the neighbours from the neighbour table (nr <= 2 / nr = 1)
 };
 
 template <class P, int BL>
@@ -171,6 +185,7 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
     long n = (long)c.npar * c.nblk * BlockShape<BL>::VBH;
     // launches that are not tuned (block-restricted hops, double-single) take one row
     if (c.hopsel != 0 || std::is_same<P, PrecDD>::value) cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
+    if (cfg.roll >= 6 && !g.nbr) cfg.roll = 11 - cfg.roll;  // no table: the computed-neighbour twin
     unsigned grid = (unsigned)(((n + cfg.nt - 1) / cfg.nt) * (c.nrhs / (cfg.nr * cfg.nw)));
     dim3 blk((unsigned)cfg.nt, (unsigned)cfg.nw);
     ++ctx->launches;
@@ -191,6 +206,9 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
             case 33: k_dslash<P, BL, 0, 1, 4><<<grid, blk, 0, ctx->stream>>>(g, a); break;
             case 41: k_dslash<P, BL, 0, 1, 5><<<grid, blk, 0, ctx->stream>>>(g, a); break;
             case 42: k_dslash<P, BL, 0, 2, 5><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 49: k_dslash<P, BL, 0, 1, 6><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 50: k_dslash<P, BL, 0, 2, 6><<<grid, blk, 0, ctx->stream>>>(g, a); break;
+            case 57: k_dslash<P, BL, 0, 1, 7><<<grid, blk, 0, ctx->stream>>>(g, a); break;
             default: k_dslash<P, BL, 0, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
             }
         } else if (c.hopsel == 1) {

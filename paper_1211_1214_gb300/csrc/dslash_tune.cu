@@ -6,7 +6,8 @@
 // mass slot), sites per CTA row in {64, 128, 256}, CTA rows (groups of NR right-hand sides of the
 // same sites, sharing links and clover terms in L1) in {1, 2}, at most 256 threads per CTA, and
 // the hop code form (unrolled, rolled, with the loads of 4 or 8 hops batched ahead of their
-// arithmetic, or unrolled under a register cap of 85 or 128 for more warps per SM) -- with CUDA
+// arithmetic, or unrolled under a register cap of 85 or 128 for more warps per SM, the last two
+// also with the neighbours read from the precomputed neighbour table) -- with CUDA
 // events on the context's stream, keeps the fastest,
 // and reuses it for every later launch of that shape.  The candidates run on the real
 // arguments: a stencil launch never reads its own output sites, so repeating it is harmless.
@@ -17,6 +18,15 @@
 #include "dslash.cuh"
 
 namespace ddrw {
+
+// right-hand sides per thread each hop code form supports
+static bool form_allowed(int nr, int roll)
+{
+    if (roll < 0 || roll > 7) return false;
+    if ((roll >= 2 && roll <= 4) || roll == 7) return nr == 1;
+    if (roll == 5 || roll == 6) return nr <= 2;
+    return true;
+}
 
 DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
                       void (*run)(ddrw_ctx *, const DslashCall &, DsConfig))
@@ -47,12 +57,11 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
     DsConfig best = def;
     float best_ms = 1e30f;
     const int nrs[3] = {1, 2, 4}, nts[3] = {64, 128, 256}, nws[2] = {1, 2};
-    for (int roll = 0; roll < 6; roll++)
+    for (int roll = 0; roll < 8; roll++)
     for (int nr : nrs) {
         // the batched and register-capped forms are for 32- and 16-bit storage: with FP64 data
         // they spill
-        if (c.nrhs % nr || rpm % nr || (roll >= 2 && prec == 64) || (roll >= 2 && roll <= 4 && nr != 1) ||
-            (roll == 5 && nr > 2))
+        if (c.nrhs % nr || rpm % nr || (roll >= 2 && prec == 64) || !form_allowed(nr, roll))
             continue;
         for (int nw : nws)
         for (int nt : nts) {
@@ -99,8 +108,8 @@ ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll)
         ctx->pinned_nr = 0;
         return DDRW_OK;
     }
-    if ((nr != 1 && nr != 2 && nr != 4) || nt < 32 || nt > 256 || nt % 32 || nw < 1 || nt * nw > 256 || roll < 0 ||
-        roll > 5 || (roll >= 2 && roll <= 4 && nr != 1) || (roll == 5 && nr > 2))
+    if ((nr != 1 && nr != 2 && nr != 4) || nt < 32 || nt > 256 || nt % 32 || nw < 1 || nt * nw > 256 ||
+        !form_allowed(nr, roll))
         return set_error(ctx, DDRW_EINVAL, "bad stencil configuration");
     ctx->pinned_nr = nr;
     ctx->pinned_nt = nt;

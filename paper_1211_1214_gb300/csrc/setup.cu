@@ -27,6 +27,33 @@ __global__ void k_pack_gauge(GeomDev g, const double *__restrict__ Ulex, double2
     }
 }
 
+// ----------------------------------------------------------------------------- neighbour table
+
+// one entry per site and hop, from decode_site / neighbour (the geometry copy has tsign = -1, so
+// that neighbour() reports every hop across the time boundary, whatever the boundary condition)
+template <int BL>
+__global__ void k_nbr_table(GeomDev g, int4 *t)
+{
+    long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    Site<BL> st;
+    decode_site<BL>(s, g, st);
+    int e[8];
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++)
+#pragma unroll
+        for (int d = 0; d < 2; d++) {
+            bool cross;
+            int ph;
+            unsigned n = (unsigned)neighbour<BL>(st, mu, d == 0 ? +1 : -1, g, &cross, &ph);
+            if (cross) n |= (unsigned)NBR_CROSS;
+            if (ph < 0) n |= 0x80000000u;
+            e[2 * mu + d] = (int)n;
+        }
+    t[s] = make_int4(e[0], e[1], e[2], e[3]);
+    t[g.V + s] = make_int4(e[4], e[5], e[6], e[7]);
+}
+
 // ----------------------------------------------------------------------------- clover
 
 template <int BL> void clover_launch(ddrw_ctx *ctx);
@@ -166,6 +193,14 @@ void pack_gauge(ddrw_ctx *ctx, const double *Ulex)
     GeomDev g = geom_dev(ctx);
     dim3 grid((unsigned)((ctx->V + 127) / 128));
     DISPATCH_BL(ctx, k_pack_gauge, grid, 128, g, Ulex, ctx->U64, ctx->U32);
+}
+
+void build_nbr_table(ddrw_ctx *ctx)
+{
+    GeomDev g = geom_dev(ctx);
+    g.tsign = -1;
+    dim3 grid((unsigned)((ctx->V + 127) / 128));
+    DISPATCH_BL(ctx, k_nbr_table, grid, 128, g, ctx->d_nbr);
 }
 
 void build_clover(ddrw_ctx *ctx)

@@ -128,6 +128,47 @@ __device__ __forceinline__ void hop_dir_multi(const GeomDev &g, const Site<BL> &
     }
 }
 
+// Hops of direction MU with the neighbours read from the neighbour table: nf / nb are the table
+// entries of the forward / backward hop (index, block-crossing bit, time-boundary sign bit).
+template <class P, int HOPSEL, int MU, int NR>
+__device__ __forceinline__ void hop_tab(const GeomDev &g, int nf, int nb, int s, const typename P::SElem *in,
+                                        long rstride, const typename P::UElem *__restrict__ U,
+                                        Spinor<typename P::R> (&acc)[NR])
+{
+    using R = typename P::R;
+    const int V = (int)g.V;
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+        const int e = d == 0 ? nf : nb;
+        const bool cross = (e & NBR_CROSS) != 0;
+        if (!(HOPSEL == 0 || (HOPSEL == 1 && !cross) || (HOPSEL == 2 && cross))) continue;
+        const int n = e & NBR_IDX;
+        const bool flip = e < 0 && g.tsign < 0;
+        Link<R> L;
+        P::load_link(U, V, MU, d == 0 ? s : n, L);  // backward links are stored at the neighbour
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            Spinor<R> p;
+            P::load_spinor(in + r * rstride, V, n, p);
+            Half<R> h, w;
+            if (d == 0) {
+                project<MU, -1>(p, h);
+                link_mul(L, h, w);
+            } else {
+                project<MU, +1>(p, h);
+                link_dag_mul(L, h, w);
+            }
+            if (flip)
+#pragma unroll
+                for (int a = 0; a < 2; a++)
+#pragma unroll
+                    for (int c = 0; c < 3; c++) w.v[a][c] = -w.v[a][c];
+            if (d == 0) reconstruct_add<MU, -1>(acc[r], w);
+            else reconstruct_add<MU, +1>(acc[r], w);
+        }
+    }
+}
+
 // ---- rolled form: the forward and backward hops of a direction share one body
 //
 // The projector sign sg (-1 forward, +1 backward) and the boundary phase enter as FMA

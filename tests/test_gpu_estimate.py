@@ -162,8 +162,9 @@ def test_mixed_precision_estimate_matches_fp64(case, prec):
 
 
 @pytest.mark.parametrize("prec", [binding.MIXED_FP32, binding.MIXED_FP16], ids=["fp32", "fp16"])
-@pytest.mark.parametrize("cfg", [(1, 128, 1, 1), (4, 64, 1, 0), (2, 64, 2, 1), (1, 128, 1, 2), (1, 64, 1, 3)],
-                         ids=["r1", "u4", "r2w2", "b4", "b8"])
+@pytest.mark.parametrize("cfg", [(1, 128, 1, 1), (4, 64, 1, 0), (2, 64, 2, 1), (1, 128, 1, 2), (1, 64, 1, 3),
+                                 (1, 64, 1, 6), (2, 128, 1, 6), (1, 64, 2, 7)],
+                         ids=["r1", "u4", "r2w2", "b4", "b8", "t1", "t2", "t1w2"])
 def test_mixed_estimate_under_pinned_stencil_configs(case, prec, cfg):
     """The low-precision stencils in each pinned launch configuration lead to the FP64 result."""
     ctx = case["ctx"]

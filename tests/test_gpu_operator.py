@@ -72,10 +72,11 @@ def test_apply_D_double_single(setup, m):
 @pytest.mark.parametrize("nr,nt,nw,roll", [(1, 64, 1, 0), (1, 64, 1, 1), (2, 128, 1, 0), (2, 128, 2, 1),
                                            (4, 32, 2, 0), (4, 256, 1, 1), (1, 32, 8, 1), (1, 128, 1, 2),
                                            (1, 64, 2, 3), (1, 256, 1, 4), (1, 128, 2, 5),
-                                           (2, 128, 1, 5)])
+                                           (2, 128, 1, 5), (1, 64, 1, 6), (2, 128, 1, 6), (1, 128, 2, 7)])
 def test_every_stencil_configuration(setup, nr, nt, nw, roll):
     """Each pinned launch configuration of the all-hop stencil (right-hand sides per thread, CTA
-    shape, unrolled or rolled hop code) gives the oracle's operator on 4 right-hand sides."""
+    shape, hop code form, computed or tabulated neighbours) gives the oracle's operator on 4
+    right-hand sides."""
     ctx, lat, dims = setup
     x = synth.spinor_field(dims, seed=9, nrhs=4)
     y = np.zeros_like(x)
@@ -98,7 +99,10 @@ def test_apply_block(setup, rows, cols):
     assert rel(y.cpu().numpy(), ref) < 1e-12
 
 
-def test_antiperiodic_time():
+@pytest.mark.parametrize("cfg", [None, (1, 64, 1, 6), (1, 64, 1, 7)], ids=["tuned", "table128", "table85"])
+def test_antiperiodic_time(cfg):
+    """Antiperiodic time boundary: the sign of the hops across t = T-1 -> 0, also in the forms that
+    read the time-boundary bit from the neighbour table."""
     dims, l = (8, 4, 4, 4), 2
     U = synth.gauge_field(dims, 0.3, seed=3)
     ctx = binding.Context(dims, (l,) * 4)
@@ -107,8 +111,14 @@ def test_antiperiodic_time():
     lat = oc.Lattice(dims, (l,) * 4, U, 1.2, antiperiodic_t=True)
     x = synth.spinor_field(dims, seed=8)
     y = np.zeros_like(x)
+    if cfg:
+        ctx.stencil_config(*cfg)
     ctx.apply_D(0.1, x, y)
     assert rel(y, lat.apply(0.1, x)) < 1e-12
+    # the same context back to periodic: the table does not depend on the boundary condition
+    ctx.set_params(1.2, 0.1, 0.09, antiperiodic_t=False)
+    ctx.apply_D(0.1, x, y)
+    assert rel(y, oc.Lattice(dims, (l,) * 4, U, 1.2).apply(0.1, x)) < 1e-12
     ctx.close()
 
 
