@@ -53,7 +53,9 @@ typedef enum {
     DDRW_ENOCONV = 4,   /* a solver hit its iteration cap; outputs hold the last iterate */
     DDRW_ENUMERIC = 5,  /* NaN or Inf in a reduction */
     DDRW_EDOMAIN = 6,   /* the estimate is outside its domain of definition */
-    DDRW_ESTATE = 7     /* call out of order (e.g. no gauge field loaded) */
+    DDRW_ESTATE = 7,    /* call out of order (e.g. no gauge field loaded) */
+    DDRW_ETIMEOUT = 8   /* a bounded device-side wait ran out (the staged stencil's copies did not
+                           land); the call's outputs are invalid, the context stays usable */
 } ddrw_status;
 
 typedef enum {
@@ -111,6 +113,15 @@ ddrw_status ddrw_apply_D(ddrw_ctx *ctx, double m, const double *in, double *out,
  * the mixed precisions use for their defect-correction residuals b - D x; for checking that
  * arithmetic against ddrw_apply_D. */
 ddrw_status ddrw_apply_D_ds(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs);
+
+/* The operator of Eq. 1 as the inner solves evaluate it: in is rounded to the storage precision
+ * prec (DDRW_MIXED_FP32: FP32 fields; DDRW_MIXED_FP16 / DDRW_MIXED_BF16: 16-bit fields with a
+ * per-site scale), one stencil launch in that storage with FP32 arithmetic (the tuned or pinned
+ * launch form, see ddrw_stencil_config) computes D(m) in, or A(m)^-1 D(m) in (the site-diagonal
+ * inverse applied to the result) when post != 0, and the result is widened to FP64 into out.
+ * Layouts as ddrw_apply_D (host or device buffers).  DDRW_EINVAL for another prec. */
+ddrw_status ddrw_apply_D_low(ddrw_ctx *ctx, ddrw_prec prec, double m, int post, const double *in, double *out,
+                             int nrhs);
 
 /* out = D_{rows,cols}(m) in: the block of Eq. 1 with rows in colour `rows` and columns in colour
  * `cols` (DDRW_BLACK, DDRW_WHITE or DDRW_ALL); rows outside `rows` are set to zero.  D_bb and
@@ -241,12 +252,23 @@ ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
  * right-hand sides per thread (1, 2 or 4), nt sites per CTA row (32 .. 256, a multiple of 32),
  * nw right-hand-side rows per CTA (nt * nw <= 256), roll 0 / 1 (unrolled / rolled hop code),
  * 2 / 3 (the loads of 4 / 8 hops issued ahead of their arithmetic), 4 / 5 (unrolled with at
- * most 85 / 128 registers per thread) or 6 / 7 (as 5 / 4, with the neighbour indices read from a
+ * most 85 / 128 registers per thread), 6 / 7 (as 5 / 4, with the neighbour indices read from a
  * table built at ddrw_create, 32 bytes per site, instead of computed from the block-major site
- * order); roll 2-4 and 7 need nr = 1, roll 5 and 6 nr <= 2.
+ * order) or 8 (staged, FP32 storage only: a CTA of nt sites x nw rows covers every right-hand side
+ * of one mass slot; the tile's links, A^-1 / clover terms and neighbour entries are brought into
+ * shared memory once by bulk asynchronous copies and shared by those right-hand sides; nt <= 128;
+ * other storage precisions run form 5 instead); roll 2-4, 7 and 8 need nr = 1, roll 5 and 6
+ * nr <= 2.
  * A launch whose right-hand sides per mass slot are not a multiple of nr * nw runs with nr = nw = 1.
  * nr = 0 returns to autotuning.  DDRW_EINVAL for values outside these ranges. */
 ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll);
+
+/* Test switch of the staged stencil's bounded wait (form 8): with enable != 0 every staged launch
+ * announces 16 bytes more than its copies deliver, so its shared-memory barrier never completes;
+ * each CTA stops polling after a bounded number of tries, sets the context's device error flag and
+ * returns, and the call that launched it returns DDRW_ETIMEOUT at its next synchronisation.
+ * enable = 0 restores normal operation; the context remains usable either way. */
+ddrw_status ddrw_test_stall_staging(ddrw_ctx *ctx, int enable);
 
 /* The exact block factor of Eq. 7: W = W_gl prod_k det D_k^2(m2) / det D_k^2(m1), k over the black
  * and the white blocks, D_k the block Dirac operators on the diagonal of D_bb and D_ww (Eq. 1).

@@ -18,7 +18,7 @@ FP64, MIXED_FP32, MIXED_FP16, MIXED_BF16 = 0, 1, 2, 3
 BLACK, WHITE, ALL = 0, 1, 2
 
 _STATUS = {0: "DDRW_OK", 1: "DDRW_EINVAL", 2: "DDRW_ENOMEM", 3: "DDRW_ECUDA", 4: "DDRW_ENOCONV",
-           5: "DDRW_ENUMERIC", 6: "DDRW_EDOMAIN", 7: "DDRW_ESTATE"}
+           5: "DDRW_ENUMERIC", 6: "DDRW_EDOMAIN", 7: "DDRW_ESTATE", 8: "DDRW_ETIMEOUT"}
 
 #: every entry point declared in include/ddrw.h
 EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", "ddrw_volume", "ddrw_load_gauge",
@@ -27,7 +27,7 @@ EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", 
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
            "ddrw_autotune", "ddrw_autotune_report", "ddrw_stencil_config", "ddrw_profile_units",
            "ddrw_block_logdet", "ddrw_block_factor", "ddrw_estimate_variant", "ddrw_force", "ddrw_use_graphs",
-           "ddrw_estimate_interp", "ddrw_apply_D_ds"]
+           "ddrw_estimate_interp", "ddrw_apply_D_ds", "ddrw_test_stall_staging", "ddrw_apply_D_low"]
 
 #: kernel classes of ddrw_profile_read
 PROF_DSLASH64, PROF_DSLASH32, PROF_DSLASH64_BLK, PROF_DSLASH32_BLK, PROF_BLOCK64, PROF_BLOCK32, PROF_BLAS, PROF_DSLASH_DS, \
@@ -78,6 +78,7 @@ def load(path: str | None = None):
         "ddrw_set_solver": (st, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
         "ddrw_apply_D": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_apply_D_ds": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
+        "ddrw_apply_D_low": (st, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, ctypes.c_int]),
         "ddrw_apply_block": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_solve_block": (st, [vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
         "ddrw_solve_D": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
@@ -92,6 +93,7 @@ def load(path: str | None = None):
         "ddrw_profile": (st, [vp, ctypes.c_int]),
         "ddrw_autotune": (st, [vp, ctypes.c_int]),
         "ddrw_stencil_config": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "ddrw_test_stall_staging": (st, [vp, ctypes.c_int]),
         "ddrw_profile_units": (st, [vp, ctypes.c_int, dp]),
         "ddrw_block_logdet": (st, [vp, ctypes.c_double, dp, dp]),
         "ddrw_block_factor": (st, [vp, dp]),
@@ -186,6 +188,11 @@ class Context:
 
     def apply_D_ds(self, m, x, out, nrhs=1):
         self._check(self.L.ddrw_apply_D_ds(self._h, float(m), _ptr(x), _ptr(out), int(nrhs)), "ddrw_apply_D_ds")
+
+    def apply_D_low(self, prec, m, x, out, nrhs=1, post=False):
+        """out = D(m) x (post: A(m)^-1 D(m) x) by one stencil launch in storage precision prec."""
+        self._check(self.L.ddrw_apply_D_low(self._h, int(prec), float(m), int(bool(post)), _ptr(x), _ptr(out),
+                                            int(nrhs)), "ddrw_apply_D_low")
 
     def apply_block(self, rows, cols, m, x, out, nrhs=1):
         self._check(self.L.ddrw_apply_block(self._h, int(rows), int(cols), float(m), _ptr(x), _ptr(out), int(nrhs)),
@@ -293,6 +300,11 @@ class Context:
     def stencil_config(self, nr=0, nt=128, nw=1, roll=0):
         """Pin the stencil launch configuration (nr = 0: back to the autotuner)."""
         self._check(self.L.ddrw_stencil_config(self._h, int(nr), int(nt), int(nw), int(roll)), "ddrw_stencil_config")
+
+    def test_stall_staging(self, enable):
+        """Test switch: staged stencil launches wait for bytes that never come (bounded wait, then
+        DDRW_ETIMEOUT); False restores normal operation."""
+        self._check(self.L.ddrw_test_stall_staging(self._h, int(bool(enable))), "ddrw_test_stall_staging")
 
     def autotune_report(self):
         buf = ctypes.create_string_buffer(1 << 16)

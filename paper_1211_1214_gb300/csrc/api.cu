@@ -6,6 +6,7 @@
 
 #include "blas.cuh"
 #include "ctx.h"
+#include "lowprec.cuh"
 
 namespace ddrw {
 
@@ -245,6 +246,10 @@ ddrw_status sync(ddrw_ctx *ctx)
 {
     DDRW_CUDA_CHECK(cudaGetLastError());
     DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->h_err && *(volatile int *)ctx->h_err) {
+        *(volatile int *)ctx->h_err = 0;
+        return set_error(ctx, DDRW_ETIMEOUT, "a staged stencil launch gave up waiting for its shared-memory copies");
+    }
     return DDRW_OK;
 }
 
@@ -359,6 +364,44 @@ static void prof_collect(ddrw_ctx *ctx)
         ctx->prof_pool.push_back(r.b);
     }
     ctx->prof_pending.clear();
+}
+
+// the storage-precision stencil on full fields: out = D(m) in, or A(m)^-1 D(m) in (post)
+template <class P>
+static ddrw_status apply_low(ddrw_ctx *ctx, double m, int post, const double2 *fin, double2 *fout, int nrhs)
+{
+    using E = typename P::SElem;
+    const long rsl = P::field_elems(ctx->V);
+    E *lin, *lout;
+    ddrw_status st;
+    if ((st = workspace(ctx, "api_low0", sizeof(E) * rsl * nrhs, (void **)&lin))) return st;
+    if ((st = workspace(ctx, "api_low1", sizeof(E) * rsl * nrhs, (void **)&lout))) return st;
+    MassInv *mi = nullptr;
+    if (post && (st = mass_inverse(ctx, m, &mi))) return st;
+    const VecRange all{ctx->V, 0, ctx->V, 12 * ctx->V, nrhs};
+    to_low<P>(ctx, all, rsl, fin, lin, nullptr);
+    DslashCall c;
+    c.in = lin;
+    c.x = lin;
+    c.out = lout;
+    c.rstride = rsl;
+    c.nrhs = nrhs;
+    c.masses[0] = m;
+    if (post) c.Ainv[0] = ainv_for(mi, P::ID);
+    c.alpha = 1.0;
+    c.beta = -0.5;
+    c.diag = 1;
+    c.post = post;
+    c.par0 = 0;
+    c.npar = 2;
+    c.blk0 = 0;
+    c.nblk = ctx->nblk;
+    if constexpr (P::ID == 32) dslash32(ctx, c);
+    else if constexpr (P::ID == 16) dslash16(ctx, c);
+    else dslashb16(ctx, c);
+    DDRW_CUDA_CHECK(cudaMemsetAsync(fout, 0, sizeof(double2) * 12 * ctx->V * nrhs, ctx->stream));
+    add_low<P>(ctx, all, rsl, lout, fout, nullptr);
+    return DDRW_OK;
 }
 
 }  // namespace ddrw
@@ -512,7 +555,12 @@ ddrw_status ddrw_create(ddrw_ctx **out, const int dims[4], const int block[4], i
     cudaMemcpy(ctx->d_blk_org, org.data(), sizeof(int) * 4 * nb, cudaMemcpyHostToDevice);
     cudaMemcpy(ctx->d_blk_index, number.data(), sizeof(int) * nb, cudaMemcpyHostToDevice);
     if (!suppP.empty()) cudaMemcpy(ctx->d_suppP, suppP.data(), sizeof(int) * suppP.size(), cudaMemcpyHostToDevice);
-    if (cudaMalloc(&ctx->d_nbr, sizeof(int4) * 2 * (size_t)ctx->V) != cudaSuccess) return fail(DDRW_ENOMEM);
+    if (cudaMalloc(&ctx->d_nbr, sizeof(int4) * 2 * (size_t)ctx->V) != cudaSuccess ||
+        cudaMalloc(&ctx->Ubw32, sizeof(float4) * 12 * (size_t)ctx->V) != cudaSuccess)
+        return fail(DDRW_ENOMEM);
+    if (cudaHostAlloc(&ctx->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess) return fail(DDRW_ENOMEM);
+    *ctx->h_err = 0;
+    if (cudaHostGetDevicePointer(&ctx->d_err, ctx->h_err, 0) != cudaSuccess) return fail(DDRW_ECUDA);
     build_nbr_table(ctx);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return fail(DDRW_ECUDA);
 
@@ -545,6 +593,8 @@ void ddrw_destroy(ddrw_ctx *ctx)
     cudaFree(ctx->d_blk_index);
     cudaFree(ctx->d_suppP);
     cudaFree(ctx->d_nbr);
+    cudaFree(ctx->Ubw32);
+    if (ctx->h_err) cudaFreeHost(ctx->h_err);
     cudaFree(ctx->U64);
     cudaFree(ctx->U32);
     cudaFree(ctx->C64);
@@ -589,6 +639,7 @@ ddrw_status ddrw_volume(ddrw_ctx *ctx, long *n)
 static ddrw_status rebuild(ddrw_ctx *ctx)
 {
     build_clover(ctx);
+    build_bw_links(ctx);
     DDRW_CUDA_CHECK(cudaGetLastError());
     // 16-bit copies of the two-row links and the clover term for the FP16 / BF16 inner solves
     f32_to_low(ctx, ctx->U32, ctx->U16, 12L * ctx->V, false);
@@ -714,6 +765,34 @@ ddrw_status ddrw_apply_block(ddrw_ctx *ctx, int rows, int cols, double m, const 
 ddrw_status ddrw_apply_D(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs)
 {
     return ddrw_apply_block(ctx, DDRW_ALL, DDRW_ALL, m, in, out, nrhs);
+}
+
+ddrw_status ddrw_apply_D_low(ddrw_ctx *ctx, ddrw_prec prec, double m, int post, const double *in, double *out,
+                             int nrhs)
+{
+    if (!ctx || !in || !out || nrhs <= 0 || (prec != DDRW_MIXED_FP32 && prec != DDRW_MIXED_FP16 && prec != DDRW_MIXED_BF16))
+        return set_error(ctx, DDRW_EINVAL, "bad argument");
+    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
+    cudaSetDevice(ctx->device);
+    size_t ubytes = sizeof(double) * 24 * (size_t)ctx->V * nrhs;
+    size_t fbytes = sizeof(double2) * 12 * (size_t)ctx->V * nrhs;
+    const void *din;
+    void *dout;
+    bool host_out;
+    double2 *fin, *fout;
+    ddrw_status st;
+    if ((st = stage_in(ctx, in, ubytes, "stage_in", &din))) return st;
+    if ((st = stage_out(ctx, out, ubytes, "stage_out", &dout, &host_out))) return st;
+    if ((st = workspace(ctx, "api_f0", fbytes, (void **)&fin))) return st;
+    if ((st = workspace(ctx, "api_f1", fbytes, (void **)&fout))) return st;
+    pack_spinor64(ctx, (const double *)din, fin, nrhs);
+    if (prec == DDRW_MIXED_FP32) st = apply_low<PrecS>(ctx, m, post != 0, fin, fout, nrhs);
+    else if (prec == DDRW_MIXED_FP16) st = apply_low<PrecH>(ctx, m, post != 0, fin, fout, nrhs);
+    else st = apply_low<PrecB>(ctx, m, post != 0, fin, fout, nrhs);
+    if (st) return st;
+    unpack_spinor64(ctx, fout, (double *)dout, nrhs);
+    if ((st = finish_out(ctx, out, dout, ubytes, host_out))) return st;
+    return sync(ctx);
 }
 
 ddrw_status ddrw_apply_D_ds(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs)

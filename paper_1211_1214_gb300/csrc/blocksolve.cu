@@ -70,7 +70,7 @@ static ddrw_status colour_norms(ddrw_ctx *ctx, int colour, const double2 *f, int
     }
     std::vector<double> h(2 * nrhs);
     DDRW_CUDA_CHECK(cudaMemcpyAsync(h.data(), d, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-    DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    DDRW_SYNC(ctx);
     out.resize(nrhs);
     for (int r = 0; r < nrhs; r++) out[r] = h[r] + h[nrhs + r];
     return DDRW_OK;

@@ -99,6 +99,9 @@ struct ddrw_ctx {
     int nblk, nblk_c;
     int *d_blk_nb = nullptr, *d_blk_org = nullptr, *d_blk_index = nullptr;
     int4 *d_nbr = nullptr;  // neighbour table of the stencil's table forms, [2][V]
+    float4 *Ubw32 = nullptr;  // [12][V]: FP32 two-row U_mu(x - mu) stored at x (staged stencil)
+    int *h_err = nullptr, *d_err = nullptr;  // device error flags, host-mapped (bit 0: staging wait ran out)
+    int stall_tx = 0;                        // test switch of the staged stencil (extra announced bytes)
     long nP = 0;
     int *d_suppP = nullptr;  // internal site index of the k-th supp-P site (lexicographic order)
 
@@ -219,6 +222,7 @@ void release_workspace(ddrw_ctx *ctx, const char *name);
 
 GeomDev geom_dev(const ddrw_ctx *ctx);
 void build_nbr_table(ddrw_ctx *ctx);
+void build_bw_links(ddrw_ctx *ctx);
 
 // mass-dependent inverse of A(m), built on first use
 ddrw_status mass_inverse(ddrw_ctx *ctx, double m, MassInv **out);
@@ -229,6 +233,12 @@ ddrw_status stage_in(ddrw_ctx *ctx, const void *user, size_t bytes, const char *
 ddrw_status stage_out(ddrw_ctx *ctx, void *user, size_t bytes, const char *name, void **dev, bool *host);
 ddrw_status finish_out(ddrw_ctx *ctx, void *user, const void *dev, size_t bytes, bool host);
 ddrw_status sync(ddrw_ctx *ctx);
+// synchronises the stream and reports CUDA errors and the device error flags as the caller's status
+#define DDRW_SYNC(ctx)                       \
+    do {                                     \
+        ddrw_status s__ = sync(ctx);         \
+        if (s__ != DDRW_OK) return s__;      \
+    } while (0)
 void zero_colour64(ddrw_ctx *ctx, double2 *f, int colour, int nrhs);
 
 // ---- launchers (all on ctx->stream)

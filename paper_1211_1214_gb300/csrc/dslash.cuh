@@ -24,6 +24,7 @@
 #include "ddprec.cuh"
 #include "lowprec.cuh"
 #include "stencil.cuh"
+#include "tma.cuh"
 
 namespace ddrw {
 
@@ -40,7 +41,182 @@ template <class P> struct DsArgs {
     int nrhs, rpm;
     typename P::R mass4[MAXM];           // 4 + m per slot
     const typename P::CElem *Ainv[MAXM];  // A(m)^-1 per slot
+    const typename P::UElem *Ubw;         // backward links U_mu(x - mu) stored at x (staged form)
+    int *err;                             // device error flags (bit 0: a staging wait ran out)
+    int stall_tx;                         // test switch: bytes announced on top of the staged copies
 };
+
+// ---- staged form (FP32 two-row links): one CTA covers a tile of consecutive output sites for all
+// right-hand sides of one mass slot.  One warp stages the tile's links (forward ones at the site,
+// backward ones from the copy stored at the site), the A^-1 and clover blocks the launch needs and
+// the neighbour-table entries into shared memory with bulk asynchronous copies, completed on an
+// mbarrier; then every thread runs its site for right-hand sides threadIdx.y, +blockDim.y, ...,
+// reading those terms from shared memory and only the spinors from global memory.  Shared memory
+// holds [plane][site of the tile] 16-byte elements:
+//   0-11 forward links (mu, row-pair), 12-23 backward links, then 18 planes of A^-1 (post),
+//   18 of the clover term (diag == 1), 2 of neighbour entries.
+constexpr int STAGE_WAIT_TRIES = 1 << 16;
+
+template <int BL>
+__global__ void __launch_bounds__(256, 2) k_dslash_staged(GeomDev g, DsArgs<PrecS> a)
+{
+    using R = float;
+    extern __shared__ __align__(128) float4 stg[];
+    __shared__ __align__(8) uint64_t bar;
+    const int NS = blockDim.x, W = blockDim.y;
+    const int tid = threadIdx.y * NS + threadIdx.x;
+    const int nslot = (a.nrhs + a.rpm - 1) / a.rpm;
+    const long nper = (long)a.nblk * BlockShape<BL>::VBH;
+    const long tile = blockIdx.x / nslot;
+    const int slot = (int)(blockIdx.x - tile * nslot);
+    const long i0 = tile * NS;
+    const int nvalid = (int)min((long)NS, nper * a.npar - i0);
+    const int pp = (int)(i0 / nper);  // the tile lies in one parity (launcher's rule)
+    const long s0 = (long)(a.par0 + pp) * g.vh + (long)a.blk0 * BlockShape<BL>::VBH + (i0 - pp * nper);
+    const long V = g.V;
+    const int pA = 24, pC = pA + (a.post ? 18 : 0), pN = pC + (a.diag == 1 ? 18 : 0), np = pN + 2;
+
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid < 32) {  // warp 0 issues the copies, lane k the planes k, k + 32
+        const uint32_t seg = (uint32_t)nvalid * 16u;
+        if (tid == 0) mbar_arrive_expect_tx(&bar, seg * (uint32_t)np + (uint32_t)a.stall_tx);
+        __syncwarp();
+        for (int q = tid; q < np; q += 32) {
+            const void *src;
+            if (q < 12) src = a.U + (long)q * V + s0;
+            else if (q < 24) src = a.Ubw + (long)(q - 12) * V + s0;
+            else if (q < pC) src = a.Ainv[slot] + (long)(q - pA) * V + s0;
+            else if (q < pN) src = a.Cl + (long)(q - pC) * V + s0;
+            else src = g.nbr + (long)(q - pN) * V + s0;
+            bulk_copy_g2s(stg + (long)q * NS, src, seg, &bar);
+        }
+    }
+    if (!mbar_wait_bounded(&bar, 0, STAGE_WAIT_TRIES)) {
+        if (threadIdx.x == 0) atomicOr(a.err, 1);
+        return;
+    }
+    const int j = threadIdx.x;
+    if (j >= nvalid) return;
+    const int s = (int)(s0 + j);
+    // neighbour entry q = 2 mu + d of this site: component q % 4 of plane pN + q / 4
+    const int *nb = reinterpret_cast<const int *>(stg + (long)pN * NS + j);
+    const int rb = slot * a.rpm, re = min(rb + a.rpm, a.nrhs);
+    for (int r = rb + threadIdx.y; r < re; r += W) {
+        const long roff = (long)r * a.rstride;
+        Spinor<R> acc;
+        zero(acc);
+        if (a.beta != R(0)) {
+            const float4 *in = a.in + roff;
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++)
+#pragma unroll
+                for (int d = 0; d < 2; d++) {
+                    const int q = 2 * mu + d;
+                    const int e = nb[(q / 4) * 4 * NS + q % 4];
+                    const int n = e & NBR_IDX;
+                    const bool flip = e < 0 && g.tsign < 0;
+                    const float4 *lk = stg + (long)(d * 12 + mu * 3) * NS + j;
+                    const float4 a0 = lk[0], a1 = lk[NS], a2 = lk[2 * NS];
+                    Link<R> L;
+                    L.m[0][0] = {a0.x, a0.y};
+                    L.m[0][1] = {a0.z, a0.w};
+                    L.m[0][2] = {a1.x, a1.y};
+                    L.m[1][0] = {a1.z, a1.w};
+                    L.m[1][1] = {a2.x, a2.y};
+                    L.m[1][2] = {a2.z, a2.w};
+                    PrecS::reconstruct_row2(L);
+                    Spinor<R> p;
+                    PrecS::load_spinor(in, (int)V, n, p);
+                    Half<R> h, w;
+                    if (d == 0) {
+                        if (mu == 0) project<0, -1>(p, h);
+                        else if (mu == 1) project<1, -1>(p, h);
+                        else if (mu == 2) project<2, -1>(p, h);
+                        else project<3, -1>(p, h);
+                        link_mul(L, h, w);
+                    } else {
+                        if (mu == 0) project<0, +1>(p, h);
+                        else if (mu == 1) project<1, +1>(p, h);
+                        else if (mu == 2) project<2, +1>(p, h);
+                        else project<3, +1>(p, h);
+                        link_dag_mul(L, h, w);
+                    }
+                    if (flip)
+#pragma unroll
+                        for (int b = 0; b < 2; b++)
+#pragma unroll
+                            for (int c = 0; c < 3; c++) w.v[b][c] = -w.v[b][c];
+                    if (d == 0) {
+                        if (mu == 0) reconstruct_add<0, -1>(acc, w);
+                        else if (mu == 1) reconstruct_add<1, -1>(acc, w);
+                        else if (mu == 2) reconstruct_add<2, -1>(acc, w);
+                        else reconstruct_add<3, -1>(acc, w);
+                    } else {
+                        if (mu == 0) reconstruct_add<0, +1>(acc, w);
+                        else if (mu == 1) reconstruct_add<1, +1>(acc, w);
+                        else if (mu == 2) reconstruct_add<2, +1>(acc, w);
+                        else reconstruct_add<3, +1>(acc, w);
+                    }
+                }
+            scale(acc, a.beta);
+        }
+        if (a.diag) {
+            const float4 *x = a.x + roff;
+#pragma unroll
+            for (int ch = 0; ch < 2; ch++) {
+                cpx<R> v6[6], o6[6];
+                PrecS::load_chiral(x, (int)V, s, ch, v6);
+                if (a.diag == 1) {
+                    R c[36];
+#pragma unroll
+                    for (int k = 0; k < 9; k++) {
+                        const float4 q = stg[(long)(pC + ch * 9 + k) * NS + j];
+                        c[4 * k] = q.x;
+                        c[4 * k + 1] = q.y;
+                        c[4 * k + 2] = q.z;
+                        c[4 * k + 3] = q.w;
+                    }
+                    herm6_mul<R>(c, a.mass4[slot], v6, o6);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 6; k++) o6[k] = v6[k];
+                }
+#pragma unroll
+                for (int k = 0; k < 6; k++)
+                    acc.v[2 * ch + k / 3][k % 3] = acc.v[2 * ch + k / 3][k % 3] + a.alpha * o6[k];
+            }
+        }
+        if (a.post) {
+#pragma unroll
+            for (int ch = 0; ch < 2; ch++) {
+                R c[36];
+#pragma unroll
+                for (int k = 0; k < 9; k++) {
+                    const float4 q = stg[(long)(pA + ch * 9 + k) * NS + j];
+                    c[4 * k] = q.x;
+                    c[4 * k + 1] = q.y;
+                    c[4 * k + 2] = q.z;
+                    c[4 * k + 3] = q.w;
+                }
+                cpx<R> v6[6], o6[6];
+#pragma unroll
+                for (int k = 0; k < 6; k++) v6[k] = acc.v[2 * ch + k / 3][k % 3];
+                herm6_mul<R>(c, R(0), v6, o6);
+#pragma unroll
+                for (int k = 0; k < 6; k++) acc.v[2 * ch + k / 3][k % 3] = o6[k];
+            }
+        }
+        PrecS::store_spinor(a.out + roff, (int)V, s, acc);
+    }
+}
+
+// shared memory of a staged launch, and the largest any staged launch asks for
+inline size_t staged_smem(int nt, int diag, int post) { return (size_t)(26 + 18 * (post != 0) + 18 * (diag == 1)) * nt * 16; }
+constexpr size_t STAGED_SMEM_MAX = (size_t)62 * 128 * 16;
 
 // ROLL selects the hop code form: 0 unrolled, 1 rolled, 2 / 3 batched loads of 4 / 8 hops,
 // 4 / 5 unrolled compiled for at least 3 / 2 CTAs of 256 threads per SM (<= 85 / 128 registers),
@@ -142,7 +318,9 @@ struct DsConfig {
     int nr = 1;    // right-hand sides per thread
     int nt = 128;  // sites per CTA (threads per CTA row)
     int nw = 1;    // CTA rows: groups of nr right-hand sides per CTA (nt * nw <= 256)
-    int roll = 0;  // 1: forward and backward hops share the direction bodies (smaller code);
+    int roll = 0;  // 8: staged (FP32 storage; nt sites by nw rows of right-hand sides, links and
+                   // clover terms in shared memory, every right-hand side of a mass slot per CTA);
+                   // 1: forward and backward hops share the direction bodies (smaller code);
                    // 2 / 3: batched loads of 4 / 8 hops before their arithmetic (nr = 1); 4 / 5:
                    // unrolled with at most 85 / 128 registers, more warps per SM (nr = 1 / nr <= 2);
                    // 6 / 7: 5 / 4 with the neighbours from the neighbour table (nr <= 2 / nr = 1)
@@ -175,6 +353,9 @@ DsArgs<P> make_args(ddrw_ctx *ctx, const DslashCall &c)
     }
     a.U = (const typename P::UElem *)links_for(ctx, P::ID);
     a.Cl = (const typename P::CElem *)clover_for(ctx, P::ID);
+    a.Ubw = std::is_same<P, PrecS>::value ? (const typename P::UElem *)ctx->Ubw32 : nullptr;
+    a.err = ctx->d_err;
+    a.stall_tx = ctx->stall_tx;
     return a;
 }
 
@@ -185,7 +366,29 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
     long n = (long)c.npar * c.nblk * BlockShape<BL>::VBH;
     // launches that are not tuned (block-restricted hops, double-single) take one row
     if (c.hopsel != 0 || std::is_same<P, PrecDD>::value) cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
-    if (cfg.roll >= 6 && !g.nbr) cfg.roll = 11 - cfg.roll;  // no table: the computed-neighbour twin
+    if (cfg.roll >= 6 && cfg.roll <= 7 && !g.nbr) cfg.roll = 11 - cfg.roll;  // no table: the computed-neighbour twin
+    if (cfg.roll == 8) {
+        // the staged form: FP32 storage, all hops, a tile never straddles the two parities
+        const long nper = n / std::max(c.npar, 1);
+        const bool ok = std::is_same<P, PrecS>::value && c.hopsel == 0 && g.nbr && a.Ubw && a.err &&
+                        (c.npar == 1 || nper % cfg.nt == 0) && cfg.nt <= 128;
+        if (!ok) cfg.nr = 1, cfg.nw = 1, cfg.roll = 5;
+    }
+    if constexpr (std::is_same<P, PrecS>::value) {
+        if (cfg.roll == 8) {
+            const int nslot = (c.nrhs + a.rpm - 1) / a.rpm;
+            static bool attr = false;  // per block length: the kernel may take up to STAGED_SMEM_MAX
+            if (!attr) {
+                cudaFuncSetAttribute(k_dslash_staged<BL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)STAGED_SMEM_MAX);
+                attr = true;
+            }
+            ++ctx->launches;
+            k_dslash_staged<BL><<<(unsigned)(((n + cfg.nt - 1) / cfg.nt) * nslot), dim3((unsigned)cfg.nt, (unsigned)cfg.nw),
+                                  staged_smem(cfg.nt, c.diag, c.post), ctx->stream>>>(g, a);
+            return;
+        }
+    }
     unsigned grid = (unsigned)(((n + cfg.nt - 1) / cfg.nt) * (c.nrhs / (cfg.nr * cfg.nw)));
     dim3 blk((unsigned)cfg.nt, (unsigned)cfg.nw);
     ++ctx->launches;

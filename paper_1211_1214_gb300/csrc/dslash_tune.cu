@@ -22,8 +22,8 @@ namespace ddrw {
 // right-hand sides per thread each hop code form supports
 static bool form_allowed(int nr, int roll)
 {
-    if (roll < 0 || roll > 7) return false;
-    if ((roll >= 2 && roll <= 4) || roll == 7) return nr == 1;
+    if (roll < 0 || roll > 8) return false;
+    if ((roll >= 2 && roll <= 4) || roll >= 7) return nr == 1;
     if (roll == 5 || roll == 6) return nr <= 2;
     return true;
 }
@@ -35,7 +35,7 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
     const int rpm = (c.nrhs + nm - 1) / nm;
     if (ctx->pinned_nr > 0) {
         DsConfig p{ctx->pinned_nr, ctx->pinned_nt, ctx->pinned_nw, ctx->pinned_roll};
-        if (c.nrhs % (p.nr * p.nw) || rpm % (p.nr * p.nw)) p.nr = 1, p.nw = 1;
+        if (p.roll != 8 && (c.nrhs % (p.nr * p.nw) || rpm % (p.nr * p.nw))) p.nr = 1, p.nw = 1;
         return p;
     }
     std::array<int, 8> key = {prec, bl, c.npar, c.nrhs, c.diag, c.post, rpm, c.beta != 0.0};
@@ -56,16 +56,21 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
     cudaEventCreate(&e1);
     DsConfig best = def;
     float best_ms = 1e30f;
-    const int nrs[3] = {1, 2, 4}, nts[3] = {64, 128, 256}, nws[2] = {1, 2};
-    for (int roll = 0; roll < 8; roll++)
+    const int nrs[3] = {1, 2, 4}, nts[3] = {64, 128, 256}, nws[2] = {1, 2}, nws8[4] = {1, 2, 4, 8};
+    for (int roll = 0; roll < 9; roll++)
     for (int nr : nrs) {
         // the batched and register-capped forms are for 32- and 16-bit storage: with FP64 data
-        // they spill
-        if (c.nrhs % nr || rpm % nr || (roll >= 2 && prec == 64) || !form_allowed(nr, roll))
+        // they spill; the staged form is for FP32 storage
+        if (c.nrhs % nr || rpm % nr || (roll >= 2 && prec == 64) || !form_allowed(nr, roll) ||
+            (roll == 8 && prec != 32))
             continue;
-        for (int nw : nws)
+        const int *nwl = roll == 8 ? nws8 : nws;
+        const int nnw = roll == 8 ? 4 : 2;
+        for (int iw = 0; iw < nnw; iw++)
         for (int nt : nts) {
-            if ((c.nrhs / nr) % nw || nt * nw > 256) continue;
+            const int nw = nwl[iw];
+            if (roll == 8 ? (nt > 128 || nw > rpm) : (c.nrhs / nr) % nw != 0) continue;
+            if (nt * nw > 256) continue;
             DsConfig cfg{nr, nt, nw, roll};
             run(ctx, c, cfg);  // warm
             cudaEventRecord(e0, ctx->stream);
@@ -109,12 +114,20 @@ ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll)
         return DDRW_OK;
     }
     if ((nr != 1 && nr != 2 && nr != 4) || nt < 32 || nt > 256 || nt % 32 || nw < 1 || nt * nw > 256 ||
-        !form_allowed(nr, roll))
+        !form_allowed(nr, roll) || (roll == 8 && nt > 128))
         return set_error(ctx, DDRW_EINVAL, "bad stencil configuration");
     ctx->pinned_nr = nr;
     ctx->pinned_nt = nt;
     ctx->pinned_nw = nw;
     ctx->pinned_roll = roll;
+    return DDRW_OK;
+}
+
+ddrw_status ddrw_test_stall_staging(ddrw_ctx *ctx, int enable)
+{
+    if (!ctx) return DDRW_EINVAL;
+    ctx->stall_tx = enable ? 16 : 0;
+    clear_graphs(ctx);  // captured launches hold the switch's value
     return DDRW_OK;
 }
 

@@ -390,7 +390,7 @@ static ddrw_status chunk_capture(ddrw_ctx *ctx, int nmass, const double *ma, con
     double hdm[MAXM];
     for (int k = 0; k < MAXM; k++) hdm[k] = k < m2s.n ? m1s.m[k < m1s.n ? k : 0] - m2s.m[k] : 0.0;
     DDRW_CUDA_CHECK(cudaMemcpyAsync(dm, hdm, sizeof(hdm), cudaMemcpyHostToDevice, ctx->stream));
-    DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    DDRW_SYNC(ctx);
 
     DDRW_CUDA_CHECK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeRelaxed));
     ctx->devctl = true;
@@ -852,7 +852,7 @@ ddrw_status ddrw_estimate_variant(ddrw_ctx *ctx, int variant, int N, int nhit, u
             const long n_range = variant == 0 ? V : ctx->vh;
             if ((st = Blas<PrecD>::norm_dot(ctx, VecRange{V, 0, n_range, 12 * V, jn}, F[1], F[0], nd))) return st;
             DDRW_CUDA_CHECK(cudaMemcpyAsync(h.data(), nd, sizeof(double) * 3 * jn, cudaMemcpyDeviceToHost, ctx->stream));
-            DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+            DDRW_SYNC(ctx);
             for (int j = 0; j < jn; j++) {
                 const double a = h[3 * j], b = h[3 * j + 1];
                 e[(size_t)i * nhit + j0 + j] = variant == 0 ? dm * dm * a + 2.0 * dm * b : a + 2.0 * b;

@@ -518,7 +518,7 @@ extern "C" ddrw_status ddrw_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64
             return st;
         std::vector<double> h(6 * nhit);
         DDRW_CUDA_CHECK(cudaMemcpyAsync(h.data(), red, sizeof(double) * 6 * nhit, cudaMemcpyDeviceToHost, ctx->stream));
-        DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        DDRW_SYNC(ctx);
         for (int j = 0; j < nhit; j++) dm2[j] = -2.0 * (h[3 * j + 1] + h[3 * nhit + 3 * j + 1]);
     }
     if (dU) {

@@ -54,6 +54,20 @@ __global__ void k_nbr_table(GeomDev g, int4 *t)
     t[g.V + s] = make_int4(e[4], e[5], e[6], e[7]);
 }
 
+// FP32 two-row U_mu(x - mu) copied to x, so that a tile of output sites finds all 8 of its links
+// in contiguous planes
+__global__ void k_bw_links(long V, const int4 *__restrict__ nbr, const float4 *__restrict__ U32, float4 *Ubw)
+{
+    long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    const int4 n0 = nbr[s], n1 = nbr[V + s];
+    const int b[4] = {n0.y & NBR_IDX, n0.w & NBR_IDX, n1.y & NBR_IDX, n1.w & NBR_IDX};
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) Ubw[(long)(mu * 3 + k) * V + s] = U32[(long)(mu * 3 + k) * V + b[mu]];
+}
+
 // ----------------------------------------------------------------------------- clover
 
 template <int BL> void clover_launch(ddrw_ctx *ctx);
@@ -201,6 +215,12 @@ void build_nbr_table(ddrw_ctx *ctx)
     g.tsign = -1;
     dim3 grid((unsigned)((ctx->V + 127) / 128));
     DISPATCH_BL(ctx, k_nbr_table, grid, 128, g, ctx->d_nbr);
+}
+
+void build_bw_links(ddrw_ctx *ctx)
+{
+    ++ctx->launches;
+    k_bw_links<<<(unsigned)((ctx->V + 127) / 128), 128, 0, ctx->stream>>>(ctx->V, ctx->d_nbr, ctx->U32, ctx->Ubw32);
 }
 
 void build_clover(ddrw_ctx *ctx)

@@ -175,7 +175,7 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
     for (int k = 0; k < check; k++, it++)
         if ((st = iteration())) return st;
     DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, sc, sizeof(KScal) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-    DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    DDRW_SYNC(ctx);
     {
         int active = 0;
         for (int k = 0; k < nrhs; k++) active += hs[k].active;
@@ -244,7 +244,7 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
         ++ctx->graph_launches;
         DDRW_CUDA_CHECK(cudaMemcpyAsync(&it, count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
         DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, sc, sizeof(KScal) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-        DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+        DDRW_SYNC(ctx);
         // kernels the graph ran: 9 per iteration (4 stencil sweeps, 5 vector kernels) and one
         // condition kernel per `check` iterations
         ctx->launches += (long)(it - it0) * 9 + (it - it0) / check;
@@ -253,7 +253,7 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
             for (int k = 0; k < check; k++, it++)
                 if ((st = iteration())) return st;
             DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, sc, sizeof(KScal) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-            DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+            DDRW_SYNC(ctx);
             int active = 0;
             for (int k = 0; k < nrhs; k++) active += hs[k].active;
             done = !active || it >= maxiter;
@@ -285,7 +285,7 @@ ddrw_status full_norms(ddrw_ctx *ctx, const double2 *f, int nrhs, std::vector<do
     if ((st = Blas<PrecD>::norm2(ctx, all, f, d))) return st;
     out.resize(nrhs);
     DDRW_CUDA_CHECK(cudaMemcpyAsync(out.data(), d, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-    DDRW_CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    DDRW_SYNC(ctx);
     return DDRW_OK;
 }
 

@@ -1,6 +1,7 @@
 """Failure detection without a GPU fault: every failure is made on the host (bad arguments,
-an iteration cap of 1, NaN in a host input buffer) and must come back as a status code with a
-message, leaving the context usable."""
+an iteration cap of 1, NaN in a host input buffer) or is a bounded device-side wait that a test
+switch lets run out, and must come back as a status code with a message, leaving the context
+usable."""
 import numpy as np
 import pytest
 
@@ -60,7 +61,8 @@ def test_bad_arguments(ctx):
     with pytest.raises(binding.DDRWError) as ei:
         c.estimate_interp(9, 2)  # at most 8 interpolation steps
     assert ei.value.status == 1
-    for cfg in [(2, 64, 1, 7), (4, 64, 1, 6), (2, 64, 1, 4), (1, 64, 1, 8), (1, 48, 1, 0), (1, 256, 2, 0)]:
+    for cfg in [(2, 64, 1, 7), (4, 64, 1, 6), (2, 64, 1, 4), (1, 64, 1, 9), (2, 64, 1, 8), (1, 256, 1, 8),
+                (1, 48, 1, 0), (1, 256, 2, 0)]:
         with pytest.raises(binding.DDRWError) as ei:
             c.stencil_config(*cfg)  # form, right-hand sides per thread or CTA shape out of range
         assert ei.value.status == 1
@@ -105,3 +107,26 @@ def test_eight_mass_slots_in_one_pass(ctx):
         e1, _, _, _ = c.estimate(2, seed=4)
         assert np.all(np.abs(e[k] - e1) <= 1e-8 * np.maximum(np.abs(e1), 1.0))
     c.set_params(1.5, 0.05, 0.045)
+
+
+def test_staged_stencil_wait_runs_out_and_the_context_recovers(ctx):
+    """The staged stencil's shared-memory barrier is told to expect 16 bytes that never arrive: every
+    CTA stops polling after its bounded number of tries, sets the device error flag and returns; the
+    call reports DDRW_ETIMEOUT, and with the switch off the same context computes the right result."""
+    c, dims = ctx
+    x = synth.spinor_field(dims, seed=85, nrhs=2)
+    y = np.zeros_like(x)
+    c.stencil_config(1, 64, 2, 8)
+    try:
+        c.test_stall_staging(True)
+        with pytest.raises(binding.DDRWError) as ei:
+            c.apply_D_low(binding.MIXED_FP32, 0.07, x, y, nrhs=2)
+        assert ei.value.status == 8
+        c.test_stall_staging(False)
+        c.apply_D_low(binding.MIXED_FP32, 0.07, x, y, nrhs=2)
+    finally:
+        c.test_stall_staging(False)
+        c.stencil_config(0)
+    ref = np.zeros_like(x)
+    c.apply_D(0.07, x, ref, nrhs=2)
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 2e-6

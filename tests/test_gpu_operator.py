@@ -89,6 +89,50 @@ def test_every_stencil_configuration(setup, nr, nt, nw, roll):
         assert rel(y[r], lat.apply(0.07, x[r])) < 1e-12
 
 
+# relative error bound of one storage-precision stencil launch against the FP64 oracle: the input,
+# links and clover terms are rounded to the storage (FP32 2^-24, FP16 with a per-site scale 2^-11,
+# BF16 2^-8 relative per component), the arithmetic is FP32; a wrong hop, link or clover term
+# gives errors of order 1e-1
+LOW_TOL = {binding.MIXED_FP32: 2e-6, binding.MIXED_FP16: 3e-3, binding.MIXED_BF16: 2e-2}
+
+
+def ainv_apply(lat, m, v):
+    """A(m)^-1 v site by site, A(m) = (4 + m) + C(x) from the oracle's clover matrices."""
+    out = np.empty_like(v)
+    for x in range(v.shape[0]):
+        out[x] = np.linalg.solve(lat.clover(x) + (4 + m) * np.eye(12), v[x].reshape(12)).reshape(4, 3)
+    return out
+
+
+@pytest.mark.parametrize("post", [False, True], ids=["D", "AinvD"])
+@pytest.mark.parametrize("prec,cfg", [(binding.MIXED_FP32, None), (binding.MIXED_FP32, (1, 64, 1, 5)),
+                                      (binding.MIXED_FP32, (2, 128, 1, 0)), (binding.MIXED_FP32, (1, 64, 1, 6)),
+                                      (binding.MIXED_FP32, (1, 64, 4, 8)), (binding.MIXED_FP32, (1, 128, 2, 8)),
+                                      (binding.MIXED_FP32, (1, 32, 8, 8)), (binding.MIXED_FP16, None),
+                                      (binding.MIXED_FP16, (1, 64, 1, 6)), (binding.MIXED_FP16, (1, 64, 4, 8)),
+                                      (binding.MIXED_BF16, None)],
+                         ids=["s-tuned", "s-f5", "s-u2", "s-table", "s-staged64x4", "s-staged128x2",
+                              "s-staged32x8", "h-tuned", "h-table", "h-staged-falls-back", "b-tuned"])
+def test_apply_D_in_storage_precision(setup, prec, cfg, post):
+    """One stencil launch in FP32 / FP16 / BF16 storage, in each launch form (computed or tabulated
+    neighbours, links and clover terms staged in shared memory by bulk copies), against the oracle's
+    D(m) and A(m)^-1 D(m) on 3 right-hand sides (fewer than some forms' right-hand-side rows)."""
+    ctx, lat, dims = setup
+    x = synth.spinor_field(dims, seed=11, nrhs=3)
+    y = np.zeros_like(x)
+    if cfg:
+        ctx.stencil_config(*cfg)
+    try:
+        ctx.apply_D_low(prec, 0.07, x, y, nrhs=3, post=post)
+    finally:
+        ctx.stencil_config(0)
+    for r in range(3):
+        ref = lat.apply(0.07, x[r])
+        if post:
+            ref = ainv_apply(lat, 0.07, ref)
+        assert rel(y[r], ref) < LOW_TOL[prec], (r, rel(y[r], ref))
+
+
 @pytest.mark.parametrize("rows,cols", [(0, 0), (1, 1), (0, 1), (1, 0), (2, 0), (1, 2)])
 def test_apply_block(setup, rows, cols):
     ctx, lat, dims = setup
