@@ -454,7 +454,7 @@ def main():
                 "measured_on": "one extra step of the same workload with the Krylov-loop graphs off "
                                f"({ms_prof:.0f} ms), every stencil launch timed by CUDA events",
                 "step_breakdown": shares}
-    # the same launches against the FP32 ALU roof: SURVEY-style flop count of the Wilson-clover
+    # the same launches against the FP32 ALU roof: the conventional flop count of the Wilson-clover
     # site update (1320 hopping + 504 clover + 48 diagonal per site and right-hand side)
     if kms > 0 and prec != binding.FP64:
         tflops = FLOPS_PER_SITE_UPDATE * kunits / (kms / 1e3) / 1e12
