@@ -68,6 +68,7 @@ def aggregate_rate(world: int, units_per_rank_step: int, steps: int, t_max_ms: f
     return world * units_per_rank_step * steps / (t_max_ms / 1e3)
 
 
+GRAPH_MODE = 2  # ddrw_use_graphs mode of the timed steps (--graph-mode)
 FLOPS_PER_SITE_UPDATE = 1872.0  # hopping 1320 + clover 504 + diagonal 48 flops per site and right-hand side
 FP32_FMA_TFLOPS = 70.06  # measured FP32 FMA throughput of one GB300 (profiles/alu_peaks_gb300.md)
 
@@ -92,7 +93,7 @@ def stencil_one_rhs(ctx, w, prec, key, hbm, tol_block):
             pass  # the iteration cap ends the solve; the launches are what is measured
     n, ms, by = ctx.profile_read(key)
     ctx.profile(False)
-    ctx.use_graphs(True)
+    ctx.use_graphs(GRAPH_MODE)
     ctx.set_solver(prec, tol_outer=1e-10, tol_block=tol_block)
     del b, x
     torch.cuda.empty_cache()
@@ -324,6 +325,8 @@ def main():
     ap.add_argument("--workload", choices=list(WORKLOADS), default="64x32^3")
     ap.add_argument("--prec", choices=["mixed32", "mixed16", "mixedbf16", "fp64"], default="mixed32")
     ap.add_argument("--fp64-hits", type=int, default=2, help="noise vectors of the FP64-path comparison (0: skip)")
+    ap.add_argument("--graph-mode", type=int, choices=[0, 1, 2], default=2,
+                    help="1: Krylov-loop graphs and whole estimate chunks as one graph; 2: Krylov-loop graphs only; 0: none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fig1", action="store_true",
@@ -331,6 +334,8 @@ def main():
     ap.add_argument("--stencil-config", default=None,
                     help="pin the stencil launch form nr,nt,nw,roll (ddrw_stencil_config) instead of autotuning")
     args = ap.parse_args()
+    global GRAPH_MODE
+    GRAPH_MODE = args.graph_mode
     w = WORKLOADS[args.workload]
     name = args.workload
 
@@ -370,6 +375,7 @@ def main():
                   binding.MIXED_BF16: "BF16-storage/FP32-arithmetic", binding.FP64: "FP64"}[prec]
     tol_block = 1e-10 if prec != binding.FP64 else 1e-13
     ctx.set_solver(prec, tol_outer=1e-10, tol_block=tol_block)
+    ctx.use_graphs(GRAPH_MODE)
     if args.stencil_config:
         ctx.stencil_config(*[int(v) for v in args.stencil_config.split(",")])
     nhit, m2s = w["nhit"], list(w["m2s"])
@@ -434,7 +440,7 @@ def main():
             shares[cls] = {"launches": n_, "ms": round(t_, 2), "share": round(t_ / ms_prof, 4)}
     kunits = ctx.profile_units(key)
     ctx.profile(False)
-    ctx.use_graphs(True)
+    ctx.use_graphs(GRAPH_MODE)
     t_max = max_over_ranks(ms, dist, dev)
     value = aggregate_rate(world, per_step, args.steps, t_max)
 
@@ -473,7 +479,9 @@ def main():
                       "lattice": list(w["dims"]), "block": w["l"], "nhit": nhit, "m1": w["m1"], "m2": m2s,
                       "estimates_per_step": per_step, "tol_outer": 1e-10, "tol_block": tol_block,
                       "l2": "inputs larger than L2 (gauge, clover and fields are GBs)",
-                      "parallelism": f"replicas x{world} (disjoint noise vectors)"},
+                      "parallelism": f"replicas x{world} (disjoint noise vectors)",
+                      "graphs": {0: "none", 1: "Krylov loops + whole estimate chunks",
+                                 2: "Krylov loops only"}[GRAPH_MODE]},
            "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
            "solver": {"outer_iters": infos[-1]["iters_outer"], "cycles": infos[-1]["cycles"],
                       "fp64_dslash_calls": infos[-1]["fp64_dslash_calls"],

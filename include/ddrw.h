@@ -234,10 +234,17 @@ ddrw_status ddrw_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64_t hit_offs
 ddrw_status ddrw_solve_block_noalloc(ddrw_ctx *ctx, int colour, double m, const double *b, double *x,
                                      ddrw_solve_info *info);
 
-/* CUDA graphs of the outer Krylov loop (default on): after its first iterations the loop runs as
- * one graph with a conditional while-node (device-side convergence test, iteration cap).
- * enable = 1 / 0 switches them, -1 leaves the setting; *graph_launches (optional) receives the
- * number of graph launches so far.  Block solves are single persistent launches either way. */
+/* CUDA graphs (default mode 2).  Mode 2: the outer Krylov loop, after its first iterations, runs as
+ * one graph with a conditional while-node (device-side convergence test, iteration cap); the
+ * defect-correction cycles around it are host-driven.  Mode 1: the same, and in addition an
+ * estimate chunk with library-drawn noise is, from the second call with the same lattice, solver
+ * settings, masses and number of hits, captured whole into one graph and replayed: noise, block
+ * solves, outer solves and their defect-correction cycles, whose continue decisions and inner
+ * tolerances are taken by condition kernels on the device (nested conditional while-nodes, every
+ * loop capped); measured on one GB300 it is as fast as mode 2 on 16^4 and 32x16^3 and 0.6 % slower
+ * on 64x32^3.  Mode 0: no graphs.  -1 leaves the setting; *graph_launches (optional) receives the
+ * number of graph launches so far.  Results are bitwise the same in every mode.  Block solves are
+ * single persistent launches. */
 ddrw_status ddrw_use_graphs(ddrw_ctx *ctx, int enable, long *graph_launches);
 
 /* Autotuner of the stencil launches: on the first launch of each shape (precision, block length,

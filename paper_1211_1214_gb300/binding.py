@@ -259,7 +259,8 @@ class Context:
         return e, dm, info.as_dict()
 
     def use_graphs(self, enable=None):
-        """Switch CUDA graphs of the outer Krylov loop (None: keep); returns graph launches so far."""
+        """Graph mode (2, the default: Krylov loops; True / 1: Krylov loops and whole estimate chunks
+        with device-controlled cycles; False / 0: none; None: keep); returns graph launches so far."""
         n = ctypes.c_long()
         self._check(self.L.ddrw_use_graphs(self._h, -1 if enable is None else int(enable), ctypes.byref(n)),
                     "ddrw_use_graphs")

@@ -428,7 +428,11 @@ ddrw_status ddrw_profile(ddrw_ctx *ctx, int enable)
 ddrw_status ddrw_use_graphs(ddrw_ctx *ctx, int enable, long *graph_launches)
 {
     if (!ctx) return DDRW_EINVAL;
-    if (enable >= 0) ctx->use_graphs = enable != 0;
+    if (enable > 2) return set_error(ctx, DDRW_EINVAL, "graph mode must be 0, 1 or 2");
+    if (enable >= 0) {
+        ctx->use_graphs = enable != 0;
+        ctx->use_est_graphs = enable == 1;  // captured graphs are kept for when the mode returns
+    }
     if (graph_launches) *graph_launches = ctx->graph_launches;
     return DDRW_OK;
 }

@@ -137,7 +137,8 @@ struct ddrw_ctx {
     size_t h_pinned_bytes = 0;
 
     // CUDA graphs of the outer Krylov loop, by launch shape and buffers
-    bool use_graphs = true;
+    bool use_graphs = true;       // Krylov-loop graphs
+    bool use_est_graphs = false;  // whole estimate chunks as one graph (mode 1; needs use_graphs)
     long graph_launches = 0;
     std::map<std::array<uintptr_t, 13 + 2 * ddrw::MAXM>, ddrw::GraphEntry> graphs;
     // whole-estimate graphs (estimate.cu): captured on the second call of a shape, replayed after

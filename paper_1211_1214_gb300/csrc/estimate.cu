@@ -489,7 +489,7 @@ static ddrw_status estimate_chunk(ddrw_ctx *ctx, int nmass, const double *ma, co
     double2 *F[5];
     if ((st = fields(ctx, "est_f", 5, nrhs, F))) return st;
     // the whole chunk as a graph: captured on the second call of this shape, replayed later
-    const bool graphable = ctx->use_graphs && !eta_user && !delta_user && !ctx->devctl;
+    const bool graphable = ctx->use_graphs && ctx->use_est_graphs && !eta_user && !delta_user && !ctx->devctl;
     EstKey key{};
     if (graphable) {
         key = est_key(ctx, nmass, ma, m2, nhit, distinct_noise);

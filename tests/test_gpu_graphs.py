@@ -1,5 +1,5 @@
-"""CUDA graphs of the outer Krylov loop and the stencil autotuner: same results with and without
-them, and the graph path is actually taken."""
+"""CUDA graphs (the outer Krylov loop; whole estimate chunks with device-controlled cycles) and the
+stencil autotuner: same results with and without them, and the graph path is actually taken."""
 import numpy as np
 import pytest
 
@@ -36,7 +36,7 @@ def test_graph_and_eager_krylov_loops_agree(ctx, prec):
         if graphs:
             assert c.use_graphs() > n0  # the loop ran as a graph
     assert np.array_equal(xs[0], xs[1])
-    c.use_graphs(True)
+    c.use_graphs(2)  # the default mode
 
 
 def test_estimate_same_with_graphs_and_without(ctx):
@@ -44,7 +44,7 @@ def test_estimate_same_with_graphs_and_without(ctx):
     c.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-12)
     c.use_graphs(False)
     e0, lw0, _, _ = c.estimate(4, seed=3)
-    c.use_graphs(True)
+    c.use_graphs(2)
     e1, lw1, _, _ = c.estimate(4, seed=3)
     assert np.array_equal(e0, e1)
 
@@ -74,15 +74,39 @@ def test_whole_estimate_graph_replays_the_eager_estimate(ctx, prec):
     m2s = [0.045, 0.04]
     c.use_graphs(False)
     ref = [c.estimate_masses(m2s, 3, seed=s)[0] for s in (11, 12, 13)]
-    c.use_graphs(True)
+    c.use_graphs(1)
     n0 = c.use_graphs()
     c.profile(True)
-    got = [c.estimate_masses(m2s, 3, seed=s) for s in (11, 12, 13)]  # eager, capture + replay, replay
-    launches = c.profile_read(binding.PROF_LAUNCHES)[0]
-    c.profile(False)
-    assert c.use_graphs() >= n0 + 2  # two replays of the whole estimate (plus Krylov-loop graphs)
+    try:
+        got = [c.estimate_masses(m2s, 3, seed=s) for s in (11, 12, 13)]  # eager, capture + replay, replay
+        launches = c.profile_read(binding.PROF_LAUNCHES)[0]
+    finally:
+        c.profile(False)
+        n1 = c.use_graphs(2)
+    assert n1 >= n0 + 2  # two replays of the whole estimate (plus Krylov-loop graphs)
     for (e, lw, rv, info), e_ref in zip(got, ref):
         assert np.array_equal(np.asarray(e), np.asarray(e_ref))
         assert info["true_rel_residual"] <= 1e-10
     assert not np.array_equal(np.asarray(got[1][0]), np.asarray(got[2][0]))  # new noise per replay
     assert launches > 1000
+
+
+def test_krylov_only_graph_mode_gives_the_same_estimate_without_whole_chunk_graphs(ctx):
+    """Mode 2 (Krylov-loop graphs, host-driven cycles) gives the eager numbers bitwise on repeated
+    calls; an unknown mode is refused."""
+    c, dims = ctx
+    m2s = [0.045, 0.04]
+    c.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-10)
+    try:
+        c.use_graphs(False)
+        ref = c.estimate_masses(m2s, 3, seed=21)[0]
+        c.use_graphs(2)
+        got = [c.estimate_masses(m2s, 3, seed=21)[0] for _ in range(3)]
+    finally:
+        c.use_graphs(2)
+        c.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+    for e in got:
+        assert np.array_equal(np.asarray(e), np.asarray(ref))
+    with pytest.raises(binding.DDRWError) as ei:
+        c.use_graphs(3)
+    assert ei.value.status == 1
