@@ -267,7 +267,8 @@ ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
  * other storage precisions run form 5 instead); roll 2-4, 7 and 8 need nr = 1, roll 5 and 6
  * nr <= 2.
  * A launch whose right-hand sides per mass slot are not a multiple of nr * nw runs with nr = nw = 1.
- * nr = 0 returns to autotuning.  DDRW_EINVAL for values outside these ranges. */
+ * nr = 0 returns to autotuning.  DDRW_EINVAL for values outside these ranges.  A change drops the
+ * captured CUDA graphs (they are captured again with the new form on next use). */
 ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll);
 
 /* Test switch of the staged stencil's bounded wait (form 8): with enable != 0 every staged launch

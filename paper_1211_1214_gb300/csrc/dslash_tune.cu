@@ -103,6 +103,7 @@ ddrw_status ddrw_autotune(ddrw_ctx *ctx, int enable)
     if (!ctx) return DDRW_EINVAL;
     ctx->autotune = enable != 0;
     ctx->tune.clear();
+    clear_graphs(ctx);  // captured launches keep the form they were captured with
     return DDRW_OK;
 }
 
@@ -110,12 +111,15 @@ ddrw_status ddrw_stencil_config(ddrw_ctx *ctx, int nr, int nt, int nw, int roll)
 {
     if (!ctx) return DDRW_EINVAL;
     if (nr == 0) {
+        if (ctx->pinned_nr) clear_graphs(ctx);  // captured launches keep the form they were captured with
         ctx->pinned_nr = 0;
         return DDRW_OK;
     }
     if ((nr != 1 && nr != 2 && nr != 4) || nt < 32 || nt > 256 || nt % 32 || nw < 1 || nt * nw > 256 ||
         !form_allowed(nr, roll) || (roll == 8 && nt > 128))
         return set_error(ctx, DDRW_EINVAL, "bad stencil configuration");
+    if (ctx->pinned_nr != nr || ctx->pinned_nt != nt || ctx->pinned_nw != nw || ctx->pinned_roll != roll)
+        clear_graphs(ctx);
     ctx->pinned_nr = nr;
     ctx->pinned_nt = nt;
     ctx->pinned_nw = nw;
