@@ -331,6 +331,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fig1", action="store_true",
                     help="run the synthetic Fig. 1 analogue (variance vs interpolation steps per operator) instead")
+    ap.add_argument("--outer-solver", choices=["sap", "bicgstab"], default="sap",
+                    help="Krylov method of the FP32 inner solves: Schwarz-preconditioned GCR or even-odd BiCGStab")
+    ap.add_argument("--sap", default=None, help="ncy,nmr,nkv of the Schwarz-preconditioned GCR")
     ap.add_argument("--stencil-config", default=None,
                     help="pin the stencil launch form nr,nt,nw,roll (ddrw_stencil_config) instead of autotuning")
     args = ap.parse_args()
@@ -376,6 +379,8 @@ def main():
     tol_block = 1e-10 if prec != binding.FP64 else 1e-13
     ctx.set_solver(prec, tol_outer=1e-10, tol_block=tol_block)
     ctx.use_graphs(GRAPH_MODE)
+    sap = [int(v) for v in args.sap.split(",")] if args.sap else [4, 4, 8]
+    ctx.set_outer_solver(1 if args.outer_solver == "sap" else 0, *sap)
     if args.stencil_config:
         ctx.stencil_config(*[int(v) for v in args.stencil_config.split(",")])
     nhit, m2s = w["nhit"], list(w["m2s"])
@@ -434,7 +439,7 @@ def main():
                        ("block_solver_fp32", binding.PROF_BLOCK32), ("block_solver_fp64", binding.PROF_BLOCK64),
                        ("krylov_vectors", binding.PROF_BLAS), ("residual_stencil_ds", binding.PROF_DSLASH_DS),
                        ("stencil_16bit", binding.PROF_DSLASH16), ("stencil_16bit_blocks", binding.PROF_DSLASH16_BLK),
-                       ("block_solver_16bit", binding.PROF_BLOCK16)):
+                       ("block_solver_16bit", binding.PROF_BLOCK16), ("schwarz_preconditioner", binding.PROF_SAP)):
         n_, t_, _ = ctx.profile_read(kind)
         if n_:
             shares[cls] = {"launches": n_, "ms": round(t_, 2), "share": round(t_ / ms_prof, 4)}
@@ -483,7 +488,11 @@ def main():
                       "graphs": {0: "none", 1: "Krylov loops + whole estimate chunks",
                                  2: "Krylov loops only"}[GRAPH_MODE]},
            "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
-           "solver": {"outer_iters": infos[-1]["iters_outer"], "cycles": infos[-1]["cycles"],
+           "solver": {"outer_method": ("Schwarz-preconditioned flexible GCR (ncy, nmr, nkv = %d, %d, %d)" % tuple(sap)
+                                       if args.outer_solver == "sap" and prec == binding.MIXED_FP32
+                                       else "even-odd BiCGStab"),
+                      "outer_iters": infos[-1]["iters_outer"], "iters_inner_total": infos[-1]["iters_inner_total"],
+                      "cycles": infos[-1]["cycles"],
                       "fp64_dslash_calls": infos[-1]["fp64_dslash_calls"],
                       "block_iters_max": infos[-1]["block_iters_max"],
                       "true_rel_residual": infos[-1]["true_rel_residual"]},

@@ -72,6 +72,9 @@ typedef enum { DDRW_BLACK = 0, DDRW_WHITE = 1, DDRW_ALL = 2 } ddrw_colour;
 
 typedef struct {
     int iters_outer;          /* outer Krylov iterations (summed over defect-correction cycles) */
+    int iters_inner_total;    /* inner iterations: the in-block iterations of every block-solver
+                                 launch (the largest over the blocks of the launch), summed over
+                                 launches and defect-correction cycles */
     int cycles;               /* defect-correction cycles (1 for the FP64 path) */
     int fp64_dslash_calls;    /* full-lattice FP64 operator applications */
     int block_iters_max;      /* largest iteration count of any block solve */
@@ -106,6 +109,24 @@ ddrw_status ddrw_set_params(ddrw_ctx *ctx, double csw, double m1, double m2, int
  * 1e-13), and the iteration cap of every solver (default 20000). */
 ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, double tol_block, int maxiter);
 
+/* Krylov method of the full-lattice solves D(m) x = b whose inner solves run on FP32 fields
+ * (DDRW_MIXED_FP32): method 0 is even-odd BiCGStab; method 1 (the default) is flexible GCR
+ * preconditioned by the Schwarz alternating procedure on the domain decomposition of Sec. 1 --
+ * Schwarz blocks of side 4 coloured black/white, ncy cycles over both colours, each block solved
+ * approximately by nmr minimal-residual steps on its even-odd reduced operator with Dirichlet
+ * boundary conditions, nkv search directions kept between restarts (defaults 4, 4, 8).  Method 1
+ * needs every lattice dimension to be a multiple of 8 (else BiCGStab runs); the FP64 path, the
+ * 16-bit storage precisions and whole-estimate graphs (ddrw_use_graphs mode 1) always use
+ * BiCGStab.  Both reach the same FP64 true residual through the defect correction.
+ * DDRW_EINVAL outside method 0..1, ncy 1..16, nmr 1..32, nkv 1..16. */
+ddrw_status ddrw_set_outer_solver(ddrw_ctx *ctx, int method, int ncy, int nmr, int nkv);
+
+/* out = M_SAP(m) in: one application of the Schwarz preconditioner of method 1 above (the
+ * context's ncy and nmr) to nrhs full-lattice fields, evaluated on FP32 fields and widened to
+ * FP64 (layouts as ddrw_apply_D).  With ncy = 1 and enough steps it is one block Gauss-Seidel
+ * sweep over the black, then the white Schwarz blocks; for testing the preconditioner. */
+ddrw_status ddrw_apply_sap(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs);
+
 /* out = D(m) in for nrhs full-lattice spinor fields, in FP64. */
 ddrw_status ddrw_apply_D(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs);
 
@@ -137,8 +158,10 @@ ddrw_status ddrw_solve_block(ddrw_ctx *ctx, int colour, double m, const double *
 /* x = D(m)^-1 b for full-lattice fields, to the outer tolerance. */
 ddrw_status ddrw_solve_D(ddrw_ctx *ctx, double m, const double *b, double *x, int nrhs, ddrw_solve_info *info);
 
-/* out = A(m) in with A(m) = P Dhat(m) P (Sec. 1), on packed supp-P vectors. */
-ddrw_status ddrw_apply_schur(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs);
+/* out = A(m) in with A(m) = P Dhat(m) P (Sec. 1), on packed supp-P vectors; with dagger != 0
+ * out = A(m)^dag in = in - P g5 D_bw D_ww^-1 D_wb D_bb^-1 g5 in, from D^dag = g5 D g5 applied to the
+ * blocks of Eq. 1 ((D_XY)^dag = g5 D_YX g5).  Block solves to tol_block in the context's precision. */
+ddrw_status ddrw_apply_schur(ddrw_ctx *ctx, double m, int dagger, const double *in, double *out, int nrhs);
 
 /* r = (A(m1) - A(m2)) eta on packed supp-P vectors, in the resolvent form
  * r = dm P D_bb(m1)^-1 [D_bw a12 + D_bb(m2)^-1 D_bw a2], u = D_wb eta, a2 = D_ww(m2)^-1 u,
@@ -216,18 +239,20 @@ ddrw_status ddrw_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64_t hit_offs
 
 /* ddrw_solve_block for callers that cannot allocate device memory.  The paper has no counterpart:
  * this is an integration aid.  Some callers may not call cudaMalloc -- code running while a
- * framework's memory pool is frozen or a graph is being built, or a host application that owns
- * every device allocation -- and ddrw_solve_block grows its workspace with cudaMalloc.  This call
- * allocates nothing: its scratch (about 40 MB: ten FP64 fields of up to 20736 sites plus reduction
- * slots) is one fixed array in device memory that every GPU using the library holds until the
- * process exits.
+ * framework's memory pool is frozen, or a host application that owns every device allocation and
+ * forbids libraries their own -- and ddrw_solve_block grows its workspace with cudaMalloc.  This
+ * call allocates nothing: its scratch (about 40 MB: ten FP64 fields of up to 20736 sites plus
+ * reduction slots) is one fixed array in device memory that every GPU using the library holds
+ * until the process exits.
  *   - One right-hand side, FP64 (whatever ddrw_set_solver chose), tolerance tol_block, same
  *     result as ddrw_solve_block: x = D_cc(m)^-1 b on colour c, x zero on the other colour.
  *   - Lattices of at most 20736 sites (12^4); larger ones return DDRW_EINVAL with a message.
  *   - b and x must be device pointers (boundary layout); host pointers return DDRW_EINVAL.
- *   - m must be m1 or m2 of the last ddrw_set_params (their inverses already exist).
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
- *     that first call before any stream capture.
+ *   - m must be m1 or m2 of the last ddrw_set_params (their inverses already exist); other
+ *     masses return DDRW_EINVAL.  A non-finite b returns DDRW_ENUMERIC.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress) with the context's
+ *     device current.  The call synchronises its stream and reads scalars back to the host, so it
+ *     must not be made while the context's stream is being captured: it then returns DDRW_ESTATE.
  *   - All calls share the array and it keeps the last call's contents; calls that overlap on the
  *     GPU (other streams or contexts on the same device) race on it, so serialise them.
  *   - With kernel timing (ddrw_profile) on, the timing events are created on first use. */
@@ -304,8 +329,9 @@ ddrw_status ddrw_block_factor(ddrw_ctx *ctx, double *log_w_blk);
  * 2 / 3 FP64 / FP32 stencil restricted to hops inside or between blocks, 4 / 5 FP64 / FP32
  * persistent block solver (bytes not counted), 6 Krylov vector kernels and reductions (bytes not
  * counted), 7 double-single residual stencil, 8 and 9 the stencil on 16-bit storage (all hops /
- * block-restricted), 10 the persistent block solver on 16-bit storage (bytes not counted); class 11
- * returns in *launches the number of kernel launches of every kind since the last reset.  ddrw_profile(ctx, enable) resets the counters. */
+ * block-restricted), 10 the persistent block solver on 16-bit storage (bytes not counted), 11 the
+ * Schwarz-preconditioner sweeps of the GCR outer solver (bytes not counted); class 12 returns in
+ * *launches the number of kernel launches of every kind since the last reset.  ddrw_profile(ctx, enable) resets the counters. */
 ddrw_status ddrw_profile(ddrw_ctx *ctx, int enable);
 ddrw_status ddrw_profile_read(ddrw_ctx *ctx, int kind, long *launches, double *ms, double *bytes);
 

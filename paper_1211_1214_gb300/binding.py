@@ -22,7 +22,7 @@ _STATUS = {0: "DDRW_OK", 1: "DDRW_EINVAL", 2: "DDRW_ENOMEM", 3: "DDRW_ECUDA", 4:
 
 #: every entry point declared in include/ddrw.h
 EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", "ddrw_volume", "ddrw_load_gauge",
-           "ddrw_set_params", "ddrw_set_solver", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
+           "ddrw_set_params", "ddrw_set_solver", "ddrw_set_outer_solver", "ddrw_apply_sap", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
            "ddrw_autotune", "ddrw_autotune_report", "ddrw_stencil_config", "ddrw_profile_units",
@@ -31,7 +31,7 @@ EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", 
 
 #: kernel classes of ddrw_profile_read
 PROF_DSLASH64, PROF_DSLASH32, PROF_DSLASH64_BLK, PROF_DSLASH32_BLK, PROF_BLOCK64, PROF_BLOCK32, PROF_BLAS, PROF_DSLASH_DS, \
-    PROF_DSLASH16, PROF_DSLASH16_BLK, PROF_BLOCK16, PROF_LAUNCHES = range(12)
+    PROF_DSLASH16, PROF_DSLASH16_BLK, PROF_BLOCK16, PROF_SAP, PROF_LAUNCHES = range(13)
 
 
 class DDRWError(RuntimeError):
@@ -41,7 +41,8 @@ class DDRWError(RuntimeError):
 
 
 class SolveInfo(ctypes.Structure):
-    _fields_ = [("iters_outer", ctypes.c_int), ("cycles", ctypes.c_int), ("fp64_dslash_calls", ctypes.c_int),
+    _fields_ = [("iters_outer", ctypes.c_int), ("iters_inner_total", ctypes.c_int), ("cycles", ctypes.c_int),
+                ("fp64_dslash_calls", ctypes.c_int),
                 ("block_iters_max", ctypes.c_int), ("true_rel_residual", ctypes.c_double),
                 ("seconds", ctypes.c_double)]
 
@@ -76,13 +77,15 @@ def load(path: str | None = None):
         "ddrw_load_gauge": (st, [vp, dp]),
         "ddrw_set_params": (st, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
         "ddrw_set_solver": (st, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+        "ddrw_set_outer_solver": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "ddrw_apply_sap": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_apply_D": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_apply_D_ds": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_apply_D_low": (st, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, ctypes.c_int]),
         "ddrw_apply_block": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_solve_block": (st, [vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
         "ddrw_solve_D": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
-        "ddrw_apply_schur": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
+        "ddrw_apply_schur": (st, [vp, ctypes.c_double, ctypes.c_int, dp, dp, ctypes.c_int]),
         "ddrw_apply_dA": (st, [vp, dp, dp, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
         "ddrw_solve_schur": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int, ctypes.POINTER(SolveInfo)]),
         "ddrw_noise": (st, [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, dp]),
@@ -183,6 +186,14 @@ class Context:
         self._check(self.L.ddrw_set_solver(self._h, int(prec), float(tol_outer), float(tol_block), int(maxiter)),
                     "ddrw_set_solver")
 
+    def set_outer_solver(self, method=1, ncy=4, nmr=4, nkv=8):
+        """Krylov method of the FP32 inner solves: 0 even-odd BiCGStab, 1 Schwarz-preconditioned GCR."""
+        self._check(self.L.ddrw_set_outer_solver(self._h, int(method), int(ncy), int(nmr), int(nkv)),
+                    "ddrw_set_outer_solver")
+
+    def apply_sap(self, m, x, out, nrhs=1):
+        self._check(self.L.ddrw_apply_sap(self._h, float(m), _ptr(x), _ptr(out), int(nrhs)), "ddrw_apply_sap")
+
     def apply_D(self, m, x, out, nrhs=1):
         self._check(self.L.ddrw_apply_D(self._h, float(m), _ptr(x), _ptr(out), int(nrhs)), "ddrw_apply_D")
 
@@ -217,8 +228,9 @@ class Context:
         self._check(st, "ddrw_solve_D")
         return info.as_dict()
 
-    def apply_schur(self, m, x, out, nrhs=1):
-        self._check(self.L.ddrw_apply_schur(self._h, float(m), _ptr(x), _ptr(out), int(nrhs)), "ddrw_apply_schur")
+    def apply_schur(self, m, x, out, nrhs=1, dagger=False):
+        self._check(self.L.ddrw_apply_schur(self._h, float(m), int(bool(dagger)), _ptr(x), _ptr(out), int(nrhs)),
+                    "ddrw_apply_schur")
 
     def apply_dA(self, eta, r, nrhs=1):
         info = SolveInfo()

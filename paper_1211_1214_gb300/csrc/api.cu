@@ -710,6 +710,18 @@ ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, dou
     return DDRW_OK;
 }
 
+ddrw_status ddrw_set_outer_solver(ddrw_ctx *ctx, int method, int ncy, int nmr, int nkv)
+{
+    if (!ctx) return DDRW_EINVAL;
+    if (method < 0 || method > 1 || ncy < 1 || ncy > 16 || nmr < 1 || nmr > 32 || nkv < 1 || nkv > 16)
+        return set_error(ctx, DDRW_EINVAL, "bad outer solver setting");
+    ctx->outer_method = method;
+    ctx->sap_ncy = ncy;
+    ctx->sap_nmr = nmr;
+    ctx->sap_nkv = nkv;
+    return DDRW_OK;
+}
+
 ddrw_status ddrw_apply_block(ddrw_ctx *ctx, int rows, int cols, double m, const double *in, double *out, int nrhs)
 {
     if (!ctx || !in || !out || nrhs <= 0) return set_error(ctx, DDRW_EINVAL, "bad argument");

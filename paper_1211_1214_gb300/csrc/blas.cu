@@ -18,73 +18,6 @@ template <class P> struct VecArgs {
     long V, off, n, rs;  // plane stride, first site, sites, rhs stride (elements)
 };
 
-// ----------------------------------------------------------------------------- reductions
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sum v[0..K) over the grid's CTAs for right-hand side blockIdx.y.  Returns true in thread 0 of the
-// last CTA, with the totals in v.  part: [nrhs][gridDim.x][K] doubles, ticket: [nrhs] zeroed.
-template <int K, int NT>
-__device__ bool grid_sum(double (&v)[K], double *part, unsigned *ticket)
-{
-    __shared__ double sm[NT / 32][K];
-    __shared__ bool last;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; k++) v[k] = warp_sum(v[k]);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; k++) sm[w][k] = v[k];
-    __syncthreads();
-    const int r = blockIdx.y, G = gridDim.x;
-    if (threadIdx.x == 0) {
-        double *pp = part + ((long)r * G + blockIdx.x) * K;
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            double s = 0;
-            for (int i = 0; i < NT / 32; i++) s += sm[i][k];
-            pp[k] = s;
-        }
-        __threadfence();
-        unsigned t = atomicAdd(ticket + r, 1u);
-        last = (t == (unsigned)(G - 1));
-    }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    double acc[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) acc[k] = 0;
-    for (int i = threadIdx.x; i < G; i += NT) {
-        const double *pp = part + ((long)r * G + i) * K;
-#pragma unroll
-        for (int k = 0; k < K; k++) acc[k] += __ldcg(pp + k);
-    }
-#pragma unroll
-    for (int k = 0; k < K; k++) acc[k] = warp_sum(acc[k]);
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; k++) sm[w][k] = acc[k];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            double s = 0;
-            for (int i = 0; i < NT / 32; i++) s += sm[i][k];
-            v[k] = s;
-        }
-        ticket[r] = 0;
-        return true;
-    }
-    return false;
-}
-
 constexpr int NT = 256;
 
 // ----------------------------------------------------------------------------- BiCGStab steps

@@ -153,6 +153,7 @@ __global__ void k_blk_ctl(int mode, int nrhs, const double *bb2, const double *r
         dc->block_cycles += 1;
         dc->fp64_dslash_half += 1;
         dc->block_iters_max = max(dc->block_iters_max, stat[0]);
+        dc->block_iters_total += stat[0];
         double worst = 0.0;
         bool nan = false;
         for (int r = 0; r < nrhs; r++) {
@@ -371,6 +372,7 @@ ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const do
         if ((st = colour_norms(ctx, colour, res64, nrhs, rr))) return st;
         if (stats) {
             stats->block_iters_max = std::max(stats->block_iters_max, hstat[0]);
+            stats->block_iters_total += hstat[0];
             stats->block_cycles += 1;
         }
         double worst = 0;

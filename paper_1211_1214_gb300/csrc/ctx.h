@@ -48,6 +48,7 @@ struct GraphEntry {
 constexpr int DC_LOOPS = 32;
 struct DcStats {
     int block_iters_max, block_cycles, outer_iters, outer_cycles;
+    long block_iters_total;
     int fp64_dslash_half, fp64_dslash_full;
     int nan, noconv;
     double block_rel_residual, outer_rel_residual;
@@ -80,6 +81,7 @@ struct MassSet {
 struct SolveStats {
     int block_iters_max = 0;     // largest in-kernel iteration count of any block solve
     int block_cycles = 0;        // block defect-correction cycles
+    long block_iters_total = 0;  // in-kernel iterations summed over block-solver launches (max over blocks each)
     double block_rel_residual = 0;
     int fp64_dslash_half = 0;    // FP64 stencil sweeps over half the lattice (one colour)
     int outer_iters = 0;         // outer Krylov iterations, summed over cycles
@@ -117,6 +119,12 @@ struct ddrw_ctx {
     double tol_outer = 1e-10, tol_block = 1e-13;
     int maxiter = 20000;
     int max_rhs = 0;  // right-hand sides per chunk of a batched estimate (0: from free memory)
+    // outer Krylov method of the mixed-precision full-lattice solves: 0 even-odd BiCGStab, 1 flexible
+    // GCR preconditioned by the Schwarz alternating procedure (sap.cu); its cycles, minimal-residual
+    // steps per block and kept search directions, and the iterations of the last inner solve
+    int outer_method = 0;
+    int sap_ncy = 4, sap_nmr = 4, sap_nkv = 8;
+    int sap_last_iters = 0;
 
     // resident fields
     double2 *U64 = nullptr;  // [4][9][V]
@@ -188,7 +196,8 @@ enum {
     PROF_DSLASH16 = 8,      // 16-bit storage (FP16 or BF16) stencil, all hops
     PROF_DSLASH16_BLK = 9,  // 16-bit storage stencil, block-restricted hops
     PROF_BLOCK16 = 10,      // persistent block solver on 16-bit storage
-    PROF_NKIND = 11
+    PROF_SAP = 11,          // Schwarz preconditioner sweeps (SAP-GCR outer solver)
+    PROF_NKIND = 12
 };
 
 // Records CUDA events around the launches in its scope when profiling is on.
@@ -318,6 +327,12 @@ ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const do
 ddrw_status full_solve_dc_prepare(ddrw_ctx *ctx, int nrhs);
 ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, double2 *x, int nrhs, double tol,
                          int maxiter, ddrw_prec prec, SolveStats *stats);
+// Schwarz-preconditioned flexible GCR on FP32 fields (sap.cu): x = D(ms)^-1 b on the full lattice
+// until |b - D x|^2 <= thresh[r] per right-hand side; adds its iterations to *iters
+bool sap_supported(const ddrw_ctx *ctx);
+size_t sap_bytes_per_site_rhs(const ddrw_ctx *ctx);
+ddrw_status sap_gcr(ddrw_ctx *ctx, const MassSet &ms, const float4 *b, float4 *x, int nrhs,
+                    const std::vector<double> &thresh, int maxiter, int *iters);
 // mass set from a list of masses (builds the inverses on first use)
 ddrw_status make_massset(ddrw_ctx *ctx, int n, const double *m, MassSet *ms);
 

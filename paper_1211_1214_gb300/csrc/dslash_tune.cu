@@ -10,8 +10,12 @@
 // also with the neighbours read from the precomputed neighbour table) -- with CUDA
 // events on the context's stream, keeps the fastest,
 // and reuses it for every later launch of that shape.  The candidates run on the real
-// arguments: a stencil launch never reads its own output sites, so repeating it is harmless.
-// While the stream is being captured into a graph nothing is timed and the default is used.
+// arguments, which is harmless only while a launch does not read its own output sites: the hop
+// input of a one-parity launch lies on the other parity, but a launch whose output is its
+// diagonal input x, or its hop input with both parities written, would change its own input on
+// every repetition.  Such a launch is never timed: it runs the default form and leaves its shape
+// untuned for a later launch with separate buffers.  While the stream is being captured into a
+// graph nothing is timed and the default is used.
 #include <cstdio>
 #include <string>
 
@@ -51,6 +55,9 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
         if (cs == cudaStreamCaptureStatusNone) ctx->tune[key] = TuneEntry{def.nr, def.nt, def.nw, def.roll, -1.0f};
         return def;
     }
+    // output aliasing an input on the sites it reads: repeated runs would not be idempotent
+    if ((c.diag != 0 && c.x != nullptr && c.x == c.out) || (c.in != nullptr && c.in == c.out && c.npar == 2))
+        return def;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

@@ -104,7 +104,7 @@ __global__ void k_project_P(GeomDev g, double2 *r, int rpm, const double *dm, lo
 
 // delta = P (r - x) on supp P, zero elsewhere
 template <int BL>
-__global__ void k_delta(GeomDev g, const double2 *r, const double2 *x, double2 *d, long rs)
+__global__ void k_delta(GeomDev g, const double2 *r, const double2 *x, double2 *d, long rs, int g5x = 0)
 {
     long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.V) return;
@@ -117,6 +117,7 @@ __global__ void k_delta(GeomDev g, const double2 *r, const double2 *x, double2 *
     long o = (long)blockIdx.y * rs + s;
     for (int k = 0; k < 12; k++) {
         double2 a = r[o + (long)k * g.V], b = x[o + (long)k * g.V];
+        if (g5x && k >= 6) b = make_double2(-b.x, -b.y);  // g5 = diag(1, 1, -1, -1) on x
         d[o + (long)k * g.V] = in ? make_double2(a.x - b.x, a.y - b.y) : make_double2(0.0, 0.0);
     }
 }
@@ -183,6 +184,16 @@ __global__ void k_scatter_packed(const int *__restrict__ idx, long n, const doub
     field[((long)h * 12 + comp) * V + idx[j]] = make_double2(p[0], p[1]);
 }
 
+// y = g5 x on every site (spins 2, 3 flipped) for nrhs full FP64 fields
+__global__ void k_gamma5_field(long n12V, long V, int nrhs, const double2 *x, double2 *y)
+{
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n12V * nrhs) return;
+    long e = i % n12V;
+    double2 v = x[i];
+    y[i] = e / V >= 6 ? make_double2(-v.x, -v.y) : v;
+}
+
 // out_e = S(m) in_e with S = A_ee - 1/4 H_eo A_oo^-1 H_oe (FP64, all blocks; tmp holds A_oo^-1 H_oe in)
 static ddrw_status apply_schur_eo64(ddrw_ctx *ctx, double m, const double2 *in, double2 *out, double2 *tmp,
                                     int nrhs)
@@ -246,6 +257,7 @@ static void fill_info(ddrw_solve_info *info, const SolveStats &s, double secs)
     info->cycles = s.outer_cycles;
     info->fp64_dslash_calls = s.fp64_dslash_full;
     info->block_iters_max = s.block_iters_max;
+    info->iters_inner_total = (int)std::min<long>(s.block_iters_total, 2147483647L);
     info->true_rel_residual = s.outer_rel_residual;
     info->seconds = secs;
 }
@@ -448,6 +460,7 @@ static ddrw_status chunk_replay(ddrw_ctx *ctx, const EstGraph &eg, int nrhs, uin
     for (auto &sl : eg.loop_launches) launches += sl.second * d.loop_iters[sl.first];
     ctx->launches += launches;
     stats.block_iters_max = std::max(stats.block_iters_max, d.block_iters_max);
+    stats.block_iters_total += d.block_iters_total;
     stats.block_cycles += d.block_cycles;
     stats.block_rel_residual = std::max(stats.block_rel_residual, d.block_rel_residual);
     stats.fp64_dslash_half += d.fp64_dslash_half;
@@ -582,6 +595,8 @@ static int rhs_budget(ddrw_ctx *ctx)
     size_t have = fr;
     for (auto &kv : ctx->ws) have += kv.second.bytes;  // workspaces are reused
     double per = 4096.0 * (double)ctx->V;
+    if (ctx->prec == DDRW_MIXED_FP32 && ctx->outer_method == 1 && sap_supported(ctx))
+        per += (double)sap_bytes_per_site_rhs(ctx) * (double)ctx->V;  // the GCR search directions
     int n = (int)((double)have * 0.85 / per);
     return std::max(1, std::min(n, 64));
 }
@@ -941,7 +956,7 @@ ddrw_status ddrw_solve_schur(ddrw_ctx *ctx, double m, const double *b, double *x
     return conv;
 }
 
-ddrw_status ddrw_apply_schur(ddrw_ctx *ctx, double m, const double *in, double *out, int nrhs)
+ddrw_status ddrw_apply_schur(ddrw_ctx *ctx, double m, int dagger, const double *in, double *out, int nrhs)
 {
     if (!ctx || !in || !out || nrhs <= 0) return set_error(ctx, DDRW_EINVAL, "bad argument");
     if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
@@ -959,16 +974,31 @@ ddrw_status ddrw_apply_schur(ddrw_ctx *ctx, double m, const double *in, double *
     if ((st = stage_out(ctx, out, pbytes, "stage_out", &dout, &host))) return st;
     const bool mixed = ctx->prec != DDRW_FP64;
     unpack_P64(ctx, (const double *)din, F[0], nrhs);
-    // A v = v - P D_bb^-1 D_bw D_ww^-1 D_wb v
-    DDRW_CUDA_CHECK(cudaMemsetAsync(F[1], 0, fb, ctx->stream));
-    hop_between(ctx, DDRW_WHITE, F[0], F[1], nrhs);
-    if ((st = block_solve64(ctx, DDRW_WHITE, ms, F[1], F[2], nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, nullptr))) return st;
-    DDRW_CUDA_CHECK(cudaMemsetAsync(F[1], 0, fb, ctx->stream));
-    hop_between(ctx, DDRW_BLACK, F[2], F[1], nrhs);
-    if ((st = block_solve64(ctx, DDRW_BLACK, ms, F[1], F[3], nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, nullptr))) return st;
     GeomDev g = geom_dev(ctx);
     dim3 grid((unsigned)((ctx->V + 127) / 128), (unsigned)nrhs);
-    DISPATCH_BL(ctx, k_delta, grid, 128, g, F[0], F[3], F[1], 12 * ctx->V);
+    if (!dagger) {
+        // A v = v - P D_bb^-1 D_bw D_ww^-1 D_wb v
+        DDRW_CUDA_CHECK(cudaMemsetAsync(F[1], 0, fb, ctx->stream));
+        hop_between(ctx, DDRW_WHITE, F[0], F[1], nrhs);
+        if ((st = block_solve64(ctx, DDRW_WHITE, ms, F[1], F[2], nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, nullptr))) return st;
+        DDRW_CUDA_CHECK(cudaMemsetAsync(F[1], 0, fb, ctx->stream));
+        hop_between(ctx, DDRW_BLACK, F[2], F[1], nrhs);
+        if ((st = block_solve64(ctx, DDRW_BLACK, ms, F[1], F[3], nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, nullptr))) return st;
+        DISPATCH_BL(ctx, k_delta, grid, 128, g, F[0], F[3], F[1], 12 * ctx->V, 0);
+    } else {
+        // A^dag v = v - P (D_wb)^dag (D_ww^-1)^dag (D_bw)^dag (D_bb^-1)^dag v, and D^dag = g5 D g5 gives
+        // (D_XY)^dag = g5 D_YX g5 for the blocks of Eq. 1:  A^dag v = v - P g5 D_bw D_ww^-1 D_wb D_bb^-1 g5 v
+        const long n12 = 12 * ctx->V;
+        ++ctx->launches;
+        k_gamma5_field<<<(unsigned)((n12 * nrhs + 255) / 256), 256, 0, ctx->stream>>>(n12, ctx->V, nrhs, F[0], F[1]);
+        if ((st = block_solve64(ctx, DDRW_BLACK, ms, F[1], F[2], nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, nullptr))) return st;
+        DDRW_CUDA_CHECK(cudaMemsetAsync(F[1], 0, fb, ctx->stream));
+        hop_between(ctx, DDRW_WHITE, F[2], F[1], nrhs);
+        if ((st = block_solve64(ctx, DDRW_WHITE, ms, F[1], F[3], nrhs, ctx->tol_block, ctx->maxiter, ctx->prec, nullptr))) return st;
+        DDRW_CUDA_CHECK(cudaMemsetAsync(F[1], 0, fb, ctx->stream));
+        hop_between(ctx, DDRW_BLACK, F[3], F[1], nrhs);
+        DISPATCH_BL(ctx, k_delta, grid, 128, g, F[0], F[1], F[1], 12 * ctx->V, 1);  // element-wise in place
+    }
     pack_P64(ctx, F[1], (double *)dout, nrhs);
     if ((st = finish_out(ctx, out, dout, pbytes, host))) return st;
     return sync(ctx);

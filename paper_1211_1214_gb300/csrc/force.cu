@@ -547,6 +547,7 @@ extern "C" ddrw_status ddrw_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64
         info->cycles = stats.outer_cycles;
         info->fp64_dslash_calls = stats.fp64_dslash_full;
         info->block_iters_max = stats.block_iters_max;
+        info->iters_inner_total = (int)std::min<long>(stats.block_iters_total, 2147483647L);
         info->true_rel_residual = stats.outer_rel_residual;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }

@@ -7,13 +7,13 @@
 // solver, the defect-correction residual and correction, the reduction slots) in one file-scope
 // device array of fixed size.  The caller still passes b and x.
 //
-// The array is a host-side stand-in in host code; its device address is taken once per device,
-// with that device current, by cudaGetSymbolAddress on the first call of the entry point on that
-// device.  Every GPU that loads this code holds the array until the process exits.  Every call
-// shares the array and leaves its contents from the last call behind; two calls that overlap on
-// the GPU (different streams or contexts on one device) race on it.
+// The array is a host-side stand-in in host code; its device address is looked up on every call,
+// with the context's device current, by cudaGetSymbolAddress (cheap, and never stale after a
+// device reset).  Every GPU that loads this code holds the array until the process exits.  Every
+// call shares the array and leaves its contents from the last call behind; two calls that overlap
+// on the GPU (different streams or contexts on one device) race on it.  The call synchronises its
+// stream and reads scalars back to the host, so it refuses to run inside a stream capture.
 #include <cmath>
-#include <mutex>
 #include <vector>
 
 #include "blocksolve.cuh"
@@ -37,22 +37,13 @@ static __device__ __align__(256) double2 noalloc_scratch[NOALLOC_FIELDS * NOALLO
 
 namespace {
 
-constexpr int MAX_DEVICES = 64;
-std::mutex scratch_mutex;
-double2 *scratch_ptr[MAX_DEVICES] = {nullptr};
-
-// device address of the scratch array on the current device (set up on first use)
+// device address of the scratch array on the current device (the context's device is current)
 ddrw_status scratch_address(ddrw_ctx *ctx, double2 **out)
 {
-    if (ctx->device < 0 || ctx->device >= MAX_DEVICES) return set_error(ctx, DDRW_EINVAL, "device ordinal too large");
-    std::lock_guard<std::mutex> lock(scratch_mutex);
-    if (!scratch_ptr[ctx->device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
-        if (e != cudaSuccess || !p) return set_cuda_error(ctx, e, "cudaGetSymbolAddress(noalloc_scratch)", __FILE__, __LINE__);
-        scratch_ptr[ctx->device] = (double2 *)p;
-    }
-    *out = scratch_ptr[ctx->device];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
+    if (e != cudaSuccess || !p) return set_cuda_error(ctx, e, "cudaGetSymbolAddress(noalloc_scratch)", __FILE__, __LINE__);
+    *out = (double2 *)p;
     return DDRW_OK;
 }
 
@@ -119,11 +110,16 @@ extern "C" ddrw_status ddrw_solve_block_noalloc(ddrw_ctx *ctx, int colour, doubl
         return set_error(ctx, DDRW_EINVAL, "ddrw_solve_block_noalloc serves lattices of at most 20736 sites (12^4)");
     if (!is_device_ptr(b) || !is_device_ptr(x))
         return set_error(ctx, DDRW_EINVAL, "ddrw_solve_block_noalloc takes device pointers only (no staging buffer)");
+    if (m != ctx->m1 && m != ctx->m2)
+        return set_error(ctx, DDRW_EINVAL, "ddrw_solve_block_noalloc needs m = m1 or m2 of ddrw_set_params");
     MassInv *mi = nullptr;
     for (auto &e : ctx->inv)
         if (e.m == m) mi = &e;
-    if (!mi) return set_error(ctx, DDRW_EINVAL, "ddrw_solve_block_noalloc needs m = m1 or m2 of ddrw_set_params");
+    if (!mi) return set_error(ctx, DDRW_ESTATE, "the in-block inverse of m1 / m2 is missing (call ddrw_set_params)");
     if (cudaSetDevice(ctx->device) != cudaSuccess) return set_error(ctx, DDRW_ECUDA, "cudaSetDevice");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return set_error(ctx, DDRW_ESTATE, "ddrw_solve_block_noalloc cannot run inside a stream capture");
 
     double2 *base;
     ddrw_status st = scratch_address(ctx, &base);
@@ -140,6 +136,7 @@ extern "C" ddrw_status ddrw_solve_block_noalloc(ddrw_ctx *ctx, int colour, doubl
     DDRW_CUDA_CHECK(cudaMemsetAsync(fx, 0, sizeof(double2) * fe, ctx->stream));
     if ((st = colour_norm(ctx, colour, fb, red, h))) return st;
     const double bb = h[0];
+    if (!std::isfinite(bb)) return set_error(ctx, DDRW_ENUMERIC, "non-finite right-hand side");
 
     BlkArgs<PrecD> a;
     a.r = F[2];
@@ -162,7 +159,7 @@ extern "C" ddrw_status ddrw_solve_block_noalloc(ddrw_ctx *ctx, int colour, doubl
     a.stat = stat;
 
     double rel = bb > 0 ? 1.0 : 0.0;
-    int itmax = 0, cycles = 0;
+    int itmax = 0, itsum = 0, cycles = 0;
     const double2 *rhs = fb;
     while (bb > 0 && cycles < 10) {
         DDRW_CUDA_CHECK(cudaMemsetAsync(stat, 0, sizeof(int) * 2, ctx->stream));
@@ -194,6 +191,7 @@ extern "C" ddrw_status ddrw_solve_block_noalloc(ddrw_ctx *ctx, int colour, doubl
         DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, stat, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
         if ((st = colour_norm(ctx, colour, fres, red + 1, h))) return st;
         itmax = std::max(itmax, hs[0]);
+        itsum += hs[0];
         cycles++;
         rel = std::sqrt(h[0] / bb);
         if (!(rel == rel)) return set_error(ctx, DDRW_ENUMERIC, "NaN in a block solve");
@@ -205,6 +203,7 @@ extern "C" ddrw_status ddrw_solve_block_noalloc(ddrw_ctx *ctx, int colour, doubl
     if (info) {
         *info = ddrw_solve_info{};
         info->block_iters_max = itmax;
+        info->iters_inner_total = itsum;
         info->cycles = cycles;
         info->true_rel_residual = rel;
     }

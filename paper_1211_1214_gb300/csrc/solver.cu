@@ -310,7 +310,12 @@ static ddrw_status inner_solve(ddrw_ctx *ctx, const MassSet &ms, const double2 *
     if ((st = workspace(ctx, ne, fl, &el))) return st;
     VecRange all{V, 0, V, 12 * V, nrhs};
     to_low<P>(ctx, all, rsl, rhs, (E *)bl, scale_d);
-    if ((st = eo_bicgstab<P>(ctx, ms, (const E *)bl, (E *)el, nrhs, th, maxiter, iters))) return st;
+    if (P::ID == 32 && ctx->outer_method == 1 && sap_supported(ctx)) {
+        // Schwarz-preconditioned flexible GCR on the FP32 fields
+        if ((st = sap_gcr(ctx, ms, (const float4 *)bl, (float4 *)el, nrhs, th, maxiter, iters))) return st;
+    } else if ((st = eo_bicgstab<P>(ctx, ms, (const E *)bl, (E *)el, nrhs, th, maxiter, iters))) {
+        return st;
+    }
     if (first) DDRW_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double2) * 12 * V * nrhs, ctx->stream));
     add_low<P>(ctx, all, rsl, (const E *)el, x, scale_d + nrhs);
     return DDRW_OK;

@@ -101,6 +101,29 @@ def test_apply_schur(case):
     assert rel(out[0].reshape(-1), want) < 1e-11
 
 
+def test_apply_schur_dagger(case):
+    """A(m)^dag on supp P (Sec. 1, with D^dag = g5 D g5): <x, A y> = <A^dag x, y>, and on the 4^4
+    lattice A^dag x equals the conjugate transpose of the oracle's dense A(m) applied to x."""
+    ctx, lat = case["ctx"], case["lat"]
+    m = case["m2"]
+    x = synth.complex_gaussian((1, ctx.nP, 4, 3), seed=34)
+    y = synth.complex_gaussian((1, ctx.nP, 4, 3), seed=35)
+    ay = np.zeros_like(y)
+    adx = np.zeros_like(x)
+    ctx.apply_schur(m, y, ay)
+    ctx.apply_schur(m, x, adx, dagger=True)
+    lhs, rhs = np.vdot(x, ay), np.vdot(adx, y)
+    assert abs(lhs - rhs) <= 1e-11 * abs(lhs)
+    if lat.V <= 256:
+        from oracle import dense as od
+        want = od.schur_on_P(lat, m).conj().T @ x.reshape(-1)
+        assert rel(adx.reshape(-1), want) < 1e-11
+        # and it is not A itself (the test is not vacuous)
+        ax = np.zeros_like(x)
+        ctx.apply_schur(m, x, ax)
+        assert rel(ax.reshape(-1), want) > 1e-3
+
+
 def test_dA_and_delta_and_exponent(case):
     """r = (A(m1) - A(m2)) eta, delta = A(m2)^-1 r and e_j against the oracle's own chain."""
     ctx, lat = case["ctx"], case["lat"]
@@ -121,6 +144,7 @@ def test_dA_and_delta_and_exponent(case):
         e_orc.append(res["e"])
     assert close(logw, oc.log_w(e_orc))
     assert info["true_rel_residual"] <= 1e-10
+    assert info["iters_inner_total"] >= info["block_iters_max"] > 0
 
 
 def test_estimate_with_own_noise_equals_estimate_with_passed_noise(case):

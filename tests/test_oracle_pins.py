@@ -518,3 +518,69 @@ def test_estimator_operators_factorise_the_determinant_ratio(c1):
     assert abs(lt - (lh + b1.sum() - b2.sum())) < 1e-9
     # the ratio matrices differ (the estimator's variance depends on the choice, Fig. 1)
     assert abs(lt - lh) > 1e-3
+
+
+# ---- the log-sum-exp of Eq. 3 / Eq. 8 (oracle.core.log_w) and the block factor of Eq. 7
+# (oracle.blockdet.log_block_factor): both serve as checkers of the GPU's log W
+
+def _log_w_decimal(exponents, digits=60):
+    """log((1/N) sum_j exp(-e_j)) in 60-digit decimal arithmetic: no shift, no overflow."""
+    from decimal import Decimal, localcontext
+    with localcontext() as ctx:
+        ctx.prec = digits
+        s = sum((-Decimal(repr(float(e)))).exp() for e in exponents)
+        return float((s / len(exponents)).ln())
+
+
+def test_log_w_against_the_direct_sum():
+    """Eq. 3: W = (1/N_hit) sum_j exp(-e_j).  On moderate exponents log_w equals the direct
+    formula evaluated in FP64 and in high precision."""
+    rng = np.random.default_rng(31)
+    for n in (1, 2, 7, 16, 48):
+        e = rng.normal(3.0, 2.0, size=n)
+        direct = float(np.log(np.mean(np.exp(-e))))
+        assert abs(oc.log_w(e) - direct) <= 1e-13 * max(1.0, abs(direct))
+        assert abs(oc.log_w(e) - _log_w_decimal(e)) <= 1e-13 * max(1.0, abs(direct))
+
+
+def test_log_w_at_exponents_where_the_direct_form_overflows():
+    """Exponents of -710 .. +760 overflow (exp(710) = inf) or underflow (exp(-760) = 0) in the
+    direct form; log_w must stay exact there (the paper's log W at 64x32^3 is O(10^3))."""
+    for e in ([-710.0, -711.5, -709.25], [700.0, 745.0, 760.0, 701.0], [-700.0, 700.0], [2571.8, 2570.1]):
+        with np.errstate(over="ignore", divide="ignore"):
+            direct = np.log(np.mean(np.exp(-np.asarray(e))))
+        want = _log_w_decimal(e)
+        got = oc.log_w(e)
+        assert np.isfinite(got)
+        assert abs(got - want) <= 1e-13 * max(1.0, abs(want))
+        if not np.isfinite(direct):
+            continue
+        assert abs(got - direct) <= 1e-12 * max(1.0, abs(want))
+
+
+def test_log_w_normalisation_and_sign():
+    """Equal exponents give log W = -e exactly (the -log N_hit offset cancels N equal terms); one
+    finite term among N whose others vanish gives -e - log N; W decreases as an exponent grows."""
+    for n in (1, 3, 16):
+        assert abs(oc.log_w([2.5] * n) - (-2.5)) < 1e-15
+        assert abs(oc.log_w([0.25] + [5000.0] * (n - 1)) - (-0.25 - np.log(n))) < 1e-14
+    assert oc.log_w([1.0]) == -1.0
+    assert oc.log_w([1.0, 2.0]) > oc.log_w([1.0, 3.0])
+
+
+def test_log_block_factor_completes_the_determinant_ratio(c1):
+    """Eq. 7 with Eq. 3: W = W_gl prod_k det D_k^2(m2)/det D_k^2(m1) with W_gl = 1/det(Mh^dag Mh)
+    (its exact value, dense), and by det D = det Dhat det D_bb det D_ww (Sec. 1) the product is
+    det D(m2)^2 / det D(m1)^2 = the two-flavour ratio 1/det(M^dag M) of the total operator, Eq. 2.
+    Swapped masses, a missing square or a lost block fail this."""
+    from oracle import blockdet as ob
+    for m1, m2 in ((0.20, 0.19), (0.20, 0.12)):
+        Mh = od.ratio_matrix(c1, m1, m2)
+        log_w_gl = float(np.log(od.inv_det_MdagM(Mh)))
+        _, l1 = od.logdet(od.dense_D(c1, m1))
+        _, l2 = od.logdet(od.dense_D(c1, m2))
+        want = 2.0 * (l2 - l1)
+        got = ob.log_block_factor(c1, m1, m2) + log_w_gl
+        assert abs(got - want) <= 1e-9 * max(1.0, abs(want))
+        # the block factor alone is not the whole ratio (the test is not vacuous)
+        assert abs(ob.log_block_factor(c1, m1, m2) - want) > 1e-3

@@ -59,3 +59,36 @@ def test_rejects_what_the_scratch_cannot_serve(ctx):
             big.solve_block_noalloc(0, 0.045, bb, torch.zeros_like(bb))
     finally:
         big.close()
+
+
+def test_non_finite_right_hand_side_is_an_error(ctx):
+    c, dims = ctx
+    b = torch.from_numpy(synth.spinor_field(dims, seed=44)).cuda()
+    b[3, 1, 2] = complex(float("nan"), 0.0)
+    x = torch.zeros_like(b)
+    with pytest.raises(binding.DDRWError, match="non-finite"):
+        c.solve_block_noalloc(0, 0.045, b, x)
+
+
+def test_calls_allocate_no_device_memory():
+    """On a fresh context (no allocating solve before it), after one warm-up call, further calls
+    leave the device's free memory unchanged: no cudaMalloc and no allocating library routine."""
+    dims, l = (8, 8, 8, 8), 4
+    c = binding.Context(dims, (l,) * 4)
+    try:
+        c.load_gauge(torch.from_numpy(synth.gauge_field(dims, 0.25, seed=2)).cuda())
+        c.set_params(1.5, 0.05, 0.045)
+        c.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+        bs = [torch.from_numpy(synth.spinor_field(dims, seed=50 + k)).cuda() for k in range(3)]
+        xs = [torch.zeros_like(b) for b in bs]
+        for colour in (0, 1):  # warm-up: first launches of each shape (stencil autotuning)
+            c.solve_block_noalloc(colour, 0.045, bs[0], xs[0])
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        c.solve_block_noalloc(1, 0.05, bs[1], xs[1])
+        c.solve_block_noalloc(0, 0.05, bs[2], xs[2])
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0
+    finally:
+        c.close()
