@@ -145,9 +145,10 @@ __device__ __noinline__ Dot3<typename P::R> site_even(const GeomDev &g, long s, 
 }
 
 template <class P, int BL, int NT>
-// 32-bit arithmetic: at least two 256-thread (three 128-thread) CTAs per SM, i.e. at most 128 (170)
-// registers, so the register allocation keeps the occupancy of the out-of-line site functions
-__global__ void __launch_bounds__(NT, sizeof(typename P::R) == 4 ? (NT >= 256 ? 2 : NT >= 128 ? 3 : 1) : 1)
+// 32-bit arithmetic: at most 128 registers (170 for 128 threads) -- two 256-thread CTAs or one
+// 512-thread CTA per SM -- so the register allocation keeps the occupancy of the out-of-line site
+// functions
+__global__ void __launch_bounds__(NT, sizeof(typename P::R) == 4 ? (NT >= 512 ? 1 : NT >= 256 ? 2 : NT >= 128 ? 3 : 1) : 1)
     k_block_solve(GeomDev g, BlkArgs<P> a)
 {
     using R = typename P::R;
@@ -313,6 +314,11 @@ __global__ void __launch_bounds__(NT, sizeof(typename P::R) == 4 ? (NT >= 256 ? 
     }
 }
 
+// Launch shape of the block solver: NT threads per (block, right-hand side), or for blocks of at
+// least 512 sites per parity on 32- and 16-bit storage also 2 NT threads (one CTA per SM instead of
+// two, half the Krylov vectors of the resident CTAs competing for L2).  The first launch of each
+// (storage, block length, right-hand sides) shape times both on the real arguments -- the kernel
+// reads b and overwrites all of x, so a repeat gives the same result -- and keeps the faster.
 template <class P, int BL>
 void launch_block_kernel(ddrw_ctx *ctx, const BlkArgs<P> &a, int nrhs)
 {
@@ -320,9 +326,42 @@ void launch_block_kernel(ddrw_ctx *ctx, const BlkArgs<P> &a, int nrhs)
     dim3 grid((unsigned)nrhs, (unsigned)ctx->nblk_c);
     constexpr int VBH = BlockShape<BL>::VBH;
     constexpr int NT = VBH <= 32 ? 32 : (VBH <= 128 ? 128 : 256);
-    ProfScope ps(ctx, P::ID == 64 ? PROF_BLOCK64 : P::ID == 32 ? PROF_BLOCK32 : PROF_BLOCK16, 0.0);
-    ++ctx->launches;
-    k_block_solve<P, BL, NT><<<grid, NT, 0, ctx->stream>>>(g, a);
+    constexpr bool WIDE = VBH >= 512 && P::ID != 64;
+    constexpr int NT2 = WIDE ? 2 * NT : NT;
+    const int kind = P::ID == 64 ? PROF_BLOCK64 : P::ID == 32 ? PROF_BLOCK32 : PROF_BLOCK16;
+    auto run = [&](int form) {
+        ++ctx->launches;
+        if (form) k_block_solve<P, BL, NT2><<<grid, NT2, 0, ctx->stream>>>(g, a);
+        else k_block_solve<P, BL, NT><<<grid, NT, 0, ctx->stream>>>(g, a);
+    };
+    int form = 0;
+    if (WIDE) {
+        const std::array<int, 3> key = {P::ID, BL, nrhs};
+        auto it = ctx->blk_tune.find(key);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(ctx->stream, &cs);
+        if (it != ctx->blk_tune.end()) {
+            form = it->second;
+        } else if (ctx->autotune && cs == cudaStreamCaptureStatusNone && a.b != a.x) {
+            cudaEvent_t e[3];
+            for (auto &ev : e) cudaEventCreate(&ev);
+            cudaEventRecord(e[0], ctx->stream);
+            run(0);
+            cudaEventRecord(e[1], ctx->stream);
+            run(1);
+            cudaEventRecord(e[2], ctx->stream);
+            cudaEventSynchronize(e[2]);
+            float t0 = 0, t1 = 0;
+            cudaEventElapsedTime(&t0, e[0], e[1]);
+            cudaEventElapsedTime(&t1, e[1], e[2]);
+            for (auto &ev : e) cudaEventDestroy(ev);
+            form = (cudaGetLastError() == cudaSuccess && t1 < t0) ? 1 : 0;
+            ctx->blk_tune[key] = form;
+            cudaMemsetAsync(a.stat, 0, 2 * sizeof(int), ctx->stream);  // the timing runs counted too
+        }
+    }
+    ProfScope ps(ctx, kind, 0.0);
+    run(form);
 }
 
 }  // namespace ddrw

@@ -164,6 +164,7 @@ struct ddrw_ctx {
     bool autotune = true;
     int pinned_nr = 0, pinned_nt = 128, pinned_nw = 1, pinned_roll = 0;
     std::map<std::array<int, 8>, ddrw::TuneEntry> tune;
+    std::map<std::array<int, 3>, int> blk_tune;  // block-solver launch shape (blocksolve.cuh)
 
     // kernel timing (ddrw_profile): CUDA events around the instrumented launches
     bool prof_on = false;

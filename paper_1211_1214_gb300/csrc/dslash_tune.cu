@@ -110,6 +110,7 @@ ddrw_status ddrw_autotune(ddrw_ctx *ctx, int enable)
     if (!ctx) return DDRW_EINVAL;
     ctx->autotune = enable != 0;
     ctx->tune.clear();
+    ctx->blk_tune.clear();
     clear_graphs(ctx);  // captured launches keep the form they were captured with
     return DDRW_OK;
 }

@@ -150,7 +150,7 @@ __device__ __forceinline__ void hop_in_dir(const float4 *sU, const float4 *in, c
     }
 }
 
-__device__ __noinline__ void hop_in(const float4 *sU, const float4 *in, int h, int p, Spinor<float> &acc)
+__device__ __forceinline__ void hop_in(const float4 *sU, const float4 *in, int h, int p, Spinor<float> &acc)
 {
     int a[4];
     sb_coords(h, p, a);
@@ -203,7 +203,7 @@ __device__ __forceinline__ void hop_out_dir(const GeomDev &g, const Site<BL> &st
 }
 
 template <int BL>
-__device__ __noinline__ void hop_out(const GeomDev &g, int s, const int (&a)[4], const float4 *f,
+__device__ __forceinline__ void hop_out(const GeomDev &g, int s, const int (&a)[4], const float4 *f,
                                      const float4 *__restrict__ U, Spinor<float> &acc)
 {
     Site<BL> st;

@@ -67,3 +67,68 @@ def test_mixed_estimate_matches_fp64_at_full_size(full, prec):
     assert abs(e32[0] - e64[0]) <= 1e-8 * max(abs(e64[0]), 1.0)
     assert abs(lw32 - lw64) <= 1e-8 * max(abs(lw64), 1.0)
     assert info["true_rel_residual"] <= 1e-10
+
+
+# ---- direct parity with the oracle at the paper-shaped sizes (Sec. 2: 64x32^3 with 8^4 blocks,
+# 48x24^3 with 6^4 blocks): the oracle's exponents of sampled noise vectors, written by
+# tests/golden/make_fullsize_oracle.py (five FP64 CGNR solves each), against the benchmark's own
+# launch configuration (FP32 inner solves, FP64 defect correction, residual 1e-10, block
+# tolerance 1e-10, every hit and target mass of one step in one batched call)
+
+import json
+import os
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name):
+    p = os.path.join(GOLDEN, name)
+    if not os.path.exists(p):
+        pytest.skip(f"{name} not written yet (tests/golden/make_fullsize_oracle.py)")
+    return json.load(open(p))
+
+
+def _check_against_golden(E, m2s, nhit, doc):
+    E = np.asarray(E, dtype=np.float64).reshape(-1)  # [mass][hit]
+    by_mass = {}
+    for ent in doc["entries"]:
+        k = min(range(len(m2s)), key=lambda i: abs(m2s[i] - ent["m2"]))
+        assert abs(m2s[k] - ent["m2"]) < 1e-12
+        e_gpu = float(E[k * nhit + ent["hit"]])
+        assert abs(e_gpu - ent["e"]) <= 1e-8 * max(abs(ent["e"]), 1.0), (ent, e_gpu)
+        by_mass.setdefault(k, []).append((ent["e"], e_gpu))
+    for k, pairs in by_mass.items():
+        lw_orc = oc.log_w([p[0] for p in pairs])
+        lw_gpu = oc.log_w([p[1] for p in pairs])
+        assert abs(lw_gpu - lw_orc) <= 1e-8 * max(abs(lw_orc), 1.0)
+    return len(doc["entries"])
+
+
+def test_bench_configuration_matches_oracle_at_64x32x32x32(full):
+    ctx, lat = full
+    doc = _golden("oracle_exponents_64x32x32x32.json")
+    m2s, nhit = [0.018, 0.015, 0.010], 16
+    ctx.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-10)
+    E, LW, _, info = ctx.estimate_masses(m2s, nhit, seed=doc["noise_seed"], hit_offset=0)
+    assert _check_against_golden(E, m2s, nhit, doc) >= 1
+    E = np.asarray(E, dtype=np.float64).reshape(len(m2s), nhit)
+    for k in range(len(m2s)):
+        lw = oc.log_w(E[k])
+        assert abs(LW[k] - lw) <= 1e-12 * max(abs(lw), 1.0)
+    assert info["true_rel_residual"] <= 1e-10
+
+
+def test_48x24x24x24_matches_oracle():
+    doc = _golden("oracle_exponents_48x24x24x24.json")
+    dims, l, m2s, nhit = (48, 24, 24, 24), 6, [0.015], 32
+    U = synth.gauge_field(dims, doc["eps"], seed=doc["gauge_seed"])
+    ctx = binding.Context(dims, (l,) * 4)
+    try:
+        ctx.load_gauge(torch.from_numpy(U).cuda())
+        ctx.set_params(doc["csw"], doc["m1"], m2s[0])
+        ctx.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-10)
+        E, _, _, info = ctx.estimate_masses(m2s, nhit, seed=doc["noise_seed"], hit_offset=0)
+        assert _check_against_golden(E, m2s, nhit, doc) >= 1
+        assert info["true_rel_residual"] <= 1e-10
+    finally:
+        ctx.close()
