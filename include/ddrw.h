@@ -289,7 +289,10 @@ ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
  * order) or 8 (staged, FP32 storage only: a CTA of nt sites x nw rows covers every right-hand side
  * of one mass slot; the tile's links, A^-1 / clover terms and neighbour entries are brought into
  * shared memory once by bulk asynchronous copies and shared by those right-hand sides; nt <= 128;
- * other storage precisions run form 5 instead); roll 2-4, 7 and 8 need nr = 1, roll 5 and 6
+ * other storage precisions run form 5 instead), 9 / 10 (pipelined, FP32 storage only: each thread
+ * copies the neighbour spinor and link of its hops into a two-slot shared-memory ring with 16-byte
+ * asynchronous copies two hops ahead of the arithmetic; at least 2 / 3 CTAs per SM; other
+ * precisions run form 5); roll 2-4 and 7-10 need nr = 1, roll 5 and 6
  * nr <= 2.
  * A launch whose right-hand sides per mass slot are not a multiple of nr * nw runs with nr = nw = 1.
  * nr = 0 returns to autotuning.  DDRW_EINVAL for values outside these ranges.  A change drops the
@@ -320,6 +323,30 @@ ddrw_status ddrw_test_stall_staging(ddrw_ctx *ctx, int enable);
  * mass (16 blocks, 16 SMs busy). */
 ddrw_status ddrw_block_logdet(ddrw_ctx *ctx, double m, double *logdet, double *sign);
 ddrw_status ddrw_block_factor(ddrw_ctx *ctx, double *log_w_blk);
+
+/* The block factor of Eq. 7 for blocks too large for a dense determinant (8^4), by the nested
+ * decomposition of Sec. 2.2 (caption of Fig. 2: the 8^4 blocks are decomposed further into an 8^4
+ * Schur complement with Dirichlet boundaries and 4^4 blocks).  Each block operator D_k is cut into
+ * sub-blocks of length lsub, coloured black/white inside the block:
+ *     det D_k = det Shat_k * prod_{sub in k} det D_sub     (Sec. 1, applied to D_k),
+ * so  log prod_k det D_k^2(m2)/det D_k^2(m1) = [sub-block factor, exact, as ddrw_block_factor on
+ * blocks of length lsub] + [log prod_k det Shat_k^2(m2)/det Shat_k^2(m1), estimated with Eq. 3 from
+ * nhit Philox noise vectors (seed, hits 0 .. nhit-1) on the supp P of the sub-blocks].  out[0] the
+ * sum, out[1] the exact part, out[2] the stochastic part; exponents[nhit] and rel_var (each
+ * optional) as in ddrw_estimate.  The work runs on an auxiliary context of the same lattice and
+ * field with blocks of length lsub and the hops across the faces of this context's blocks removed
+ * (the clover term kept): about the memory of a second context.  lsub in {2, 4, 6} with
+ * l / lsub even; precision and tolerances of ddrw_set_solver. */
+ddrw_status ddrw_block_factor_nested(ddrw_ctx *ctx, int lsub, int nhit, uint64_t seed, double *out, double *exponents,
+                                     double *rel_var);
+
+/* Dirichlet boxes: with cut > 0 (a multiple of the block length dividing every dimension) the hops
+ * across the faces of the cut^4 boxes (U_mu(x) with x_mu = cut - 1 mod cut) are removed from the
+ * operator after the clover term has been built from the full field, so that D is the direct sum of
+ * the boxes' Dirichlet operators D_k of Eq. 7.  Must precede ddrw_load_gauge (DDRW_ESTATE after);
+ * 0 (the default) keeps every hop.  Used by ddrw_block_factor_nested; the full field's links are
+ * kept on the device for rebuilding the clover term. */
+ddrw_status ddrw_set_dirichlet(ddrw_ctx *ctx, int cut);
 
 /* Kernel timing for measurement (not part of the method): with profiling enabled, CUDA events
  * bracket every launch of the instrumented kernel classes on the context's stream, and

@@ -80,3 +80,27 @@ def log_block_factor(lat: "core.Lattice", m1: float, m2: float) -> float:
     l2, _ = block_logdets(lat, m2)
     l1, _ = block_logdets(lat, m1)
     return float(2.0 * (l2.sum() - l1.sum()))
+
+
+# ---- the nested decomposition of large blocks (Sec. 2.2, caption of Fig. 2: the 8^4 blocks are
+# decomposed further into an 8^4 Schur complement with Dirichlet boundaries and 4^4 blocks)
+
+def dirichlet_links(U: np.ndarray, dims, cut: int) -> np.ndarray:
+    """The links with every hop across a face of the cut^4 boxes removed (U_mu(x) = 0 where
+    x_mu = cut - 1 mod cut): with them the hopping term of D is the direct sum of the boxes'
+    Dirichlet operators D_k (hops inside the box).  The clover term is not computed from these."""
+    dims = tuple(int(d) for d in dims)
+    V = int(np.prod(dims))
+    X = np.stack(np.unravel_index(np.arange(V), dims), -1)
+    out = np.array(U, dtype=np.complex128, copy=True).reshape(V, 4, 3, 3)
+    for mu in range(4):
+        out[X[:, mu] % cut == cut - 1, mu] = 0.0
+    return out
+
+
+def dirichlet_lattice(dims, block, U, csw, cut, antiperiodic_t=False) -> "core.Lattice":
+    """A lattice whose operator is the direct sum of the cut^4 boxes' Dirichlet operators (clover
+    term of the full field U, hops inside the boxes only), cut into blocks of length `block`."""
+    lat = core.Lattice(dims, block, U, csw, antiperiodic_t)
+    lat.set_hopping_links(dirichlet_links(U, dims, cut))
+    return lat

@@ -41,6 +41,7 @@ def lib():
         L.orc_create.restype = ctypes.c_void_p
         L.orc_create.argtypes = [ip, ip, dp, ctypes.c_double, ctypes.c_int]
         L.orc_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_set_hopping_links.argtypes = [ctypes.c_void_p, dp]
         L.orc_volume.restype = ctypes.c_long
         L.orc_volume.argtypes = [ctypes.c_void_p]
         L.orc_clover_matrix.argtypes = [ctypes.c_void_p, ctypes.c_long, dp]
@@ -115,6 +116,13 @@ class Lattice:
         if h and _lib is not None:
             _lib.orc_destroy(h)
             self._h = None
+
+    def set_hopping_links(self, U: np.ndarray) -> None:
+        """Links of the hopping term from now on; the clover term stays the one of the creation links."""
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+        if U.shape != (self.V, 4, 3, 3):
+            raise ValueError("U must have shape (V, 4, 3, 3)")
+        lib().orc_set_hopping_links(self._h, _dp(U))
 
     # -- geometry
     def colour(self) -> np.ndarray:

@@ -261,6 +261,15 @@ void *orc_create(const int *L, const int *B, const double *U, double csw, int an
     return g;
 }
 
+/* Replace the links of the hopping term, keeping the clover term built at creation: with links
+ * that are zero across the faces of boxes, D becomes the direct sum of the boxes' Dirichlet
+ * operators (each D_k of Eq. 7 is such a box operator: hops inside the block, the full clover). */
+void orc_set_hopping_links(void *p, const double *U)
+{
+    orc_lat *g = (orc_lat *)p;
+    memcpy(g->U, U, sizeof(cplx) * 36 * (size_t)g->V);
+}
+
 void orc_destroy(void *p)
 {
     orc_lat *g = (orc_lat *)p;

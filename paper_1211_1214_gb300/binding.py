@@ -22,7 +22,8 @@ _STATUS = {0: "DDRW_OK", 1: "DDRW_EINVAL", 2: "DDRW_ENOMEM", 3: "DDRW_ECUDA", 4:
 
 #: every entry point declared in include/ddrw.h
 EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", "ddrw_volume", "ddrw_load_gauge",
-           "ddrw_set_params", "ddrw_set_solver", "ddrw_set_outer_solver", "ddrw_apply_sap", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
+           "ddrw_set_params", "ddrw_set_solver", "ddrw_set_outer_solver", "ddrw_set_dirichlet",
+           "ddrw_block_factor_nested", "ddrw_apply_sap", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
            "ddrw_autotune", "ddrw_autotune_report", "ddrw_stencil_config", "ddrw_profile_units",
@@ -79,6 +80,8 @@ def load(path: str | None = None):
         "ddrw_set_solver": (st, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
         "ddrw_set_outer_solver": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "ddrw_apply_sap": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
+        "ddrw_set_dirichlet": (st, [vp, ctypes.c_int]),
+        "ddrw_block_factor_nested": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, dp, dp, dp]),
         "ddrw_apply_D": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_apply_D_ds": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_apply_D_low": (st, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp, dp, ctypes.c_int]),
@@ -309,6 +312,18 @@ class Context:
         v = ctypes.c_double(0)
         self._check(self.L.ddrw_block_factor(self._h, ctypes.byref(v)), "ddrw_block_factor")
         return v.value
+
+    def block_factor_nested(self, lsub, nhit, seed=2):
+        """Eq. 7's block factor by the nested decomposition (Sec. 2.2): returns (total, exact sub-block
+        part, stochastic Schur part, exponents[nhit], relative sample variance)."""
+        out, e, rv = np.zeros(3), np.zeros(int(nhit)), np.zeros(1)
+        self._check(self.L.ddrw_block_factor_nested(self._h, int(lsub), int(nhit), ctypes.c_uint64(seed),
+                                                     _ptr(out), _ptr(e), _ptr(rv)), "ddrw_block_factor_nested")
+        return float(out[0]), float(out[1]), float(out[2]), e, float(rv[0])
+
+    def set_dirichlet(self, cut):
+        """Remove the hops across the faces of cut^4 boxes (before load_gauge)."""
+        self._check(self.L.ddrw_set_dirichlet(self._h, int(cut)), "ddrw_set_dirichlet")
 
     def stencil_config(self, nr=0, nt=128, nw=1, roll=0):
         """Pin the stencil launch configuration (nr = 0: back to the autotuner)."""

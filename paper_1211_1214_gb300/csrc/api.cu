@@ -601,6 +601,8 @@ void ddrw_destroy(ddrw_ctx *ctx)
     if (ctx->h_err) cudaFreeHost(ctx->h_err);
     cudaFree(ctx->U64);
     cudaFree(ctx->U32);
+    cudaFree(ctx->U64f);
+    cudaFree(ctx->U32f);
     cudaFree(ctx->C64);
     cudaFree(ctx->C32);
     cudaFree(ctx->U16);
@@ -642,7 +644,14 @@ ddrw_status ddrw_volume(ddrw_ctx *ctx, long *n)
 
 static ddrw_status rebuild(ddrw_ctx *ctx)
 {
+    if (ctx->cut > 0 && ctx->U64f) {  // the clover term comes from the full field's links
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(ctx->U64, ctx->U64f, sizeof(double2) * 36 * (size_t)ctx->V,
+                                        cudaMemcpyDeviceToDevice, ctx->stream));
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(ctx->U32, ctx->U32f, sizeof(float4) * 12 * (size_t)ctx->V,
+                                        cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     build_clover(ctx);
+    if (ctx->cut > 0) cut_links(ctx);
     build_bw_links(ctx);
     DDRW_CUDA_CHECK(cudaGetLastError());
     // 16-bit copies of the two-row links and the clover term for the FP16 / BF16 inner solves
@@ -672,6 +681,16 @@ ddrw_status ddrw_load_gauge(ddrw_ctx *ctx, const double *U)
     if (st) return st;
     pack_gauge(ctx, (const double *)dU);
     DDRW_CUDA_CHECK(cudaGetLastError());
+    if (ctx->cut > 0) {  // keep the full field's links for the clover term
+        if (!ctx->U64f && cudaMalloc(&ctx->U64f, sizeof(double2) * 36 * (size_t)ctx->V) != cudaSuccess)
+            return set_error(ctx, DDRW_ENOMEM, "links of the full field");
+        if (!ctx->U32f && cudaMalloc(&ctx->U32f, sizeof(float4) * 12 * (size_t)ctx->V) != cudaSuccess)
+            return set_error(ctx, DDRW_ENOMEM, "links of the full field");
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(ctx->U64f, ctx->U64, sizeof(double2) * 36 * (size_t)ctx->V,
+                                        cudaMemcpyDeviceToDevice, ctx->stream));
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(ctx->U32f, ctx->U32, sizeof(float4) * 12 * (size_t)ctx->V,
+                                        cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     ctx->have_gauge = true;
     st = rebuild(ctx);
     // the staging buffer for the gauge field is large and used once: release it
@@ -707,6 +726,17 @@ ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, dou
     ctx->tol_outer = tol_outer;
     ctx->tol_block = tol_block;
     ctx->maxiter = maxiter;
+    return DDRW_OK;
+}
+
+ddrw_status ddrw_set_dirichlet(ddrw_ctx *ctx, int cut)
+{
+    if (!ctx) return DDRW_EINVAL;
+    if (ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "ddrw_set_dirichlet must precede ddrw_load_gauge");
+    if (cut < 0 || (cut > 0 && cut % ctx->l != 0)) return set_error(ctx, DDRW_EINVAL, "cut must be a multiple of the block length");
+    for (int mu = 0; mu < 4 && cut > 0; mu++)
+        if (ctx->dims[mu] % cut) return set_error(ctx, DDRW_EINVAL, "cut must divide every lattice dimension");
+    ctx->cut = cut;
     return DDRW_OK;
 }
 

@@ -64,6 +64,51 @@ __global__ void k_scatter_cols(const double2 *__restrict__ Y, long V, int vbh, i
     S[(size_t)kb * n * n + (size_t)(j0 + r) * n + i] = Y[(long)r * 12 * V + (long)a * V + (long)(k0 + kb) * vbh + h];
 }
 
+// ----------------------------------------------------------------------------- Dirichlet cut
+
+// zero the links U_mu(x) with x_mu = cut - 1 mod cut (FP64 full and FP32 two-row copies)
+template <int BL>
+__global__ void k_cut_links(GeomDev g, int cut, double2 *U64, float4 *U32)
+{
+    const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    Site<BL> st;
+    decode_site<BL>(s, g, st);
+    const int *o = g.blk_org + st.blk * 4;
+    for (int mu = 0; mu < 4; mu++) {
+        if ((o[mu] + st.c[mu]) % cut != cut - 1) continue;
+        for (int k = 0; k < 9; k++) U64[(long)(mu * 9 + k) * g.V + s] = make_double2(0.0, 0.0);
+        for (int k = 0; k < 3; k++) U32[(long)(mu * 3 + k) * g.V + s] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// the FP64 links in the boundary layout: out[(lex * 4 + mu) * 9 + k] = U64[(mu * 9 + k) V + s]
+template <int BL>
+__global__ void k_gauge_lex(GeomDev g, const double2 *U64, double2 *out)
+{
+    const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.V) return;
+    Site<BL> st;
+    decode_site<BL>(s, g, st);
+    const long x = lex_index<BL>(st, g);
+    for (int mu = 0; mu < 4; mu++)
+        for (int k = 0; k < 9; k++) out[(x * 4 + mu) * 9 + k] = U64[(long)(mu * 9 + k) * g.V + s];
+}
+
+#define DISPATCH_L(ctx, KERNEL, ...)                                                                    \
+    do {                                                                                                \
+        const unsigned gr__ = (unsigned)(((ctx)->V + 255) / 256);                                       \
+        ++(ctx)->launches;                                                                              \
+        switch ((ctx)->l) {                                                                             \
+        case 2: KERNEL<2><<<gr__, 256, 0, (ctx)->stream>>>(__VA_ARGS__); break;                         \
+        case 4: KERNEL<4><<<gr__, 256, 0, (ctx)->stream>>>(__VA_ARGS__); break;                         \
+        case 6: KERNEL<6><<<gr__, 256, 0, (ctx)->stream>>>(__VA_ARGS__); break;                         \
+        default: KERNEL<8><<<gr__, 256, 0, (ctx)->stream>>>(__VA_ARGS__); break;                        \
+        }                                                                                               \
+    } while (0)
+
+void gauge_to_lex(ddrw_ctx *ctx, double2 *out) { DISPATCH_L(ctx, k_gauge_lex, geom_dev(ctx), ctx->U64, out); }
+
 // ----------------------------------------------------------------------------- det A_oo
 
 // log |det| and sign of a 6x6 complex matrix by LU with partial pivoting (in place)
@@ -277,6 +322,8 @@ __global__ void __launch_bounds__(LU_NT) k_lu_logdet(int n, double2 *mats, doubl
 
 }  // namespace
 
+void cut_links(ddrw_ctx *ctx) { DISPATCH_L(ctx, k_cut_links, geom_dev(ctx), ctx->cut, ctx->U64, ctx->U32); }
+
 // log |det D_k(m)| and sign for all blocks (host vectors, library block numbering)
 static ddrw_status block_logdets(ddrw_ctx *ctx, double m, std::vector<double> &logdet, std::vector<double> &sign)
 {
@@ -409,6 +456,55 @@ ddrw_status ddrw_block_factor(ddrw_ctx *ctx, double *log_w_blk)
     for (size_t k = 0; k < l1.size(); k++) acc += 2.0 * (l2[k] - l1[k]);
     *log_w_blk = acc;
     return DDRW_OK;
+}
+
+// The block factor of Eq. 7 for blocks too large for a dense determinant, by the nested
+// decomposition of Sec. 2.2 (caption of Fig. 2): each block's Dirichlet operator D_k is cut into
+// sub-blocks of length lsub (a black/white checkerboard inside the block), so that
+//   det D_k = det Shat_k * prod_{sub in k} det D_sub,
+// Shat_k the Schur complement of D_k with respect to its sub-blocks (Sec. 1).  The sub-block
+// determinants are exact (ddrw_block_factor on sub-blocks); the product over the blocks of
+// det Shat_k^2(m2) / det Shat_k^2(m1) is the global factor of the direct sum of the blocks' Dirichlet
+// operators with sub-block domain decomposition, and it is estimated stochastically with Eq. 3
+// (nhit noise vectors) -- the same estimator as W_gl, on an auxiliary context: the same lattice
+// and field, blocks of length lsub, every hop across a face of the original blocks removed
+// (ddrw_set_dirichlet) while the clover term stays the full field's.
+ddrw_status ddrw_block_factor_nested(ddrw_ctx *ctx, int lsub, int nhit, uint64_t seed, double *out, double *exponents,
+                                     double *rel_var)
+{
+    if (!ctx || !out || nhit <= 0) return set_error(ctx, DDRW_EINVAL, "bad argument");
+    if (!ctx->have_gauge) return set_error(ctx, DDRW_ESTATE, "no gauge field loaded");
+    if (ctx->cut) return set_error(ctx, DDRW_EINVAL, "the context is itself cut into Dirichlet boxes");
+    if (lsub < 2 || lsub > 6 || lsub % 2 || ctx->l % lsub || (ctx->l / lsub) % 2)
+        return set_error(ctx, DDRW_EINVAL, "lsub must be 2, 4 or 6 with an even number of sub-blocks per block side");
+    cudaSetDevice(ctx->device);
+    // the field in the boundary layout, from the context's FP64 links (device buffer)
+    double2 *lex = nullptr;
+    if (cudaMalloc(&lex, sizeof(double2) * 36 * (size_t)ctx->V) != cudaSuccess)
+        return set_error(ctx, DDRW_ENOMEM, "gauge field copy");
+    gauge_to_lex(ctx, lex);
+    ddrw_status st = sync(ctx);
+    ddrw_ctx *aux = nullptr;
+    const int blk[4] = {lsub, lsub, lsub, lsub};
+    double fx = 0.0, lw = 0.0;
+    if (!st) st = ddrw_create(&aux, ctx->dims, blk, ctx->device, ctx->stream);
+    if (!st) st = ddrw_set_dirichlet(aux, ctx->l);
+    if (!st) st = ddrw_set_params(aux, ctx->csw, ctx->m1, ctx->m2, ctx->antiperiodic);
+    if (!st) st = ddrw_load_gauge(aux, (const double *)lex);
+    if (!st) st = ddrw_set_solver(aux, ctx->prec, ctx->tol_outer, ctx->tol_block, ctx->maxiter);
+    if (!st) st = ddrw_block_factor(aux, &fx);
+    if (!st) {
+        st = ddrw_estimate(aux, nhit, seed, 0, nullptr, exponents, &lw, rel_var, nullptr, nullptr);
+        if (st == DDRW_ENOCONV) st = DDRW_OK, lw = NAN;
+    }
+    if (st && aux) ctx->err = std::string("nested block factor: ") + ddrw_last_error(aux);
+    if (aux) ddrw_destroy(aux);
+    cudaFree(lex);
+    if (st) return st;
+    out[0] = fx + lw;
+    out[1] = fx;
+    out[2] = lw;
+    return lw == lw ? DDRW_OK : set_error(ctx, DDRW_ENOCONV, "nested block factor: a solve missed its tolerance");
 }
 
 }  // extern "C"

@@ -126,6 +126,12 @@ struct ddrw_ctx {
     int sap_ncy = 4, sap_nmr = 4, sap_nkv = 8;
     int sap_last_iters = 0;
 
+    // Dirichlet cut (ddrw_set_dirichlet): hops across the faces of cut^4 boxes removed from the
+    // hopping term after the clover term is built from the full field, whose links stay in U64f / U32f
+    int cut = 0;
+    double2 *U64f = nullptr;
+    float4 *U32f = nullptr;
+
     // resident fields
     double2 *U64 = nullptr;  // [4][9][V]
     float4 *U32 = nullptr;   // [4][3][V] two-row
@@ -283,6 +289,7 @@ inline const void *clover_for(const ddrw_ctx *ctx, int id)
 }
 
 void pack_gauge(ddrw_ctx *ctx, const double *Ulex);  // fills U64 and U32
+void cut_links(ddrw_ctx *ctx);                       // zeroes U64 / U32 links across the cut faces
 void build_clover(ddrw_ctx *ctx);                    // fills C64 and C32 from U64
 void build_inverse(ddrw_ctx *ctx, double m, MassInv &mi);
 

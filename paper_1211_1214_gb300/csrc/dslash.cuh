@@ -313,6 +313,144 @@ __global__ void __launch_bounds__(256, (ROLL == 4 || ROLL == 7) ? 3 : (ROLL == 5
     for (int r = 0; r < NR; r++) P::store_spinor(a.out + roff + r * a.rstride, g.V, s, acc[r]);
 }
 
+// ---- pipelined form (FP32 storage, all hops, one right-hand side per thread): the neighbour
+// spinor and the link of every hop are brought into a two-slot ring in shared memory with 16-byte
+// asynchronous copies (cp.async), two hops ahead of the arithmetic, so that the loads in flight
+// hold no registers and each thread keeps two hops' worth of memory requests outstanding.  The
+// neighbours come from the neighbour table, the backward links from their copy stored at the site
+// (coalesced).  Ring layout: [slot][plane 0-5 spinor, 6-8 link][thread], 16-byte elements.
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+inline size_t pipe_smem(int nthreads) { return (size_t)2 * 9 * nthreads * 16; }
+
+// issue the copies of hop q (2 mu + backward) of site s into ring slot q % 2
+__device__ __forceinline__ void pipe_issue(float4 *ring, int nth, int tid, int q, int e, int s, long V, const float4 *in,
+                                           const float4 *U, const float4 *Ubw)
+{
+    float4 *dst = ring + (long)((q & 1) * 9) * nth + tid;
+    const int n = e & NBR_IDX, mu = q >> 1;
+#pragma unroll
+    for (int k = 0; k < 6; k++) cp_async16(dst + k * nth, in + k * V + n);
+    const float4 *L = ((q & 1) ? Ubw : U) + (long)mu * 3 * V + s;
+#pragma unroll
+    for (int k = 0; k < 3; k++) cp_async16(dst + (6 + k) * nth, L + k * V);
+    cp_async_commit();
+}
+
+// hop Q from its ring slot: acc += (1 -+ g_mu) U^(dag) in(x +- mu), then refill the slot with hop Q + 2
+template <int Q>
+__device__ __forceinline__ void pipe_hop(float4 *ring, int nth, int tid, const int (&nb)[8], int s, long V,
+                                         const float4 *in, const float4 *U, const float4 *Ubw, int tsign,
+                                         Spinor<float> &acc)
+{
+    constexpr int MU = Q >> 1;
+    if (Q < 7) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    const float4 *src = ring + (long)((Q & 1) * 9) * nth + tid;
+    Spinor<float> p;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        const float4 v = src[k * nth];
+        p.v[(2 * k) / 3][(2 * k) % 3] = {v.x, v.y};
+        p.v[(2 * k + 1) / 3][(2 * k + 1) % 3] = {v.z, v.w};
+    }
+    PrecS::URaw ur;
+#pragma unroll
+    for (int k = 0; k < 3; k++) ur.e[k] = src[(6 + k) * nth];
+    Link<float> L;
+    PrecS::decode_link(ur, L);
+    Half<float> h, w;
+    if ((Q & 1) == 0) {
+        project<MU, -1>(p, h);
+        link_mul(L, h, w);
+    } else {
+        project<MU, +1>(p, h);
+        link_dag_mul(L, h, w);
+    }
+    if (nb[Q] < 0 && tsign < 0)
+#pragma unroll
+        for (int x = 0; x < 2; x++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) w.v[x][c] = -w.v[x][c];
+    if ((Q & 1) == 0) reconstruct_add<MU, -1>(acc, w);
+    else reconstruct_add<MU, +1>(acc, w);
+    if (Q + 2 < 8) pipe_issue(ring, nth, tid, Q + 2, nb[(Q + 2) & 7], s, V, in, U, Ubw);
+}
+
+template <int BL, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_dslash_pipe(GeomDev g, DsArgs<PrecS> a)
+{
+    using R = float;
+    extern __shared__ __align__(16) float4 ring[];
+    const int nth = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int ncg = a.nrhs / (int)blockDim.y;
+    const int grp = (blockIdx.x % ncg) * blockDim.y + threadIdx.y;
+    const long tile = blockIdx.x / ncg;
+    const long nper = (long)a.nblk * BlockShape<BL>::VBH;
+    const long i = tile * blockDim.x + threadIdx.x;
+    if (i >= nper * a.npar) return;  // no barrier below: threads past the end may leave
+    const long roff = (long)grp * a.rstride;
+    const int pp = (int)(i / nper);
+    const int s = (int)((long)(a.par0 + pp) * g.vh + (long)a.blk0 * BlockShape<BL>::VBH + (i - pp * nper));
+    const long V = g.V;
+    Spinor<R> acc;
+    zero(acc);
+    if (a.beta != R(0)) {
+        const float4 *in = a.in + roff;
+        const int4 n0 = g.nbr[s], n1 = g.nbr[V + s];
+        const int nb[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+        pipe_issue(ring, nth, tid, 0, nb[0], s, V, in, a.U, a.Ubw);
+        pipe_issue(ring, nth, tid, 1, nb[1], s, V, in, a.U, a.Ubw);
+        pipe_hop<0>(ring, nth, tid, nb, s, V, in, a.U, a.Ubw, g.tsign, acc);
+        pipe_hop<1>(ring, nth, tid, nb, s, V, in, a.U, a.Ubw, g.tsign, acc);
+        pipe_hop<2>(ring, nth, tid, nb, s, V, in, a.U, a.Ubw, g.tsign, acc);
+        pipe_hop<3>(ring, nth, tid, nb, s, V, in, a.U, a.Ubw, g.tsign, acc);
+        pipe_hop<4>(ring, nth, tid, nb, s, V, in, a.U, a.Ubw, g.tsign, acc);
+        pipe_hop<5>(ring, nth, tid, nb, s, V, in, a.U, a.Ubw, g.tsign, acc);
+        pipe_hop<6>(ring, nth, tid, nb, s, V, in, a.U, a.Ubw, g.tsign, acc);
+        pipe_hop<7>(ring, nth, tid, nb, s, V, in, a.U, a.Ubw, g.tsign, acc);
+        scale(acc, a.beta);
+    }
+    if (a.diag) {
+        const float4 *x = a.x + roff;
+#pragma unroll
+        for (int ch = 0; ch < 2; ch++) {
+            R c[36];
+            if (a.diag == 1) PrecS::load_clover(a.Cl, V, s, ch, c);
+            cpx<R> v6[6], o6[6];
+            PrecS::load_chiral(x, (int)V, s, ch, v6);
+            if (a.diag == 1) herm6_mul<R>(c, a.mass4[grp / a.rpm], v6, o6);
+            else
+#pragma unroll
+                for (int k = 0; k < 6; k++) o6[k] = v6[k];
+#pragma unroll
+            for (int k = 0; k < 6; k++) acc.v[2 * ch + k / 3][k % 3] = acc.v[2 * ch + k / 3][k % 3] + a.alpha * o6[k];
+        }
+    }
+    if (a.post) {
+        const float4 *Ai = a.Ainv[grp / a.rpm];
+#pragma unroll
+        for (int ch = 0; ch < 2; ch++) {
+            R c[36];
+            PrecS::load_clover(Ai, V, s, ch, c);
+            cpx<R> v6[6], o6[6];
+#pragma unroll
+            for (int k = 0; k < 6; k++) v6[k] = acc.v[2 * ch + k / 3][k % 3];
+            herm6_mul<R>(c, R(0), v6, o6);
+#pragma unroll
+            for (int k = 0; k < 6; k++) acc.v[2 * ch + k / 3][k % 3] = o6[k];
+        }
+    }
+    PrecS::store_spinor(a.out + roff, (int)V, s, acc);
+}
+
 // launch configuration of one stencil launch
 struct DsConfig {
     int nr = 1;    // right-hand sides per thread
@@ -323,7 +461,9 @@ struct DsConfig {
                    // 1: forward and backward hops share the direction bodies (smaller code);
                    // 2 / 3: batched loads of 4 / 8 hops before their arithmetic (nr = 1); 4 / 5:
                    // unrolled with at most 85 / 128 registers, more warps per SM (nr = 1 / nr <= 2);
-                   // 6 / 7: 5 / 4 with the neighbours from the neighbour table (nr <= 2 / nr = 1)
+                   // 6 / 7: 5 / 4 with the neighbours from the neighbour table (nr <= 2 / nr = 1);
+                   // 9 / 10: pipelined (FP32 storage, nr = 1): neighbour spinors and links two
+                   // hops ahead through a shared-memory ring, at least 2 / 3 CTAs per SM
 };
 
 template <class P, int BL>
@@ -374,7 +514,25 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
                         (c.npar == 1 || nper % cfg.nt == 0) && cfg.nt <= 128;
         if (!ok) cfg.nr = 1, cfg.nw = 1, cfg.roll = 5;
     }
+    if (cfg.roll == 9 || cfg.roll == 10) {
+        const bool ok = std::is_same<P, PrecS>::value && c.hopsel == 0 && g.nbr && a.Ubw && cfg.nr == 1;
+        if (!ok) cfg.nr = 1, cfg.nw = 1, cfg.roll = 5;
+    }
     if constexpr (std::is_same<P, PrecS>::value) {
+        if (cfg.roll == 9 || cfg.roll == 10) {
+            const int nth = cfg.nt * cfg.nw;
+            const size_t smem = pipe_smem(nth);
+            unsigned grid = (unsigned)(((n + cfg.nt - 1) / cfg.nt) * (c.nrhs / cfg.nw));
+            ++ctx->launches;
+            if (cfg.roll == 9) {
+                cudaFuncSetAttribute(k_dslash_pipe<BL, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipe_smem(256));
+                k_dslash_pipe<BL, 2><<<grid, dim3((unsigned)cfg.nt, (unsigned)cfg.nw), smem, ctx->stream>>>(g, a);
+            } else {
+                cudaFuncSetAttribute(k_dslash_pipe<BL, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipe_smem(256));
+                k_dslash_pipe<BL, 3><<<grid, dim3((unsigned)cfg.nt, (unsigned)cfg.nw), smem, ctx->stream>>>(g, a);
+            }
+            return;
+        }
         if (cfg.roll == 8) {
             const int nslot = (c.nrhs + a.rpm - 1) / a.rpm;
             static bool attr = false;  // per block length: the kernel may take up to STAGED_SMEM_MAX

@@ -26,7 +26,7 @@ namespace ddrw {
 // right-hand sides per thread each hop code form supports
 static bool form_allowed(int nr, int roll)
 {
-    if (roll < 0 || roll > 8) return false;
+    if (roll < 0 || roll > 10) return false;
     if ((roll >= 2 && roll <= 4) || roll >= 7) return nr == 1;
     if (roll == 5 || roll == 6) return nr <= 2;
     return true;
@@ -64,12 +64,12 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
     DsConfig best = def;
     float best_ms = 1e30f;
     const int nrs[3] = {1, 2, 4}, nts[3] = {64, 128, 256}, nws[2] = {1, 2}, nws8[4] = {1, 2, 4, 8};
-    for (int roll = 0; roll < 9; roll++)
+    for (int roll = 0; roll < 11; roll++)
     for (int nr : nrs) {
         // the batched and register-capped forms are for 32- and 16-bit storage: with FP64 data
-        // they spill; the staged form is for FP32 storage
+        // they spill; the staged and pipelined forms are for FP32 storage
         if (c.nrhs % nr || rpm % nr || (roll >= 2 && prec == 64) || !form_allowed(nr, roll) ||
-            (roll == 8 && prec != 32))
+            (roll >= 8 && prec != 32))
             continue;
         const int *nwl = roll == 8 ? nws8 : nws;
         const int nnw = roll == 8 ? 4 : 2;

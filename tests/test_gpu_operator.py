@@ -72,7 +72,8 @@ def test_apply_D_double_single(setup, m):
 @pytest.mark.parametrize("nr,nt,nw,roll", [(1, 64, 1, 0), (1, 64, 1, 1), (2, 128, 1, 0), (2, 128, 2, 1),
                                            (4, 32, 2, 0), (4, 256, 1, 1), (1, 32, 8, 1), (1, 128, 1, 2),
                                            (1, 64, 2, 3), (1, 256, 1, 4), (1, 128, 2, 5),
-                                           (2, 128, 1, 5), (1, 64, 1, 6), (2, 128, 1, 6), (1, 128, 2, 7)])
+                                           (2, 128, 1, 5), (1, 64, 1, 6), (2, 128, 1, 6), (1, 128, 2, 7),
+                                           (1, 64, 1, 9), (1, 128, 1, 10)])
 def test_every_stencil_configuration(setup, nr, nt, nw, roll):
     """Each pinned launch configuration of the all-hop stencil (right-hand sides per thread, CTA
     shape, hop code form, computed or tabulated neighbours) gives the oracle's operator on 4
@@ -110,9 +111,12 @@ def ainv_apply(lat, m, v):
                                       (binding.MIXED_FP32, (1, 64, 4, 8)), (binding.MIXED_FP32, (1, 128, 2, 8)),
                                       (binding.MIXED_FP32, (1, 32, 8, 8)), (binding.MIXED_FP16, None),
                                       (binding.MIXED_FP16, (1, 64, 1, 6)), (binding.MIXED_FP16, (1, 64, 4, 8)),
-                                      (binding.MIXED_BF16, None)],
+                                      (binding.MIXED_BF16, None), (binding.MIXED_FP32, (1, 64, 1, 9)),
+                                      (binding.MIXED_FP32, (1, 128, 2, 10)), (binding.MIXED_FP32, (1, 32, 8, 9)),
+                                      (binding.MIXED_FP16, (1, 64, 1, 9))],
                          ids=["s-tuned", "s-f5", "s-u2", "s-table", "s-staged64x4", "s-staged128x2",
-                              "s-staged32x8", "h-tuned", "h-table", "h-staged-falls-back", "b-tuned"])
+                              "s-staged32x8", "h-tuned", "h-table", "h-staged-falls-back", "b-tuned",
+                              "s-pipe64", "s-pipe128x2", "s-pipe32x8", "h-pipe-falls-back"])
 def test_apply_D_in_storage_precision(setup, prec, cfg, post):
     """One stencil launch in FP32 / FP16 / BF16 storage, in each launch form (computed or tabulated
     neighbours, links and clover terms staged in shared memory by bulk copies), against the oracle's
@@ -141,6 +145,27 @@ def test_apply_block(setup, rows, cols):
     ctx.apply_block(rows, cols, 0.045, torch.from_numpy(x).cuda(), y)
     ref = lat.apply(0.045, x, rows=rows, cols=cols)
     assert rel(y.cpu().numpy(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("cfg", [(1, 64, 1, 9), (1, 128, 2, 10), (1, 64, 1, 6)], ids=["pipe", "pipe3", "table"])
+def test_antiperiodic_time_fp32_forms(cfg):
+    """The time-boundary sign in the FP32 forms that read it from the neighbour table (one launch in
+    FP32 storage against the oracle's operator)."""
+    dims, l = (8, 4, 4, 4), 2
+    U = synth.gauge_field(dims, 0.3, seed=3)
+    ctx = binding.Context(dims, (l,) * 4)
+    try:
+        ctx.load_gauge(torch.from_numpy(U).cuda())
+        ctx.set_params(1.2, 0.1, 0.09, antiperiodic_t=True)
+        lat = oc.Lattice(dims, (l,) * 4, U, 1.2, antiperiodic_t=True)
+        x = synth.spinor_field(dims, seed=8, nrhs=2)
+        y = np.zeros_like(x)
+        ctx.stencil_config(*cfg)
+        ctx.apply_D_low(binding.MIXED_FP32, 0.1, x, y, nrhs=2)
+        for r in range(2):
+            assert rel(y[r], lat.apply(0.1, x[r])) < LOW_TOL[binding.MIXED_FP32]
+    finally:
+        ctx.close()
 
 
 @pytest.mark.parametrize("cfg", [None, (1, 64, 1, 6), (1, 64, 1, 7)], ids=["tuned", "table128", "table85"])

@@ -584,3 +584,64 @@ def test_log_block_factor_completes_the_determinant_ratio(c1):
         assert abs(got - want) <= 1e-9 * max(1.0, abs(want))
         # the block factor alone is not the whole ratio (the test is not vacuous)
         assert abs(ob.log_block_factor(c1, m1, m2) - want) > 1e-3
+
+
+# ---- nested decomposition of large blocks (Sec. 2.2, Fig. 2 caption): a block determinant is the
+# Schur complement of the block's Dirichlet operator with respect to its sub-blocks times the
+# sub-block determinants (oracle.blockdet.dirichlet_links / dirichlet_lattice)
+
+@pytest.fixture(scope="module")
+def boxes():
+    """8x4x4x4 lattice cut into two 4^4 Dirichlet boxes along t (hops across every box face,
+    including the periodic wrap in x, y, z, removed), as blocks of length 4 and 2."""
+    from oracle import blockdet as ob
+    dims, csw = (8, 4, 4, 4), 1.2
+    U = synth.gauge_field(dims, 0.3, seed=5)
+    full = oc.Lattice(dims, (4, 4, 4, 4), U, csw)
+    cut4 = ob.dirichlet_lattice(dims, (4, 4, 4, 4), U, csw, cut=4)
+    cut2 = ob.dirichlet_lattice(dims, (2, 2, 2, 2), U, csw, cut=4)
+    return dims, full, cut4, cut2
+
+
+def test_dirichlet_operator_is_the_direct_sum_of_the_box_operators(boxes):
+    """The cut operator keeps exactly the site terms (the clover term of the full field) and the
+    hops that stay inside a box, with the full operator's entries, and couples no two boxes."""
+    dims, full, cut4, cut2 = boxes
+    m = 0.07
+    Dc = od.dense_D(cut2, m).reshape(cut2.V, 12, cut2.V, 12).transpose(0, 2, 1, 3)  # [x][y][12][12]
+    D = od.dense_D(full, m).reshape(full.V, 12, full.V, 12).transpose(0, 2, 1, 3)
+    X = coords(dims)
+    keep = np.eye(full.V, dtype=bool)
+    for mu in range(4):
+        for d in (1, -1):
+            Y = X.copy()
+            Y[:, mu] = (Y[:, mu] + d) % dims[mu]
+            inside = (X[:, mu] // 4 == Y[:, mu] // 4) & (np.abs(X[:, mu] - Y[:, mu]) == 1)
+            y = ((Y[:, 0] * dims[1] + Y[:, 1]) * dims[2] + Y[:, 2]) * dims[3] + Y[:, 3]
+            keep[np.arange(full.V)[inside], y[inside]] = True
+    assert np.max(np.abs(Dc[keep] - D[keep])) < 1e-15
+    assert np.max(np.abs(Dc[~keep])) == 0.0
+    assert np.max(np.abs(D[~keep])) > 0.1  # the removed hops were there
+    for x in (0, 37, 200, 511):
+        assert np.max(np.abs(cut2.clover(x) - full.clover(x))) == 0.0
+
+
+def test_nested_block_determinant_equals_the_block_determinant(boxes):
+    """For the Dirichlet boxes D_k: sum_k log|det D_k| = sum over the 2^4 sub-blocks of
+    log|det D_sub| + log|det Dhat'| (Dhat' the Schur complement of the cut operator with respect
+    to the sub-blocks, Sec. 1); and for a mass pair the block factor of Eq. 7 equals the sub-block
+    factor times 1/det(Mh'^dag Mh'), Mh' the sub-block ratio matrix of the cut operator -- the
+    quantity the nested estimate samples."""
+    from oracle import blockdet as ob
+    dims, full, cut4, cut2 = boxes
+    for m in (0.07, -0.2):
+        ld4, _ = ob.block_logdets(cut4, m)
+        ld2, _ = ob.block_logdets(cut2, m)
+        _, lS = od.logdet(od.schur(cut2, m))
+        assert abs(ld4.sum() - (ld2.sum() + lS)) < 1e-9 * max(1.0, abs(ld4.sum()))
+    m1, m2 = 0.10, 0.06
+    exact = ob.log_block_factor(cut4, m1, m2)
+    sub = ob.log_block_factor(cut2, m1, m2)
+    schur_part = float(np.log(od.inv_det_MdagM(od.ratio_matrix(cut2, m1, m2))))
+    assert abs(exact - (sub + schur_part)) < 1e-9 * max(1.0, abs(exact))
+    assert abs(schur_part) > 1e-3 and abs(sub) > 1e-3  # both parts carry weight
