@@ -331,9 +331,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fig1", action="store_true",
                     help="run the synthetic Fig. 1 analogue (variance vs interpolation steps per operator) instead")
-    ap.add_argument("--outer-solver", choices=["sap", "bicgstab"], default="sap",
+    ap.add_argument("--outer-solver", choices=["sap", "bicgstab"], default="bicgstab",
                     help="Krylov method of the FP32 inner solves: Schwarz-preconditioned GCR or even-odd BiCGStab")
     ap.add_argument("--sap", default=None, help="ncy,nmr,nkv of the Schwarz-preconditioned GCR")
+    ap.add_argument("--block-solver", choices=["persistent", "krylov"], default="persistent",
+                    help="block solves: persistent kernel or the Krylov-loop BiCGStab on each colour")
     ap.add_argument("--stencil-config", default=None,
                     help="pin the stencil launch form nr,nt,nw,roll (ddrw_stencil_config) instead of autotuning")
     args = ap.parse_args()
@@ -381,6 +383,7 @@ def main():
     ctx.use_graphs(GRAPH_MODE)
     sap = [int(v) for v in args.sap.split(",")] if args.sap else [4, 4, 8]
     ctx.set_outer_solver(1 if args.outer_solver == "sap" else 0, *sap)
+    ctx.set_block_solver(1 if args.block_solver == "krylov" else 0)
     if args.stencil_config:
         ctx.stencil_config(*[int(v) for v in args.stencil_config.split(",")])
     nhit, m2s = w["nhit"], list(w["m2s"])

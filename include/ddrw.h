@@ -121,6 +121,16 @@ ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, dou
  * DDRW_EINVAL outside method 0..1, ncy 1..16, nmr 1..32, nkv 1..16. */
 ddrw_status ddrw_set_outer_solver(ddrw_ctx *ctx, int method, int ncy, int nmr, int nkv);
 
+/* How the block solves D_cc(m)^-1 of the mixed precisions run (Eq. 1; the four solves of r and the
+ * block solves of the Schur operator): method 0, the persistent kernel -- one CTA per (block,
+ * right-hand side) running the whole in-block even-odd BiCGStab with CTA-wide reductions; method 1,
+ * all blocks of the colour as one block-diagonal system in the graph-captured even-odd BiCGStab
+ * of the outer solver (tuned stencil launches restricted to the hops inside the blocks, scalars
+ * per right-hand side over the colour).  Both feed the same FP64 defect correction to tol_block;
+ * the FP64 path and whole-estimate graphs (ddrw_use_graphs mode 1) use method 0.  DDRW_EINVAL
+ * for another method. */
+ddrw_status ddrw_set_block_solver(ddrw_ctx *ctx, int method);
+
 /* out = M_SAP(m) in: one application of the Schwarz preconditioner of method 1 above (the
  * context's ncy and nmr) to nrhs full-lattice fields, evaluated on FP32 fields and widened to
  * FP64 (layouts as ddrw_apply_D).  With ncy = 1 and enough steps it is one block Gauss-Seidel

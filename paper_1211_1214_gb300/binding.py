@@ -22,7 +22,7 @@ _STATUS = {0: "DDRW_OK", 1: "DDRW_EINVAL", 2: "DDRW_ENOMEM", 3: "DDRW_ECUDA", 4:
 
 #: every entry point declared in include/ddrw.h
 EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", "ddrw_volume", "ddrw_load_gauge",
-           "ddrw_set_params", "ddrw_set_solver", "ddrw_set_outer_solver", "ddrw_set_dirichlet",
+           "ddrw_set_params", "ddrw_set_solver", "ddrw_set_outer_solver", "ddrw_set_block_solver", "ddrw_set_dirichlet",
            "ddrw_block_factor_nested", "ddrw_apply_sap", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
@@ -81,6 +81,7 @@ def load(path: str | None = None):
         "ddrw_set_outer_solver": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "ddrw_apply_sap": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_set_dirichlet": (st, [vp, ctypes.c_int]),
+        "ddrw_set_block_solver": (st, [vp, ctypes.c_int]),
         "ddrw_block_factor_nested": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, dp, dp, dp]),
         "ddrw_apply_D": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_apply_D_ds": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
@@ -320,6 +321,10 @@ class Context:
         self._check(self.L.ddrw_block_factor_nested(self._h, int(lsub), int(nhit), ctypes.c_uint64(seed),
                                                      _ptr(out), _ptr(e), _ptr(rv)), "ddrw_block_factor_nested")
         return float(out[0]), float(out[1]), float(out[2]), e, float(rv[0])
+
+    def set_block_solver(self, method):
+        """Block solves of the mixed precisions: 0 persistent kernel, 1 Krylov-loop BiCGStab."""
+        self._check(self.L.ddrw_set_block_solver(self._h, int(method)), "ddrw_set_block_solver")
 
     def set_dirichlet(self, cut):
         """Remove the hops across the faces of cut^4 boxes (before load_gauge)."""

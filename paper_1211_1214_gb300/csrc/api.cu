@@ -740,6 +740,14 @@ ddrw_status ddrw_set_dirichlet(ddrw_ctx *ctx, int cut)
     return DDRW_OK;
 }
 
+ddrw_status ddrw_set_block_solver(ddrw_ctx *ctx, int method)
+{
+    if (!ctx) return DDRW_EINVAL;
+    if (method < 0 || method > 1) return set_error(ctx, DDRW_EINVAL, "block solver method must be 0 or 1");
+    ctx->block_method = method;
+    return DDRW_OK;
+}
+
 ddrw_status ddrw_set_outer_solver(ddrw_ctx *ctx, int method, int ncy, int nmr, int nkv)
 {
     if (!ctx) return DDRW_EINVAL;

@@ -104,7 +104,18 @@ static ddrw_status low_cycle(ddrw_ctx *ctx, int colour, const MassSet &ms, const
     a.tol2_dev = tol2_dev;
     a.maxiter = maxiter;
     a.stat = stat;
-    launch_block(ctx, a, nrhs);
+    if (ctx->block_method == 1 && !tol2_dev) {
+        // all blocks of the colour as one block-diagonal system in the Krylov-loop BiCGStab
+        // (tuned stencil launches, graph-captured loop); per right-hand side the colour's residual
+        int it = 0;
+        std::vector<double> th(nrhs, tol_inner * tol_inner);
+        if ((st = colour_bicgstab(ctx, P::ID, ms, bl, el, nrhs, th, maxiter, &it, colour))) return st;
+        int hs[2] = {it, 0};
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(stat, hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
+        DDRW_SYNC(ctx);  // hs is stack memory
+    } else {
+        launch_block(ctx, a, nrhs);
+    }
     if (first) zero_colour64(ctx, x, colour, nrhs);
     for (int p = 0; p < 2; p++) add_low<P>(ctx, colour_range(ctx, colour, p, nrhs, rs64), rsl, (const E *)el, x, scale_d + nrhs);
     return DDRW_OK;

@@ -125,6 +125,9 @@ struct ddrw_ctx {
     int outer_method = 0;
     int sap_ncy = 4, sap_nmr = 4, sap_nkv = 8;
     int sap_last_iters = 0;
+    // block solves of the mixed precisions: 0 the persistent kernel (one CTA per block and right-hand
+    // side), 1 the Krylov-loop BiCGStab on the colour's blocks as one block-diagonal system
+    int block_method = 0;
 
     // Dirichlet cut (ddrw_set_dirichlet): hops across the faces of cut^4 boxes removed from the
     // hopping term after the clover term is built from the full field, whose links stay in U64f / U32f
@@ -335,6 +338,10 @@ ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const do
 ddrw_status full_solve_dc_prepare(ddrw_ctx *ctx, int nrhs);
 ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, double2 *x, int nrhs, double tol,
                          int maxiter, ddrw_prec prec, SolveStats *stats);
+// the block operator of one colour by the Krylov-loop even-odd BiCGStab (solver.cu), fields in the
+// storage of policy id pid (32, 16 = FP16, 17 = BF16)
+ddrw_status colour_bicgstab(ddrw_ctx *ctx, int pid, const MassSet &ms, const void *b, void *x, int nrhs,
+                            const std::vector<double> &thresh, int maxiter, int *iters, int colour);
 // Schwarz-preconditioned flexible GCR on FP32 fields (sap.cu): x = D(ms)^-1 b on the full lattice
 // until |b - D x|^2 <= thresh[r] per right-hand side; adds its iterations to *iters
 bool sap_supported(const ddrw_ctx *ctx);

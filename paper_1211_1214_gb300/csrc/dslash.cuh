@@ -504,8 +504,11 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
 {
     GeomDev g = geom_dev(ctx);
     long n = (long)c.npar * c.nblk * BlockShape<BL>::VBH;
-    // launches that are not tuned (block-restricted hops, double-single) take one row
-    if (c.hopsel != 0 || std::is_same<P, PrecDD>::value) cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
+    // double-single launches and hops between blocks take one row; hops inside blocks take the
+    // unrolled, register-capped or table form with one right-hand side per thread
+    if (c.hopsel == 2 || std::is_same<P, PrecDD>::value) cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
+    if (c.hopsel == 1 && (cfg.nr != 1 || (cfg.roll != 0 && cfg.roll != 5 && cfg.roll != 6))) cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
+    if (c.hopsel == 1 && cfg.roll == 6 && !g.nbr) cfg.roll = 5;
     if (cfg.roll >= 6 && cfg.roll <= 7 && !g.nbr) cfg.roll = 11 - cfg.roll;  // no table: the computed-neighbour twin
     if (cfg.roll == 8) {
         // the staged form: FP32 storage, all hops, a tile never straddles the two parities
@@ -573,7 +576,9 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
             default: k_dslash<P, BL, 0, 1><<<grid, blk, 0, ctx->stream>>>(g, a); break;
             }
         } else if (c.hopsel == 1) {
-            k_dslash<P, BL, 1, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
+            if (cfg.roll == 5) k_dslash<P, BL, 1, 1, 5><<<grid, blk, 0, ctx->stream>>>(g, a);
+            else if (cfg.roll == 6) k_dslash<P, BL, 1, 1, 6><<<grid, blk, 0, ctx->stream>>>(g, a);
+            else k_dslash<P, BL, 1, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
         } else {
             k_dslash<P, BL, 2, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
         }
@@ -612,7 +617,7 @@ void launch_bl(ddrw_ctx *ctx, const DslashCall &c)
     DsConfig cfg;
     constexpr bool split = std::is_same<P, PrecDD>::value;
     if constexpr (!split)
-        if (c.hopsel == 0) cfg = tuned_config(ctx, c, P::ID, BL, &run_cfg<P, BL>);
+        if (c.hopsel != 2) cfg = tuned_config(ctx, c, P::ID, BL, &run_cfg<P, BL>);
     int kind = split ? PROF_DSLASH_DS
                      : P::ID < 32 ? PROF_DSLASH16 + (c.hopsel != 0)
                                   : (sizeof(R) == 8 ? PROF_DSLASH64 : PROF_DSLASH32) + (c.hopsel != 0 ? 2 : 0);

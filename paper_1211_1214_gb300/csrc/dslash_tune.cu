@@ -42,7 +42,7 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
         if (p.roll != 8 && (c.nrhs % (p.nr * p.nw) || rpm % (p.nr * p.nw))) p.nr = 1, p.nw = 1;
         return p;
     }
-    std::array<int, 8> key = {prec, bl, c.npar, c.nrhs, c.diag, c.post, rpm, c.beta != 0.0};
+    std::array<int, 8> key = {prec, bl, c.npar, c.nrhs, c.diag, c.post, rpm, (c.beta != 0.0) + 2 * c.hopsel};
     auto it = ctx->tune.find(key);
     if (it != ctx->tune.end()) return DsConfig{it->second.nr, it->second.nt, it->second.nw, it->second.roll};
 
@@ -71,6 +71,9 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
         if (c.nrhs % nr || rpm % nr || (roll >= 2 && prec == 64) || !form_allowed(nr, roll) ||
             (roll >= 8 && prec != 32))
             continue;
+        // launches restricted to the hops inside the blocks come in the unrolled, register-capped
+        // and table forms with one right-hand side per thread
+        if (c.hopsel != 0 && (nr != 1 || (roll != 0 && roll != 5 && roll != 6))) continue;
         const int *nwl = roll == 8 ? nws8 : nws;
         const int nnw = roll == 8 ? 4 : 2;
         for (int iw = 0; iw < nnw; iw++)
@@ -151,9 +154,9 @@ ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len)
         const auto &k = kv.first;
         char line[200];
         snprintf(line, sizeof line,
-                 "fp%d l=%d npar=%d nrhs=%d diag=%d post=%d rpm=%d hop=%d -> nr=%d nt=%d nw=%d roll=%d ms=%.4f\n", k[0],
-                 k[1], k[2], k[3], k[4], k[5], k[6], k[7], kv.second.nr, kv.second.nt, kv.second.nw, kv.second.roll,
-                 kv.second.ms);
+                 "fp%d l=%d npar=%d nrhs=%d diag=%d post=%d rpm=%d hop=%d sel=%d -> nr=%d nt=%d nw=%d roll=%d ms=%.4f\n",
+                 k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7] & 1, k[7] >> 1, kv.second.nr, kv.second.nt, kv.second.nw,
+                 kv.second.roll, kv.second.ms);
         s += line;
     }
     if ((long)s.size() + 1 > len) return set_error(ctx, DDRW_EINVAL, "report buffer too small");

@@ -59,7 +59,9 @@ template <class P> void stencil(ddrw_ctx *ctx, const DslashCall &c)
     }
 }
 
-template <class P> DslashCall base_call(const ddrw_ctx *ctx, const MassSet &ms, int nrhs, long rs)
+// colour < 0: the whole lattice (all hops); colour 0 / 1: the blocks of that colour with the hops
+// inside the blocks only (the block operator D_bb / D_ww of Eq. 1)
+template <class P> DslashCall base_call(const ddrw_ctx *ctx, const MassSet &ms, int nrhs, long rs, int colour = -1)
 {
     DslashCall c;
     c.rstride = rs;
@@ -69,8 +71,9 @@ template <class P> DslashCall base_call(const ddrw_ctx *ctx, const MassSet &ms, 
         c.masses[k] = ms.m[k];
         c.Ainv[k] = ainv_for(ms.inv[k], P::ID);
     }
-    c.blk0 = 0;
-    c.nblk = ctx->nblk;
+    c.blk0 = colour < 0 ? 0 : colour * ctx->nblk_c;
+    c.nblk = colour < 0 ? ctx->nblk : ctx->nblk_c;
+    c.hopsel = colour < 0 ? 0 : 1;
     c.npar = 1;
     return c;
 }
@@ -78,16 +81,16 @@ template <class P> DslashCall base_call(const ddrw_ctx *ctx, const MassSet &ms, 
 // out_e = Mhat in_e  (tmp on odd sites)
 template <class P>
 void apply_mhat(ddrw_ctx *ctx, const MassSet &ms, int nrhs, long rs, const typename P::SElem *in,
-                typename P::SElem *tmp, typename P::SElem *out)
+                typename P::SElem *tmp, typename P::SElem *out, int colour = -1)
 {
-    DslashCall c = base_call<P>(ctx, ms, nrhs, rs);
+    DslashCall c = base_call<P>(ctx, ms, nrhs, rs, colour);
     c.in = in;
     c.out = tmp;
     c.beta = 1.0;
     c.post = 1;
     c.par0 = 1;
     stencil<P>(ctx, c);
-    DslashCall d = base_call<P>(ctx, ms, nrhs, rs);
+    DslashCall d = base_call<P>(ctx, ms, nrhs, rs, colour);
     d.in = tmp;
     d.x = in;
     d.out = out;
@@ -103,13 +106,13 @@ template <class P>
 static ddrw_status bicg_iteration(ddrw_ctx *ctx, const MassSet &ms, int nrhs, long rs, const VecRange &ev,
                                   typename P::SElem *x, typename P::SElem *r, typename P::SElem *rh,
                                   typename P::SElem *p, typename P::SElem *v, typename P::SElem *t,
-                                  typename P::SElem *tmp, KScal *sc)
+                                  typename P::SElem *tmp, KScal *sc, int colour = -1)
 {
     ddrw_status s2;
-    apply_mhat<P>(ctx, ms, nrhs, rs, p, tmp, v);
+    apply_mhat<P>(ctx, ms, nrhs, rs, p, tmp, v, colour);
     if ((s2 = Blas<P>::bicg_alpha(ctx, ev, rh, v, sc))) return s2;
     Blas<P>::bicg_s(ctx, ev, r, v, sc);
-    apply_mhat<P>(ctx, ms, nrhs, rs, r, tmp, t);
+    apply_mhat<P>(ctx, ms, nrhs, rs, r, tmp, t, colour);
     if ((s2 = Blas<P>::bicg_omega(ctx, ev, t, r, sc))) return s2;
     if ((s2 = Blas<P>::bicg_xr(ctx, ev, x, p, r, t, rh, sc))) return s2;
     Blas<P>::bicg_p(ctx, ev, p, r, v, sc);
@@ -117,10 +120,12 @@ static ddrw_status bicg_iteration(ddrw_ctx *ctx, const MassSet &ms, int nrhs, lo
 }
 
 // Inner even-odd BiCGStab in policy P: solve D x = b (full fields) until the even-odd residual of
-// right-hand side r satisfies ||r||^2 <= thresh[r].  Adds iterations to *iters.
+// right-hand side r satisfies ||r||^2 <= thresh[r].  Adds iterations to *iters.  With colour 0 or
+// 1 it solves the block operator D_cc of that colour instead (all its blocks as one block-diagonal
+// system, hops inside the blocks only): only the sites of that colour are read and written.
 template <class P>
 ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SElem *b, typename P::SElem *x, int nrhs,
-                        const std::vector<double> &thresh, int maxiter, int *iters)
+                        const std::vector<double> &thresh, int maxiter, int *iters, int colour = -1)
 {
     using E = typename P::SElem;
     const long rs = P::field_elems(ctx->V);
@@ -138,7 +143,7 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
     if ((st = workspace(ctx, "eo_kscal", sizeof(KScal) * nrhs, (void **)&sc))) return st;
 
     // btil_e = b_e + 1/2 H_eo A_oo^-1 b_o  (into r)
-    DslashCall c = base_call<P>(ctx, ms, nrhs, rs);
+    DslashCall c = base_call<P>(ctx, ms, nrhs, rs, colour);
     c.x = b;
     c.out = tmp;
     c.alpha = 1.0;
@@ -146,7 +151,7 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
     c.post = 1;
     c.par0 = 1;
     stencil<P>(ctx, c);
-    DslashCall d = base_call<P>(ctx, ms, nrhs, rs);
+    DslashCall d = base_call<P>(ctx, ms, nrhs, rs, colour);
     d.in = tmp;
     d.x = b;
     d.out = r;
@@ -163,12 +168,13 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
         h[k].maxiter = maxiter;
     }
     DDRW_CUDA_CHECK(cudaMemcpyAsync(sc, h.data(), sizeof(KScal) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
-    VecRange ev{ctx->V, 0, ctx->vh, rs, nrhs};
+    const long nc = (long)ctx->nblk_c * (ctx->vh / ctx->nblk);  // sites of one colour and parity
+    VecRange ev = colour < 0 ? VecRange{ctx->V, 0, ctx->vh, rs, nrhs} : VecRange{ctx->V, colour * nc, nc, rs, nrhs};
     if ((st = Blas<P>::bicg_init(ctx, ev, r, rh, p, x, sc))) return st;
 
     KScal *hs = (KScal *)ctx->h_pinned;
     const int check = sizeof(typename P::R) == 8 ? 1 : 4;
-    auto iteration = [&]() -> ddrw_status { return bicg_iteration<P>(ctx, ms, nrhs, rs, ev, x, r, rh, p, v, t, tmp, sc); };
+    auto iteration = [&]() -> ddrw_status { return bicg_iteration<P>(ctx, ms, nrhs, rs, ev, x, r, rh, p, v, t, tmp, sc, colour); };
     int it = 0;
     bool done = false;
     // first iterations eagerly: they tune the stencil launches and create every workspace
@@ -189,7 +195,7 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
         int *count;
         if ((st = workspace(ctx, "eo_graph_count", sizeof(int), (void **)&count))) return st;
         std::array<uintptr_t, 13 + 2 * MAXM> key{};
-        key[0] = P::ID;
+        key[0] = P::ID + 1000 * (colour + 1);  // the colour selects other launches
         key[1] = (uintptr_t)nrhs;
         key[2] = (uintptr_t)maxiter;
         const void *ptrs[9] = {r, rh, p, v, t, tmp, x, sc, count};
@@ -263,7 +269,7 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
     for (int k = 0; k < nrhs; k++) itmax = std::max(itmax, hs[k].iters);
     *iters += itmax;
     // x_o = A_oo^-1 (b_o + 1/2 H_oe x_e)
-    DslashCall e = base_call<P>(ctx, ms, nrhs, rs);
+    DslashCall e = base_call<P>(ctx, ms, nrhs, rs, colour);
     e.in = x;
     e.x = b;
     e.out = x;
@@ -275,6 +281,22 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
     stencil<P>(ctx, e);
     return DDRW_OK;
 }
+
+}  // namespace
+
+// the block operator D_cc of one colour solved by the Krylov-loop BiCGStab above, on fields in the
+// storage of policy id pid (32 FP32, 16 FP16, 17 BF16)
+ddrw_status colour_bicgstab(ddrw_ctx *ctx, int pid, const MassSet &ms, const void *b, void *x, int nrhs,
+                            const std::vector<double> &thresh, int maxiter, int *iters, int colour)
+{
+    switch (pid) {
+    case 32: return eo_bicgstab<PrecS>(ctx, ms, (const float4 *)b, (float4 *)x, nrhs, thresh, maxiter, iters, colour);
+    case 16: return eo_bicgstab<PrecH>(ctx, ms, (const PrecH::SElem *)b, (PrecH::SElem *)x, nrhs, thresh, maxiter, iters, colour);
+    default: return eo_bicgstab<PrecB>(ctx, ms, (const PrecB::SElem *)b, (PrecB::SElem *)x, nrhs, thresh, maxiter, iters, colour);
+    }
+}
+
+namespace {
 
 ddrw_status full_norms(ddrw_ctx *ctx, const double2 *f, int nrhs, std::vector<double> &out)
 {
