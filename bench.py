@@ -143,6 +143,35 @@ def fig1(args):
                       "variants": rows, "seconds": time.perf_counter() - t0}), flush=True)
 
 
+def block_factor(args, w, name):
+    """The exact block factor of Eq. 7 for the workload's blocks: dense block determinants where the
+    blocks are small enough (l <= 6), else the nested decomposition of Sec. 2.2 (4^4 sub-blocks
+    exact, the blocks' Schur complements with respect to them by Eq. 3 with N_hit noise vectors),
+    for the middle target mass; prints one JSON line with the parts and the time."""
+    import torch
+    from paper_1211_1214_gb300 import binding, synth
+    m2 = w["m2s"][len(w["m2s"]) // 2]
+    ctx = binding.Context(w["dims"], w["l"])
+    ctx.load_gauge(torch.from_numpy(synth.gauge_field(w["dims"], w["eps"], seed=1)).cuda())
+    ctx.set_params(w["csw"], w["m1"], m2)
+    ctx.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = {"metric": "log prod_k det D_k^2(m2) / det D_k^2(m1) (Eq. 7)", "workload": describe(name, w, "FP32"),
+           "m1": w["m1"], "m2": m2}
+    if w["l"] <= 6:
+        out.update(method="dense block determinants", log_block_factor=ctx.block_factor())
+    else:
+        tot, ex, sto, e, rv = ctx.block_factor_nested(4, w["nhit"], seed=2)
+        out.update(method="nested: exact 4^4 sub-block determinants x stochastic Schur factor (Eq. 3)",
+                   log_block_factor=tot, exact_sub_blocks=ex, stochastic_schur=sto, nhit=w["nhit"],
+                   stochastic_error=float(np.sqrt(rv / w["nhit"])), exponent_spread=float(np.std(e, ddof=1)))
+    torch.cuda.synchronize()
+    out["seconds"] = time.perf_counter() - t0
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def variance_check(E, RV, m2s, nhit, m1):
     """Per target mass: the sample relative variance of exp(-e_j) (Eq. 4 estimated from the
     samples) beside its small-dm expansion.  With X = Mh^dag Mh - 1, Eq. 4 gives
@@ -329,6 +358,8 @@ def main():
                     help="1: Krylov-loop graphs and whole estimate chunks as one graph; 2: Krylov-loop graphs only; 0: none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--block-factor", action="store_true",
+                    help="compute the block factor of Eq. 7 for the workload (nested decomposition for 8^4 blocks) instead")
     ap.add_argument("--fig1", action="store_true",
                     help="run the synthetic Fig. 1 analogue (variance vs interpolation steps per operator) instead")
     ap.add_argument("--outer-solver", choices=["sap", "bicgstab"], default="bicgstab",
@@ -349,6 +380,9 @@ def main():
         return
     if args.fig1:
         fig1(args)
+        return
+    if args.block_factor:
+        block_factor(args, w, name)
         return
 
     import torch

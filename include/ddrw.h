@@ -121,6 +121,13 @@ ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, dou
  * DDRW_EINVAL outside method 0..1, ncy 1..16, nmr 1..32, nkv 1..16. */
 ddrw_status ddrw_set_outer_solver(ddrw_ctx *ctx, int method, int ncy, int nmr, int nkv);
 
+/* With enable != 0 (the default) the FP32 even-odd BiCGStab of the full-lattice solves computes the
+ * inner products of alpha = rho / (rh, v) and omega = (t, s) / (t, t) in the epilogue of the stencil
+ * launch that writes v and t (one partial per warp of 32 sites, summed in FP64 in a fixed order by a
+ * small kernel) instead of re-reading v, t and s in separate reductions; 0 uses the separate
+ * reduction kernels.  Results differ only by the rounding of the sums. */
+ddrw_status ddrw_fuse_reductions(ddrw_ctx *ctx, int enable);
+
 /* How the block solves D_cc(m)^-1 of the mixed precisions run (Eq. 1; the four solves of r and the
  * block solves of the Schur operator): method 0, the persistent kernel -- one CTA per (block,
  * right-hand side) running the whole in-block even-odd BiCGStab with CTA-wide reductions; method 1,
@@ -285,8 +292,10 @@ ddrw_status ddrw_use_graphs(ddrw_ctx *ctx, int enable, long *graph_launches);
 /* Autotuner of the stencil launches: on the first launch of each shape (precision, block length,
  * parities, right-hand sides, diagonal/post modes) it times right-hand sides per thread {1,2,4},
  * sites per CTA row {64,128,256}, right-hand-side rows per CTA {1,2} and the hop code form
- * (unrolled, rolled, batched loads, register caps, neighbour table) with CUDA events and keeps the fastest.  enable = 0 uses a fixed choice; either call
- * clears the tuned table.  The report lists the tuned shapes, one per line. */
+ * (unrolled, rolled, batched loads, register caps, neighbour table) with CUDA events and keeps the fastest.  Tuned choices are
+ * also kept for the process, by device and lattice geometry, and reused by later contexts of the
+ * same geometry.  enable = 0 uses a fixed choice; either call clears the tuned tables of the context
+ * and of the process.  The report lists the tuned shapes, one per line. */
 ddrw_status ddrw_autotune(ddrw_ctx *ctx, int enable);
 ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
 

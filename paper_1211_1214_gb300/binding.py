@@ -22,7 +22,8 @@ _STATUS = {0: "DDRW_OK", 1: "DDRW_EINVAL", 2: "DDRW_ENOMEM", 3: "DDRW_ECUDA", 4:
 
 #: every entry point declared in include/ddrw.h
 EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", "ddrw_volume", "ddrw_load_gauge",
-           "ddrw_set_params", "ddrw_set_solver", "ddrw_set_outer_solver", "ddrw_set_block_solver", "ddrw_set_dirichlet",
+           "ddrw_set_params", "ddrw_set_solver", "ddrw_set_outer_solver", "ddrw_set_block_solver",
+           "ddrw_fuse_reductions", "ddrw_set_dirichlet",
            "ddrw_block_factor_nested", "ddrw_apply_sap", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
@@ -82,6 +83,7 @@ def load(path: str | None = None):
         "ddrw_apply_sap": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_set_dirichlet": (st, [vp, ctypes.c_int]),
         "ddrw_set_block_solver": (st, [vp, ctypes.c_int]),
+        "ddrw_fuse_reductions": (st, [vp, ctypes.c_int]),
         "ddrw_block_factor_nested": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, dp, dp, dp]),
         "ddrw_apply_D": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_apply_D_ds": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
@@ -321,6 +323,10 @@ class Context:
         self._check(self.L.ddrw_block_factor_nested(self._h, int(lsub), int(nhit), ctypes.c_uint64(seed),
                                                      _ptr(out), _ptr(e), _ptr(rv)), "ddrw_block_factor_nested")
         return float(out[0]), float(out[1]), float(out[2]), e, float(rv[0])
+
+    def fuse_reductions(self, enable=True):
+        """Inner products of the BiCGStab recurrence in the stencil epilogue (True) or separate kernels."""
+        self._check(self.L.ddrw_fuse_reductions(self._h, int(bool(enable))), "ddrw_fuse_reductions")
 
     def set_block_solver(self, method):
         """Block solves of the mixed precisions: 0 persistent kernel, 1 Krylov-loop BiCGStab."""

@@ -740,6 +740,14 @@ ddrw_status ddrw_set_dirichlet(ddrw_ctx *ctx, int cut)
     return DDRW_OK;
 }
 
+ddrw_status ddrw_fuse_reductions(ddrw_ctx *ctx, int enable)
+{
+    if (!ctx) return DDRW_EINVAL;
+    ctx->fuse_dots = enable != 0;
+    clear_graphs(ctx);  // captured iterations keep the kernels they were captured with
+    return DDRW_OK;
+}
+
 ddrw_status ddrw_set_block_solver(ddrw_ctx *ctx, int method)
 {
     if (!ctx) return DDRW_EINVAL;

@@ -226,6 +226,62 @@ __global__ void __launch_bounds__(NT) k_bicg_p(VecArgs<P> va, typename P::SElem 
         }
 }
 
+// alpha (MODE 1) or omega (MODE 2) from the per-warp partial sums a fused stencil epilogue wrote:
+// part[(r * nwt + j) * 3 + k], summed in FP64 in a fixed order (one CTA per right-hand side)
+template <int MODE>
+__global__ void __launch_bounds__(NT) k_bicg_fin(const double *part, long nwt, KScal *sc)
+{
+    __shared__ double sm[NT / 32][3];
+    const int r = blockIdx.x;
+    if (!sc[r].active) return;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (long j = threadIdx.x; j < nwt; j += NT) {
+        const double *pp = part + ((long)r * nwt + j) * 3;
+        v[0] += pp[0];
+        v[1] += pp[1];
+        v[2] += pp[2];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; k++) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 3; k++) sm[w][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double val[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < NT / 32; i++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) val[k] += sm[i][k];
+    KScal &s = sc[r];
+    if (MODE == 1) {  // alpha = rho / (rh, v)
+        const double den = val[0] * val[0] + val[1] * val[1];
+        if (den == 0.0 || !(den == den)) {
+            s.breakdown = 1;
+            s.active = 0;
+            s.alpha = make_double2(0.0, 0.0);
+            return;
+        }
+        s.alpha = make_double2((s.rho.x * val[0] + s.rho.y * val[1]) / den, (s.rho.y * val[0] - s.rho.x * val[1]) / den);
+    } else {  // omega = (t, s) / (t, t)
+        if (val[2] == 0.0 || !(val[2] == val[2])) {
+            s.breakdown = 2;
+            s.active = 0;
+            s.omega = make_double2(0.0, 0.0);
+            return;
+        }
+        s.omega = make_double2(val[0] / val[2], val[1] / val[2]);
+    }
+}
+
+void bicg_fin(ddrw_ctx *ctx, int mode, int nrhs, const double *part, long nwt, KScal *sc)
+{
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
+    ++ctx->launches;
+    if (mode == 1) k_bicg_fin<1><<<nrhs, NT, 0, ctx->stream>>>(part, nwt, sc);
+    else k_bicg_fin<2><<<nrhs, NT, 0, ctx->stream>>>(part, nwt, sc);
+}
+
 // ----------------------------------------------------------------------------- generic kernels
 
 // out[r] = sum |f|^2 over the range (FP64 result per right-hand side)

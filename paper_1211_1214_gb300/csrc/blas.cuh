@@ -105,6 +105,10 @@ __device__ bool grid_sum(double (&v)[K], double *part, unsigned *ticket)
     return false;
 }
 
+// alpha (mode 1) or omega (mode 2) of the BiCGStab recurrence from the per-warp partial sums of a
+// fused stencil epilogue (DslashCall::red), nwt partials of 3 doubles per right-hand side
+void bicg_fin(ddrw_ctx *ctx, int mode, int nrhs, const double *part, long nwt, KScal *sc);
+
 // partial-sum and ticket buffers of grid_sum for nrhs right-hand sides (at most 608 CTAs per
 // right-hand side and 4 doubles per CTA)
 ddrw_status reduce_ws(ddrw_ctx *ctx, int nrhs, double **part, unsigned **ticket);

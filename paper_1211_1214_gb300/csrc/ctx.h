@@ -128,6 +128,9 @@ struct ddrw_ctx {
     // block solves of the mixed precisions: 0 the persistent kernel (one CTA per block and right-hand
     // side), 1 the Krylov-loop BiCGStab on the colour's blocks as one block-diagonal system
     int block_method = 0;
+    // the BiCGStab inner products of alpha and omega fused into the epilogue of the stencil launch
+    // that writes v and t (FP32 storage, full lattice); off: separate reduction kernels
+    bool fuse_dots = true;
 
     // Dirichlet cut (ddrw_set_dirichlet): hops across the faces of cut^4 boxes removed from the
     // hopping term after the clover term is built from the full field, whose links stay in U64f / U32f
@@ -313,6 +316,12 @@ struct DslashCall {
     double alpha = 0.0, beta = 0.0;
     int diag = 0, post = 0, hopsel = 0;
     int par0 = 0, npar = 2, blk0 = 0, nblk = 0;
+    // fused inner products of the output (FP32 storage, all hops, one parity, one right-hand side
+    // per thread): red 1 -> conj(w) out, red 2 -> conj(out) x and |out|^2, per warp of 32 sites into
+    // red_part[(rhs * (n / 32) + warp) * 3 + k]
+    int red = 0;
+    const void *w = nullptr;
+    double *red_part = nullptr;
 };
 void dslash64(ddrw_ctx *ctx, const DslashCall &c);
 void dslash32(ddrw_ctx *ctx, const DslashCall &c);

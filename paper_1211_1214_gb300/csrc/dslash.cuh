@@ -44,6 +44,9 @@ template <class P> struct DsArgs {
     const typename P::UElem *Ubw;         // backward links U_mu(x - mu) stored at x (staged form)
     int *err;                             // device error flags (bit 0: a staging wait ran out)
     int stall_tx;                         // test switch: bytes announced on top of the staged copies
+    const typename P::SElem *w;           // fused inner products: the other vector of red 1
+    double *part;                         // per-warp partial sums [rhs][n / 32][3]
+    long nwt;                             // warps of 32 output sites per right-hand side (n / 32)
 };
 
 // ---- staged form (FP32 two-row links): one CTA covers a tile of consecutive output sites for all
@@ -221,7 +224,10 @@ constexpr size_t STAGED_SMEM_MAX = (size_t)62 * 128 * 16;
 // ROLL selects the hop code form: 0 unrolled, 1 rolled, 2 / 3 batched loads of 4 / 8 hops,
 // 4 / 5 unrolled compiled for at least 3 / 2 CTAs of 256 threads per SM (<= 85 / 128 registers),
 // 6 / 7 as 5 / 4 with the neighbours read from the neighbour table instead of computed
-template <class P, int BL, int HOPSEL, int NR, int ROLL = 0>
+// RED != 0 adds the inner products of the output to the epilogue (red 1: conj(w) out; red 2:
+// conj(out) x and |out|^2), one partial per warp of 32 sites, summed in FP64 by k_bicg_fin; the
+// launcher only fuses launches whose output sites fill whole CTAs (no thread leaves early)
+template <class P, int BL, int HOPSEL, int NR, int ROLL = 0, int RED = 0>
 __global__ void __launch_bounds__(256, (ROLL == 4 || ROLL == 7) ? 3 : (ROLL == 5 || ROLL == 6) ? 2 : 1)
     k_dslash(GeomDev g, DsArgs<P> a)
 {
@@ -307,6 +313,34 @@ __global__ void __launch_bounds__(256, (ROLL == 4 || ROLL == 7) ? 3 : (ROLL == 5
 #pragma unroll
                 for (int k = 0; k < 6; k++) acc[r].v[2 * ch + k / 3][k % 3] = o6[k];
             }
+        }
+    }
+    if constexpr (RED != 0) {
+        static_assert(NR == 1, "fused inner products take one right-hand side per thread");
+        Spinor<R> q;
+        P::load_spinor(RED == 1 ? a.w + roff : a.x + roff, g.V, s, q);
+        R d0 = 0, d1 = 0, d2 = 0;
+#pragma unroll
+        for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const cpx<R> z = RED == 1 ? cmulc(q.v[sp][c], acc[0].v[sp][c]) : cmulc(acc[0].v[sp][c], q.v[sp][c]);
+                d0 += z.re;
+                d1 += z.im;
+                d2 += acc[0].v[sp][c].re * acc[0].v[sp][c].re + acc[0].v[sp][c].im * acc[0].v[sp][c].im;
+            }
+        double e0 = d0, e1 = d1, e2 = d2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            e0 += __shfl_xor_sync(0xffffffffu, e0, o);
+            e1 += __shfl_xor_sync(0xffffffffu, e1, o);
+            e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            double *pp = a.part + ((long)r0 * a.nwt + tile * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 3;
+            pp[0] = e0;
+            pp[1] = e1;
+            pp[2] = e2;
         }
     }
 #pragma unroll
@@ -496,6 +530,9 @@ DsArgs<P> make_args(ddrw_ctx *ctx, const DslashCall &c)
     a.Ubw = std::is_same<P, PrecS>::value ? (const typename P::UElem *)ctx->Ubw32 : nullptr;
     a.err = ctx->d_err;
     a.stall_tx = ctx->stall_tx;
+    a.w = (const typename P::SElem *)c.w;
+    a.part = c.red_part;
+    a.nwt = (long)c.npar * c.nblk * BlockShape<BL>::VBH / 32;
     return a;
 }
 
@@ -509,6 +546,24 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
     if (c.hopsel == 2 || std::is_same<P, PrecDD>::value) cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
     if (c.hopsel == 1 && (cfg.nr != 1 || (cfg.roll != 0 && cfg.roll != 5 && cfg.roll != 6))) cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
     if (c.hopsel == 1 && cfg.roll == 6 && !g.nbr) cfg.roll = 5;
+    if constexpr (std::is_same<P, PrecS>::value) {
+        if (c.red != 0) {
+            // the fused epilogue: one right-hand side per thread, unrolled or register-capped form,
+            // whole CTAs (the caller checks that 256 divides the output sites)
+            if (cfg.nr != 1 || (cfg.roll != 0 && cfg.roll != 5) || n % cfg.nt) cfg = DsConfig{1, 64, 1, 5};
+            const unsigned gr = (unsigned)((n / cfg.nt) * (c.nrhs / cfg.nw));
+            const dim3 bk((unsigned)cfg.nt, (unsigned)cfg.nw);
+            ++ctx->launches;
+            if (c.red == 1) {
+                if (cfg.roll == 5) k_dslash<P, BL, 0, 1, 5, 1><<<gr, bk, 0, ctx->stream>>>(g, a);
+                else k_dslash<P, BL, 0, 1, 0, 1><<<gr, bk, 0, ctx->stream>>>(g, a);
+            } else {
+                if (cfg.roll == 5) k_dslash<P, BL, 0, 1, 5, 2><<<gr, bk, 0, ctx->stream>>>(g, a);
+                else k_dslash<P, BL, 0, 1, 0, 2><<<gr, bk, 0, ctx->stream>>>(g, a);
+            }
+            return;
+        }
+    }
     if (cfg.roll >= 6 && cfg.roll <= 7 && !g.nbr) cfg.roll = 11 - cfg.roll;  // no table: the computed-neighbour twin
     if (cfg.roll == 8) {
         // the staged form: FP32 storage, all hops, a tile never straddles the two parities
@@ -596,6 +651,7 @@ double compulsory_bytes(const DslashCall &c, long n)
     if (c.beta != 0.0) per += (c.npar == 1 ? 8.0 : 4.0) * Lk;
     if (c.diag == 1) per += Cb;
     if (c.post) per += Cb;
+    if (c.red == 1) per += S * c.nrhs;  // the fused inner product's second vector
     return per * (double)n;
 }
 

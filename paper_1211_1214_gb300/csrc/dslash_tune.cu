@@ -17,11 +17,31 @@
 // untuned for a later launch with separate buffers.  While the stream is being captured into a
 // graph nothing is timed and the default is used.
 #include <cstdio>
+#include <mutex>
 #include <string>
 
 #include "dslash.cuh"
 
 namespace ddrw {
+
+// Tuned shapes are also kept for the whole process, by device and lattice geometry, so that a new
+// context on the same lattice (the auxiliary context of the nested block factor, a second
+// configuration) starts from the measured choices instead of timing them again.
+namespace {
+std::mutex g_tune_mutex;
+std::map<std::array<long, 15>, TuneEntry> g_tune;
+
+std::array<long, 15> process_key(const ddrw_ctx *ctx, const std::array<int, 8> &k)
+{
+    std::array<long, 15> pk{};
+    pk[0] = ctx->device;
+    for (int mu = 0; mu < 4; mu++) pk[1 + mu] = ctx->dims[mu];
+    pk[5] = ctx->l;
+    pk[6] = ctx->cut;
+    for (int i = 0; i < 8; i++) pk[7 + i] = k[i];
+    return pk;
+}
+}  // namespace
 
 // right-hand sides per thread each hop code form supports
 static bool form_allowed(int nr, int roll)
@@ -45,6 +65,14 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
     std::array<int, 8> key = {prec, bl, c.npar, c.nrhs, c.diag, c.post, rpm, (c.beta != 0.0) + 2 * c.hopsel};
     auto it = ctx->tune.find(key);
     if (it != ctx->tune.end()) return DsConfig{it->second.nr, it->second.nt, it->second.nw, it->second.roll};
+    if (ctx->autotune) {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto g = g_tune.find(process_key(ctx, key));
+        if (g != g_tune.end()) {
+            ctx->tune[key] = g->second;
+            return DsConfig{g->second.nr, g->second.nt, g->second.nw, g->second.roll};
+        }
+    }
 
     DsConfig def;
     def.nr = (rpm % 2 == 0 && c.nrhs % 2 == 0) ? 2 : 1;
@@ -99,6 +127,10 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->tune[key] = TuneEntry{best.nr, best.nt, best.nw, best.roll, best_ms / 2};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune[process_key(ctx, key)] = ctx->tune[key];
+    }
     return best;
 }
 
@@ -114,6 +146,10 @@ ddrw_status ddrw_autotune(ddrw_ctx *ctx, int enable)
     ctx->autotune = enable != 0;
     ctx->tune.clear();
     ctx->blk_tune.clear();
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune.clear();
+    }
     clear_graphs(ctx);  // captured launches keep the form they were captured with
     return DDRW_OK;
 }

@@ -81,7 +81,8 @@ template <class P> DslashCall base_call(const ddrw_ctx *ctx, const MassSet &ms, 
 // out_e = Mhat in_e  (tmp on odd sites)
 template <class P>
 void apply_mhat(ddrw_ctx *ctx, const MassSet &ms, int nrhs, long rs, const typename P::SElem *in,
-                typename P::SElem *tmp, typename P::SElem *out, int colour = -1)
+                typename P::SElem *tmp, typename P::SElem *out, int colour = -1, int red = 0,
+                const typename P::SElem *w = nullptr, double *part = nullptr)
 {
     DslashCall c = base_call<P>(ctx, ms, nrhs, rs, colour);
     c.in = in;
@@ -98,6 +99,9 @@ void apply_mhat(ddrw_ctx *ctx, const MassSet &ms, int nrhs, long rs, const typen
     d.beta = -0.25;
     d.diag = 1;
     d.par0 = 0;
+    d.red = red;  // fused inner products of the output (1: with w, 2: with the input, and its norm)
+    d.w = w;
+    d.red_part = part;
     stencil<P>(ctx, d);
 }
 
@@ -109,11 +113,23 @@ static ddrw_status bicg_iteration(ddrw_ctx *ctx, const MassSet &ms, int nrhs, lo
                                   typename P::SElem *tmp, KScal *sc, int colour = -1)
 {
     ddrw_status s2;
-    apply_mhat<P>(ctx, ms, nrhs, rs, p, tmp, v, colour);
-    if ((s2 = Blas<P>::bicg_alpha(ctx, ev, rh, v, sc))) return s2;
-    Blas<P>::bicg_s(ctx, ev, r, v, sc);
-    apply_mhat<P>(ctx, ms, nrhs, rs, r, tmp, t, colour);
-    if ((s2 = Blas<P>::bicg_omega(ctx, ev, t, r, sc))) return s2;
+    if (P::ID == 32 && colour < 0 && ctx->fuse_dots && ctx->vh % 256 == 0) {
+        // the inner products of alpha and omega in the epilogue of the stencil that writes v and t
+        const long nwt = ctx->vh / 32;
+        double *part;
+        if ((s2 = workspace(ctx, "eo_redpart", sizeof(double) * 3 * (size_t)nwt * nrhs, (void **)&part))) return s2;
+        apply_mhat<P>(ctx, ms, nrhs, rs, p, tmp, v, colour, 1, rh, part);
+        bicg_fin(ctx, 1, nrhs, part, nwt, sc);
+        Blas<P>::bicg_s(ctx, ev, r, v, sc);
+        apply_mhat<P>(ctx, ms, nrhs, rs, r, tmp, t, colour, 2, nullptr, part);
+        bicg_fin(ctx, 2, nrhs, part, nwt, sc);
+    } else {
+        apply_mhat<P>(ctx, ms, nrhs, rs, p, tmp, v, colour);
+        if ((s2 = Blas<P>::bicg_alpha(ctx, ev, rh, v, sc))) return s2;
+        Blas<P>::bicg_s(ctx, ev, r, v, sc);
+        apply_mhat<P>(ctx, ms, nrhs, rs, r, tmp, t, colour);
+        if ((s2 = Blas<P>::bicg_omega(ctx, ev, t, r, sc))) return s2;
+    }
     if ((s2 = Blas<P>::bicg_xr(ctx, ev, x, p, r, t, rh, sc))) return s2;
     Blas<P>::bicg_p(ctx, ev, p, r, v, sc);
     return DDRW_OK;
@@ -547,6 +563,7 @@ ddrw_status full_solve_dc_prepare(ddrw_ctx *ctx, int nrhs)
     if ((st = workspace(ctx, "dcf_ctl", sizeof(int), &p))) return st;
     if ((st = workspace(ctx, "full_e64", sizeof(double2) * 12 * ctx->V * nrhs, &p))) return st;
     if ((st = workspace(ctx, "eo_graph_count", sizeof(int), &p))) return st;
+    if ((st = workspace(ctx, "eo_redpart", sizeof(double) * 3 * (size_t)(ctx->vh / 32) * nrhs, &p))) return st;
     return DDRW_OK;
 }
 

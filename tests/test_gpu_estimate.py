@@ -101,6 +101,28 @@ def test_block_solve_krylov_loop(case, colour):
         ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
 
 
+def test_fused_inner_products(case):
+    """The BiCGStab inner products fused into the stencil epilogue and in separate kernels give the
+    same solves up to the rounding of the sums: both reach the outer tolerance by the oracle's
+    operator and the exponents agree."""
+    ctx, lat, dims = case["ctx"], case["lat"], case["dims"]
+    ctx.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-12)
+    try:
+        b = synth.spinor_field(dims, seed=36, nrhs=2)
+        e = {}
+        for fuse in (True, False):
+            ctx.fuse_reductions(fuse)
+            x = np.zeros_like(b)
+            ctx.solve_D(case["m2"], b, x, nrhs=2)
+            for r in range(2):
+                assert rel(lat.apply(case["m2"], x[r]), b[r]) <= 1e-10, (fuse, r)
+            e[fuse], _, _, _ = ctx.estimate(1, seed=2, hit_offset=3)
+        assert close(e[True][0], e[False][0], tol=1e-9)
+    finally:
+        ctx.fuse_reductions(True)
+        ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+
+
 def test_full_solve(case):
     ctx, lat, dims = case["ctx"], case["lat"], case["dims"]
     b = synth.spinor_field(dims, seed=32)
