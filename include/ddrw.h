@@ -110,7 +110,7 @@ ddrw_status ddrw_set_params(ddrw_ctx *ctx, double csw, double m1, double m2, int
 ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, double tol_block, int maxiter);
 
 /* Krylov method of the full-lattice solves D(m) x = b whose inner solves run on FP32 fields
- * (DDRW_MIXED_FP32): method 0 is even-odd BiCGStab; method 1 (the default) is flexible GCR
+ * (DDRW_MIXED_FP32): method 0 (the default) is even-odd BiCGStab; method 1 is flexible GCR
  * preconditioned by the Schwarz alternating procedure on the domain decomposition of Sec. 1 --
  * Schwarz blocks of side 4 coloured black/white, ncy cycles over both colours, each block solved
  * approximately by nmr minimal-residual steps on its even-odd reduced operator with Dirichlet
@@ -121,11 +121,25 @@ ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, dou
  * DDRW_EINVAL outside method 0..1, ncy 1..16, nmr 1..32, nkv 1..16. */
 ddrw_status ddrw_set_outer_solver(ddrw_ctx *ctx, int method, int ncy, int nmr, int nkv);
 
-/* With enable != 0 (the default) the FP32 even-odd BiCGStab of the full-lattice solves computes the
- * inner products of alpha = rho / (rh, v) and omega = (t, s) / (t, t) in the epilogue of the stencil
- * launch that writes v and t (one partial per warp of 32 sites, summed in FP64 in a fixed order by a
- * small kernel) instead of re-reading v, t and s in separate reductions; 0 uses the separate
- * reduction kernels.  Results differ only by the rounding of the sums. */
+/* The 16-bit storage precisions (DDRW_MIXED_FP16, DDRW_MIXED_BF16).  reliable_updates != 0 (the
+ * default): the full-lattice inner solves keep the BiCGStab vectors in 16-bit storage with a per-site
+ * norm and make reliable updates -- whenever a right-hand side's recursive residual has fallen ten-fold,
+ * the 16-bit solution increment is folded into an FP32 solution and the true residual of the even-odd
+ * system, recomputed with the FP32 operator, replaces the recursive one -- so that they reach FP32
+ * accuracy (relative residual 1e-6 per defect-correction cycle) with 16-bit vector traffic; 0:
+ * plain 16-bit inner solves that stop near the 16-bit rounding (1e-3 / 5e-3) and restart at every
+ * cycle.  block_solves_16bit != 0: the block solves run on 16-bit storage too; 0 (the default): in
+ * FP32 (on 64x32^3 with 8^4 blocks the 16-bit block solves need a second defect-correction cycle and
+ * its double-single residual, and the step is 5 % slower).  Whole-estimate graphs (ddrw_use_graphs
+ * mode 1) use the plain form. */
+ddrw_status ddrw_set_low_precision(ddrw_ctx *ctx, int reliable_updates, int block_solves_16bit);
+
+/* With enable != 0 the FP32 even-odd BiCGStab of the full-lattice solves computes the inner
+ * products of alpha = rho / (rh, v) and omega = (t, s) / (t, t) in the epilogue of the stencil launch
+ * that writes v and t (one partial per warp of 32 sites, summed in FP64 in a fixed order by a small
+ * kernel) instead of re-reading v, t and s in separate reductions; 0 (the default) uses the
+ * separate reduction kernels -- on one GB300 the fused launch is 40 % slower than the plain one,
+ * which outweighs the reductions it saves.  Results differ only by the rounding of the sums. */
 ddrw_status ddrw_fuse_reductions(ddrw_ctx *ctx, int enable);
 
 /* How the block solves D_cc(m)^-1 of the mixed precisions run (Eq. 1; the four solves of r and the
@@ -237,10 +251,12 @@ ddrw_status ddrw_estimate_masses(ddrw_ctx *ctx, int nmass, const double *m2, int
  *                            W_1f = prod_i Re((1/N_hit) sum_j exp(-e1_ij)); sign of W_1f; and the
  *                            root trick log sqrt(W_gl) = logW[0] / 2
  *   logW_factors[N], rel_var[N]  per factor: log of its two-flavour estimate, sample variance / mean^2.
+ *   rel_var_1f[N]            per factor: the sample variance of the complex one-flavour estimator
+ *                            exp(-e1_ij), E|X|^2 - |E X|^2 (what Eq. 12 gives exactly), over |mean|^2.
  * 1 <= N <= 8. */
 ddrw_status ddrw_estimate_interp(ddrw_ctx *ctx, int N, int nhit, uint64_t seed, uint64_t hit_offset, double *exponents,
                                  double *exponents_1f, double *logW, double *logW_factors, double *rel_var,
-                                 ddrw_solve_info *info);
+                                 double *rel_var_1f, ddrw_solve_info *info);
 
 /* The adjoint of the estimate: for each of nhit noise vectors (as in ddrw_estimate) the exponent
  * e_j, its derivative with respect to every link and with respect to m2 (m1 fixed), by reverse

@@ -23,7 +23,7 @@ _STATUS = {0: "DDRW_OK", 1: "DDRW_EINVAL", 2: "DDRW_ENOMEM", 3: "DDRW_ECUDA", 4:
 #: every entry point declared in include/ddrw.h
 EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", "ddrw_volume", "ddrw_load_gauge",
            "ddrw_set_params", "ddrw_set_solver", "ddrw_set_outer_solver", "ddrw_set_block_solver",
-           "ddrw_fuse_reductions", "ddrw_set_dirichlet",
+           "ddrw_fuse_reductions", "ddrw_set_low_precision", "ddrw_set_dirichlet",
            "ddrw_block_factor_nested", "ddrw_apply_sap", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
@@ -84,6 +84,7 @@ def load(path: str | None = None):
         "ddrw_set_dirichlet": (st, [vp, ctypes.c_int]),
         "ddrw_set_block_solver": (st, [vp, ctypes.c_int]),
         "ddrw_fuse_reductions": (st, [vp, ctypes.c_int]),
+        "ddrw_set_low_precision": (st, [vp, ctypes.c_int, ctypes.c_int]),
         "ddrw_block_factor_nested": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, dp, dp, dp]),
         "ddrw_apply_D": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_apply_D_ds": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
@@ -110,7 +111,7 @@ def load(path: str | None = None):
                                        dp, dp, dp, dp, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(SolveInfo)]),
         "ddrw_use_graphs": (st, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_long)]),
         "ddrw_estimate_interp": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp, dp, dp,
-                                      dp, ctypes.POINTER(SolveInfo)]),
+                                      dp, dp, ctypes.POINTER(SolveInfo)]),
         "ddrw_force": (st, [vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, dp, dp, dp, dp, dp,
                             ctypes.POINTER(SolveInfo)]),
         "ddrw_autotune_report": (st, [vp, ctypes.c_char_p, ctypes.c_long]),
@@ -324,6 +325,11 @@ class Context:
                                                      _ptr(out), _ptr(e), _ptr(rv)), "ddrw_block_factor_nested")
         return float(out[0]), float(out[1]), float(out[2]), e, float(rv[0])
 
+    def set_low_precision(self, reliable_updates=True, block_solves_16bit=False):
+        """16-bit precisions: reliable updates in the inner solves; 16-bit or FP32 block solves."""
+        self._check(self.L.ddrw_set_low_precision(self._h, int(bool(reliable_updates)), int(bool(block_solves_16bit))),
+                    "ddrw_set_low_precision")
+
     def fuse_reductions(self, enable=True):
         """Inner products of the BiCGStab recurrence in the stencil epilogue (True) or separate kernels."""
         self._check(self.L.ddrw_fuse_reductions(self._h, int(bool(enable))), "ddrw_fuse_reductions")
@@ -375,12 +381,14 @@ class Context:
         lw = np.zeros(4, dtype=np.float64)
         lf = np.zeros(N, dtype=np.float64)
         rv = np.zeros(N, dtype=np.float64)
+        rv1 = np.zeros(N, dtype=np.float64)
         info = SolveInfo()
         st = self.L.ddrw_estimate_interp(self._h, int(N), int(nhit), ctypes.c_uint64(seed), ctypes.c_uint64(hit_offset),
-                                         _ptr(e), _ptr(e1), _ptr(lw), _ptr(lf), _ptr(rv), ctypes.byref(info))
+                                         _ptr(e), _ptr(e1), _ptr(lw), _ptr(lf), _ptr(rv), _ptr(rv1), ctypes.byref(info))
         self._check(st, "ddrw_estimate_interp")
         return {"exponents": e, "exponents_1f": e1[..., 0] + 1j * e1[..., 1], "logW": lw[0], "logW_1f": lw[1],
-                "sign_1f": lw[2], "logW_root": lw[3], "logW_factors": lf, "rel_var": rv, "info": info.as_dict()}
+                "sign_1f": lw[2], "logW_root": lw[3], "logW_factors": lf, "rel_var": rv, "rel_var_1f": rv1,
+                "info": info.as_dict()}
 
     def estimate_masses(self, m2s, nhit, seed=2, hit_offset=0):
         """Batched estimate for several target masses: (exponents [nmass, nhit], logW [nmass],

@@ -740,6 +740,15 @@ ddrw_status ddrw_set_dirichlet(ddrw_ctx *ctx, int cut)
     return DDRW_OK;
 }
 
+ddrw_status ddrw_set_low_precision(ddrw_ctx *ctx, int reliable_updates, int block_solves_16bit)
+{
+    if (!ctx) return DDRW_EINVAL;
+    ctx->reliable16 = reliable_updates != 0;
+    ctx->block16 = block_solves_16bit != 0;
+    clear_graphs(ctx);
+    return DDRW_OK;
+}
+
 ddrw_status ddrw_fuse_reductions(ddrw_ctx *ctx, int enable)
 {
     if (!ctx) return DDRW_EINVAL;

@@ -570,6 +570,64 @@ void f32_to_low(ddrw_ctx *ctx, const float4 *in, uint2 *out, long n, bool bf)
     else k_f32_to_low<false><<<g, 256, 0, ctx->stream>>>(n, in, out);
 }
 
+// FP32 field -> 16-bit field over a site range (the 16-bit spinor takes its per-site norm anew)
+template <class P16>
+__global__ void __launch_bounds__(NT) k_f32_to_16(long V, long off, long n, long rs32, long rs16, const float4 *in,
+                                                  typename P16::SElem *out)
+{
+    const float4 *ib = in + (long)blockIdx.y * rs32;
+    typename P16::SElem *ob = out + (long)blockIdx.y * rs16;
+    for (long j = (long)blockIdx.x * NT + threadIdx.x; j < n; j += (long)gridDim.x * NT) {
+        Spinor<float> p;
+        PrecS::load_spinor_rw(ib, (int)V, (int)(off + j), p);
+        P16::store_spinor(ob, (int)V, (int)(off + j), p);
+    }
+}
+
+// x32 += x16 over a site range, then x16 = 0 (the reliable update of a 16-bit Krylov solve)
+template <class P16>
+__global__ void __launch_bounds__(NT) k_fold_16_into_32(long V, long off, long n, long rs16, long rs32,
+                                                        typename P16::SElem *x16, float4 *x32)
+{
+    typename P16::SElem *hb = x16 + (long)blockIdx.y * rs16;
+    float4 *fb = x32 + (long)blockIdx.y * rs32;
+    Spinor<float> z;
+    zero(z);
+    for (long j = (long)blockIdx.x * NT + threadIdx.x; j < n; j += (long)gridDim.x * NT) {
+        const int sj = (int)(off + j);
+        Spinor<float> a, b;
+        P16::load_spinor_rw(hb, (int)V, sj, a);
+        PrecS::load_spinor_rw(fb, (int)V, sj, b);
+#pragma unroll
+        for (int sp = 0; sp < 4; sp++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) b.v[sp][c] = b.v[sp][c] + a.v[sp][c];
+        PrecS::store_spinor(fb, (int)V, sj, b);
+        P16::store_spinor(hb, (int)V, sj, z);
+    }
+}
+
+template <class P16>
+void f32_to_16(ddrw_ctx *ctx, const VecRange &vr, long rs16, const float4 *in, typename P16::SElem *out)
+{
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
+    ++ctx->launches;
+    k_f32_to_16<P16><<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(vr.V, vr.off, vr.n, vr.rs, rs16, in, out);
+}
+
+template <class P16>
+void fold_16_into_32(ddrw_ctx *ctx, const VecRange &vr, long rs16, typename P16::SElem *x16, float4 *x32)
+{
+    ProfScope ps(ctx, PROF_BLAS, 0.0);
+    ++ctx->launches;
+    k_fold_16_into_32<P16><<<dim3(grid_for(vr.n), vr.nrhs), NT, 0, ctx->stream>>>(vr.V, vr.off, vr.n, rs16, vr.rs, x16,
+                                                                                   x32);
+}
+template void f32_to_16<PrecH>(ddrw_ctx *, const VecRange &, long, const float4 *, PrecH::SElem *);
+template void f32_to_16<PrecB>(ddrw_ctx *, const VecRange &, long, const float4 *, PrecB::SElem *);
+template void fold_16_into_32<PrecH>(ddrw_ctx *, const VecRange &, long, PrecH::SElem *, float4 *);
+template void fold_16_into_32<PrecB>(ddrw_ctx *, const VecRange &, long, PrecB::SElem *, float4 *);
+
 #define DDRW_LOW_INST(P)                                                                                      \
     template void to_low<P>(ddrw_ctx *, const VecRange &, long, const double2 *, P::SElem *, const double *); \
     template void add_low<P>(ddrw_ctx *, const VecRange &, long, const P::SElem *, double2 *, const double *);

@@ -120,6 +120,11 @@ void to_low(ddrw_ctx *ctx, const VecRange &vr, long rsl, const double2 *in, type
             const double *scale);
 template <class P>
 void add_low(ddrw_ctx *ctx, const VecRange &vr, long rsl, const typename P::SElem *e, double2 *x, const double *scale);
+// FP32 field (stride vr.rs) -> 16-bit field (stride rs16) over the range; and x32 += x16, x16 = 0
+template <class P16>
+void f32_to_16(ddrw_ctx *ctx, const VecRange &vr, long rs16, const float4 *in, typename P16::SElem *out);
+template <class P16>
+void fold_16_into_32(ddrw_ctx *ctx, const VecRange &vr, long rs16, typename P16::SElem *x16, float4 *x32);
 // FP32 link / clover planes -> 16-bit planes of the same order (n float4 elements; bf: BF16, else FP16)
 void f32_to_low(ddrw_ctx *ctx, const float4 *in, uint2 *out, long n, bool bf);
 

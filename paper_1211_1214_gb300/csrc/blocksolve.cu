@@ -89,6 +89,24 @@ static ddrw_status low_cycle(ddrw_ctx *ctx, int colour, const MassSet &ms, const
     const size_t fl = sizeof(E) * rsl * nrhs;
     void *bl, *el;
     ddrw_status st;
+    if (P::ID != 32 && P::ID != 64 && ctx->block_method == 1 && !tol2_dev && ctx->reliable_updates()) {
+        // 16-bit Krylov vectors on all blocks of the colour with reliable updates into FP32 fields
+        float4 *b32, *x32;
+        const size_t f32 = sizeof(float4) * 6 * ctx->V * nrhs;
+        if ((st = workspace(ctx, "blkl_b32", f32, (void **)&b32))) return st;
+        if ((st = workspace(ctx, "blkl_e32", f32, (void **)&x32))) return st;
+        for (int p = 0; p < 2; p++) to_low<PrecS>(ctx, colour_range(ctx, colour, p, nrhs, rs64), 6 * ctx->V, rhs, b32, scale_d);
+        int it = 0;
+        std::vector<double> th(nrhs, tol_inner * tol_inner);
+        if ((st = colour_bicgstab_reliable(ctx, P::ID, ms, b32, x32, nrhs, th, maxiter, &it, colour))) return st;
+        int hs[2] = {it, 0};
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(stat, hs, sizeof(hs), cudaMemcpyHostToDevice, ctx->stream));
+        DDRW_SYNC(ctx);  // hs is stack memory
+        if (first) zero_colour64(ctx, x, colour, nrhs);
+        for (int p = 0; p < 2; p++)
+            add_low<PrecS>(ctx, colour_range(ctx, colour, p, nrhs, rs64), 6 * ctx->V, x32, x, scale_d + nrhs);
+        return DDRW_OK;
+    }
     if ((st = workspace(ctx, "blkl_b", fl, &bl))) return st;
     if ((st = workspace(ctx, "blkl_e", fl, &el))) return st;
     for (int p = 0; p < 2; p++) to_low<P>(ctx, colour_range(ctx, colour, p, nrhs, rs64), rsl, rhs, (E *)bl, scale_d);
@@ -297,13 +315,17 @@ static ddrw_status block_solve_dc(ddrw_ctx *ctx, int colour, const MassSet &ms, 
 ddrw_status block_solve64(ddrw_ctx *ctx, int colour, const MassSet &ms, const double2 *b, double2 *x, int nrhs,
                           double tol, int maxiter, ddrw_prec prec, SolveStats *stats)
 {
+    // under the 16-bit precisions the block solves may run in FP32 instead (ddrw_set_low_precision)
+    if ((prec == DDRW_MIXED_FP16 || prec == DDRW_MIXED_BF16) && !ctx->block16) prec = DDRW_MIXED_FP32;
     if (ctx->devctl) return block_solve_dc(ctx, colour, ms, b, x, nrhs, tol, maxiter, prec);
     const bool mixed = prec != DDRW_FP64;
     const long V = ctx->V, rs64 = 12 * V;
     // the inner Krylov vectors: FP64 fields, or the largest low-precision field (FP32)
     const size_t f64 = sizeof(double2) * rs64 * nrhs, f32 = sizeof(float4) * 6 * V * nrhs;
     // deepest relative residual an inner solve is asked for: what its storage reliably reaches
-    const double floor = prec == DDRW_MIXED_FP32 ? 1e-6 : prec == DDRW_MIXED_FP16 ? 1e-3 : 5e-3;
+    // (16-bit Krylov-loop block solves with reliable updates reach what FP32 reaches)
+    const bool rel16 = prec != DDRW_MIXED_FP32 && ctx->block_method == 1 && ctx->reliable_updates();
+    const double floor = (prec == DDRW_MIXED_FP32 || rel16) ? 1e-6 : prec == DDRW_MIXED_FP16 ? 1e-3 : 5e-3;
     ddrw_status st;
     std::vector<double> bb, rr;
     if ((st = colour_norms(ctx, colour, b, nrhs, bb))) return st;

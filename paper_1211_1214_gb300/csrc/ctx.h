@@ -129,8 +129,14 @@ struct ddrw_ctx {
     // side), 1 the Krylov-loop BiCGStab on the colour's blocks as one block-diagonal system
     int block_method = 0;
     // the BiCGStab inner products of alpha and omega fused into the epilogue of the stencil launch
-    // that writes v and t (FP32 storage, full lattice); off: separate reduction kernels
-    bool fuse_dots = true;
+    // that writes v and t (FP32 storage, full lattice); off (the default, measured faster on
+    // GB300): separate reduction kernels
+    bool fuse_dots = false;
+    // 16-bit storage precisions: the full-lattice inner solves keep their Krylov vectors in 16-bit
+    // storage with reliable updates into FP32 (true), or restart at each defect-correction cycle;
+    // the block solves run on 16-bit storage (true) or in FP32
+    bool reliable16 = true;
+    bool block16 = false;
 
     // Dirichlet cut (ddrw_set_dirichlet): hops across the faces of cut^4 boxes removed from the
     // hopping term after the clover term is built from the full field, whose links stay in U64f / U32f
@@ -159,6 +165,9 @@ struct ddrw_ctx {
     // CUDA graphs of the outer Krylov loop, by launch shape and buffers
     bool use_graphs = true;       // Krylov-loop graphs
     bool use_est_graphs = false;  // whole estimate chunks as one graph (mode 1; needs use_graphs)
+    // reliable updates are on and not excluded by the whole-estimate graphs, whose captured solvers
+    // (and, for equal results, the eager calls of that mode) use the plain 16-bit form
+    bool reliable_updates() const { return reliable16 && !(use_graphs && use_est_graphs); }
     long graph_launches = 0;
     std::map<std::array<uintptr_t, 13 + 2 * ddrw::MAXM>, ddrw::GraphEntry> graphs;
     // whole-estimate graphs (estimate.cu): captured on the second call of a shape, replayed after
@@ -351,6 +360,10 @@ ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, dou
 // storage of policy id pid (32, 16 = FP16, 17 = BF16)
 ddrw_status colour_bicgstab(ddrw_ctx *ctx, int pid, const MassSet &ms, const void *b, void *x, int nrhs,
                             const std::vector<double> &thresh, int maxiter, int *iters, int colour);
+// the same on 16-bit Krylov vectors (pid 16 FP16, 17 BF16) with reliable updates into the FP32
+// fields b and x (full-field layout)
+ddrw_status colour_bicgstab_reliable(ddrw_ctx *ctx, int pid, const MassSet &ms, const float4 *b, float4 *x, int nrhs,
+                                     const std::vector<double> &thresh, int maxiter, int *iters, int colour);
 // Schwarz-preconditioned flexible GCR on FP32 fields (sap.cu): x = D(ms)^-1 b on the full lattice
 // until |b - D x|^2 <= thresh[r] per right-hand side; adds its iterations to *iters
 bool sap_supported(const ddrw_ctx *ctx);

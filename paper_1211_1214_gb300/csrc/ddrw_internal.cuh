@@ -212,6 +212,39 @@ __device__ __forceinline__ void project(const Spinor<R> &p, Half<R> &h)
     }
 }
 
+// Storage policies whose spinors carry a per-site norm (16-bit storage) declare NORMED = true.
+template <class P, class = void> struct Normed {
+    static constexpr bool value = false;
+};
+template <class P> struct Normed<P, decltype((void)P::NORMED)> {
+    static constexpr bool value = P::NORMED;
+};
+
+// acc += n (1 +- g_mu)-reconstruction of the half spinor w, the scale n folded into the FMAs that
+// add the hop (a 16-bit neighbour's norm and the boundary sign cost no separate multiplies)
+template <int MU, int SIGN, typename R>
+__device__ __forceinline__ void reconstruct_add_scaled(Spinor<R> &acc, const Half<R> &w, R n)
+{
+    const R ns = SIGN > 0 ? n : -n;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        cpx<R> w0 = w.v[0][c], w1 = w.v[1][c];
+        cpx<R> f0, f1;  // e_mu^dag w
+        if (MU == 0) { f0 = -w0; f1 = -w1; }
+        else if (MU == 1) { f0 = timesI(w1); f1 = timesI(w0); }
+        else if (MU == 2) { f0 = w1; f1 = -w0; }
+        else { f0 = timesI(w0); f1 = timesMinusI(w1); }
+        acc.v[0][c].re = fmad(n, w0.re, acc.v[0][c].re);
+        acc.v[0][c].im = fmad(n, w0.im, acc.v[0][c].im);
+        acc.v[1][c].re = fmad(n, w1.re, acc.v[1][c].re);
+        acc.v[1][c].im = fmad(n, w1.im, acc.v[1][c].im);
+        acc.v[2][c].re = fmad(ns, f0.re, acc.v[2][c].re);
+        acc.v[2][c].im = fmad(ns, f0.im, acc.v[2][c].im);
+        acc.v[3][c].re = fmad(ns, f1.re, acc.v[3][c].re);
+        acc.v[3][c].im = fmad(ns, f1.im, acc.v[3][c].im);
+    }
+}
+
 // acc += coef * (1 +- g_mu)-reconstruction of the half spinor w
 template <int MU, int SIGN, typename R>
 __device__ __forceinline__ void reconstruct_add(Spinor<R> &acc, const Half<R> &w)

@@ -543,8 +543,12 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
     long n = (long)c.npar * c.nblk * BlockShape<BL>::VBH;
     // double-single launches and hops between blocks take one row; hops inside blocks take the
     // unrolled, register-capped or table form with one right-hand side per thread
-    if (c.hopsel == 2 || std::is_same<P, PrecDD>::value) cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
-    if (c.hopsel == 1 && (cfg.nr != 1 || (cfg.roll != 0 && cfg.roll != 5 && cfg.roll != 6))) cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
+    if (c.hopsel == 2) cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
+    // double-single: one right-hand side per thread, unrolled or rolled hop code (the rolled form
+    // has half the code of the unrolled one, which is instruction-fetch bound)
+    if (std::is_same<P, PrecDD>::value) cfg.nr = 1, cfg.nw = 1, cfg.roll = (cfg.roll == 1 && c.hopsel != 2) ? 1 : 0;
+    if (!std::is_same<P, PrecDD>::value && c.hopsel == 1 && (cfg.nr != 1 || (cfg.roll != 0 && cfg.roll != 5 && cfg.roll != 6)))
+        cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
     if (c.hopsel == 1 && cfg.roll == 6 && !g.nbr) cfg.roll = 5;
     if constexpr (std::is_same<P, PrecS>::value) {
         if (c.red != 0) {
@@ -609,7 +613,9 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
     dim3 blk((unsigned)cfg.nt, (unsigned)cfg.nw);
     ++ctx->launches;
     if constexpr (std::is_same<P, PrecDD>::value) {  // one right-hand side per thread
-        if (c.hopsel == 0) k_dslash<P, BL, 0, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
+        if (c.hopsel == 0 && cfg.roll == 1) k_dslash<P, BL, 0, 1, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
+        else if (c.hopsel == 1 && cfg.roll == 1) k_dslash<P, BL, 1, 1, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
+        else if (c.hopsel == 0) k_dslash<P, BL, 0, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
         else if (c.hopsel == 1) k_dslash<P, BL, 1, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
         else k_dslash<P, BL, 2, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
     } else {
@@ -672,8 +678,7 @@ void launch_bl(ddrw_ctx *ctx, const DslashCall &c)
     if (n == 0 || c.nrhs == 0) return;
     DsConfig cfg;
     constexpr bool split = std::is_same<P, PrecDD>::value;
-    if constexpr (!split)
-        if (c.hopsel != 2) cfg = tuned_config(ctx, c, P::ID, BL, &run_cfg<P, BL>);
+    if (c.hopsel != 2) cfg = tuned_config(ctx, c, P::ID, BL, &run_cfg<P, BL>);
     int kind = split ? PROF_DSLASH_DS
                      : P::ID < 32 ? PROF_DSLASH16 + (c.hopsel != 0)
                                   : (sizeof(R) == 8 ? PROF_DSLASH64 : PROF_DSLASH32) + (c.hopsel != 0 ? 2 : 0);

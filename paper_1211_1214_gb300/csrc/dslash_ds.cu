@@ -4,6 +4,12 @@
 
 namespace ddrw {
 
+// the block lengths are instantiated in dslash_ds<l>.cu, so that they compile in parallel
+extern template void launch_bl<PrecDD, 2>(ddrw_ctx *, const DslashCall &);
+extern template void launch_bl<PrecDD, 4>(ddrw_ctx *, const DslashCall &);
+extern template void launch_bl<PrecDD, 6>(ddrw_ctx *, const DslashCall &);
+extern template void launch_bl<PrecDD, 8>(ddrw_ctx *, const DslashCall &);
+
 void dslash_ds(ddrw_ctx *ctx, const DslashCall &c) { launch<PrecDD>(ctx, c); }
 
 // one complex FP64 number (x, y) per element -> (hi(x), lo(x), hi(y), lo(y)).  The elements are

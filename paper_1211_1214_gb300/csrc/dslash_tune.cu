@@ -102,11 +102,14 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
         // launches restricted to the hops inside the blocks come in the unrolled, register-capped
         // and table forms with one right-hand side per thread
         if (c.hopsel != 0 && (nr != 1 || (roll != 0 && roll != 5 && roll != 6))) continue;
+        // double-single launches: unrolled or rolled, one right-hand side per thread, one row
+        if (prec == 128 && (nr != 1 || roll > 1)) continue;
         const int *nwl = roll == 8 ? nws8 : nws;
         const int nnw = roll == 8 ? 4 : 2;
         for (int iw = 0; iw < nnw; iw++)
         for (int nt : nts) {
             const int nw = nwl[iw];
+            if (prec == 128 && nw != 1) continue;
             if (roll == 8 ? (nt > 128 || nw > rpm) : (c.nrhs / nr) % nw != 0) continue;
             if (nt * nw > 256) continue;
             DsConfig cfg{nr, nt, nw, roll};

@@ -725,9 +725,33 @@ static void one_flavour_factor(const double *e1, int n, double *logabs, double *
     *sign = mean >= 0 ? 1.0 : -1.0;
 }
 
+// sample variance of the complex one-flavour estimator exp(-eta^dag (M - 1) eta) over its squared
+// modulus mean (Eq. 12 measured on the samples: E|X|^2 - |E X|^2), scale-free via a common shift
+static double one_flavour_rel_var(const double *e1, int n)
+{
+    if (n < 2) return 0.0;
+    double mx = -e1[0];
+    for (int j = 1; j < n; j++) mx = std::max(mx, -e1[2 * j]);
+    double mr = 0, mi = 0;
+    for (int j = 0; j < n; j++) {
+        const double a = std::exp(-e1[2 * j] - mx);
+        mr += a * std::cos(e1[2 * j + 1]);
+        mi -= a * std::sin(e1[2 * j + 1]);
+    }
+    mr /= n;
+    mi /= n;
+    double v = 0;
+    for (int j = 0; j < n; j++) {
+        const double a = std::exp(-e1[2 * j] - mx);
+        const double dr = a * std::cos(e1[2 * j + 1]) - mr, di = -a * std::sin(e1[2 * j + 1]) - mi;
+        v += dr * dr + di * di;
+    }
+    return v / (n - 1) / (mr * mr + mi * mi);
+}
+
 ddrw_status ddrw_estimate_interp(ddrw_ctx *ctx, int N, int nhit, uint64_t seed, uint64_t hit_offset, double *exponents,
                                  double *exponents_1f, double *logW, double *logW_factors, double *rel_var,
-                                 ddrw_solve_info *info)
+                                 double *rel_var_1f, ddrw_solve_info *info)
 {
     if (!ctx) return DDRW_EINVAL;
     if (N < 1 || N > MAXM || nhit <= 0) return set_error(ctx, DDRW_EINVAL, "1 <= N <= 8 interpolation steps, nhit > 0");
@@ -772,6 +796,7 @@ ddrw_status ddrw_estimate_interp(ddrw_ctx *ctx, int N, int nhit, uint64_t seed, 
         sg *= sgn;
         if (logW_factors) logW_factors[i] = lf;
         if (rel_var) rel_var[i] = rv;
+        if (rel_var_1f) rel_var_1f[i] = one_flavour_rel_var(e1.data() + 2 * (size_t)i * nhit, nhit);
     }
     if (exponents) std::copy(e.begin(), e.end(), exponents);
     if (exponents_1f) std::copy(e1.begin(), e1.end(), exponents_1f);
@@ -800,7 +825,7 @@ ddrw_status ddrw_estimate_variant(ddrw_ctx *ctx, int variant, int N, int nhit, u
         if (eta) return set_error(ctx, DDRW_EINVAL, "the block variant draws its own noise (ddrw_estimate_interp)");
         double lw[4];
         if (dim) *dim = 12 * ctx->nP;
-        ddrw_status st = ddrw_estimate_interp(ctx, N, nhit, seed, hit_offset, exponents, nullptr, lw, nullptr,
+        ddrw_status st = ddrw_estimate_interp(ctx, N, nhit, seed, hit_offset, exponents, nullptr, lw, nullptr, nullptr,
                                               rel_var, info);
         if (logW) *logW = lw[0];
         return st;

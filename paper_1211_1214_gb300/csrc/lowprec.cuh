@@ -70,6 +70,8 @@ template <bool BF> struct PrecLow {
     static constexpr int CPLANES = 18;
     static constexpr double SBYTES = 52, UBYTES = 24, CBYTES = 144;
     static constexpr int NCHUNK = 1, CW = 12;  // BLAS granularity: the whole site (one norm)
+    // the hop code keeps a neighbour's norm apart and applies it in the FMAs that add the hop
+    static constexpr bool NORMED = true;
     __host__ __device__ static long field_elems(long V) { return 3 * V + V / 4; }
 
     __device__ static __forceinline__ cpx<R> cx(uint32_t w, float n)
@@ -115,6 +117,22 @@ template <bool BF> struct PrecLow {
         load_all<true>(f, stride, s, c);
 #pragma unroll
         for (int i = 0; i < 12; i++) p.v[i / 3][i % 3] = c[i];
+    }
+    // the stored (normalised) components and the site's norm n: the spinor is n p
+    __device__ static __forceinline__ void load_spinor_unscaled(const SElem *__restrict__ f, int stride, int s,
+                                                                Spinor<R> &p, R &n)
+    {
+        n = __ldg(reinterpret_cast<const float *>(f + 3 * stride) + s);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const uint4 e = __ldg(f + (k * stride + s));
+            const uint32_t w[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const float2 u = K::unpack(w[q]);
+                p.v[(4 * k + q) / 3][(4 * k + q) % 3] = {u.x, u.y};
+            }
+        }
     }
     __device__ static __forceinline__ void load_spinor_rw(const SElem *f, int stride, int s, Spinor<R> &p)
     {
@@ -182,6 +200,18 @@ template <bool BF> struct PrecLow {
         r.n = __ldg(reinterpret_cast<const float *>(f + 3 * stride) + s);
 #pragma unroll
         for (int k = 0; k < 3; k++) r.e[k] = __ldg(f + (k * stride + s));
+    }
+    __device__ static __forceinline__ void decode_unscaled(const SRaw &r, Spinor<R> &p)
+    {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const uint32_t w[4] = {r.e[k].x, r.e[k].y, r.e[k].z, r.e[k].w};
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const float2 u = K::unpack(w[q]);
+                p.v[(4 * k + q) / 3][(4 * k + q) % 3] = {u.x, u.y};
+            }
+        }
     }
     __device__ static __forceinline__ void decode(const SRaw &r, Spinor<R> &p)
     {

@@ -329,6 +329,144 @@ ddrw_status full_norms(ddrw_ctx *ctx, const double2 *f, int nrhs, std::vector<do
 
 }  // namespace
 
+// Even-odd BiCGStab on 16-bit storage with reliable updates: the Krylov vectors (r, rh, p, v, t)
+// and the running solution increment x16 live in P16 (FP16 or BF16 with per-site norms); whenever a
+// right-hand side's recursive residual has fallen by the factor delta since the last update (or
+// has reached its target), the increment is folded into the FP32 solution x32, the true residual
+// of the even-odd system b - Mhat x32 is recomputed with the FP32 operator and replaces r, and
+// rho = (rh, r) is recomputed; p, v and the scalars carry on (the Krylov space is kept).  The
+// solve thus reaches FP32 accuracy with 16-bit storage traffic, instead of stalling near the
+// 16-bit rounding and restarting.  b and x are full FP32 fields; stops when ||r32||^2 <= thresh[r].
+// With colour 0 / 1 it solves the block operator of that colour (its sites only, hops inside the
+// blocks), as eo_bicgstab does.
+template <class P16>
+static ddrw_status eo_bicgstab_reliable(ddrw_ctx *ctx, const MassSet &ms, const float4 *b, float4 *x, int nrhs,
+                                        const std::vector<double> &thresh, int maxiter, int *iters, int colour = -1)
+{
+    using E = typename P16::SElem;
+    const long V = ctx->V, rs16 = P16::field_elems(V), rs32 = 6 * V;
+    const size_t fb16 = sizeof(E) * rs16 * nrhs, fb32 = sizeof(float4) * rs32 * nrhs;
+    const char *names[7] = {"eo_r", "eo_rh", "eo_p", "eo_v", "eo_t", "eo_tmp", "eo_x"};
+    void *w[7];
+    ddrw_status st;
+    for (int k = 0; k < 7; k++) {
+        char nm[32];
+        snprintf(nm, sizeof nm, "%s%d", names[k], P16::ID);
+        if ((st = workspace(ctx, nm, fb16, &w[k]))) return st;
+    }
+    E *r = (E *)w[0], *rh = (E *)w[1], *p = (E *)w[2], *v = (E *)w[3], *t = (E *)w[4], *tmp = (E *)w[5], *x16 = (E *)w[6];
+    float4 *bh32, *r32, *tmp32;
+    if ((st = workspace(ctx, "rel_bh32", fb32, (void **)&bh32))) return st;
+    if ((st = workspace(ctx, "rel_r32", fb32, (void **)&r32))) return st;
+    if ((st = workspace(ctx, "rel_tmp32", fb32, (void **)&tmp32))) return st;
+    KScal *sc;
+    double *red;
+    if ((st = workspace(ctx, "eo_kscal", sizeof(KScal) * nrhs, (void **)&sc))) return st;
+    if ((st = workspace(ctx, "rel_red", sizeof(double) * 4 * nrhs, (void **)&red))) return st;
+    // the even sites of the whole lattice, or of the blocks of one colour (block operator)
+    const long nc = colour < 0 ? ctx->vh : (long)ctx->nblk_c * (ctx->vh / ctx->nblk), o0 = colour < 0 ? 0 : colour * nc;
+    const VecRange ev32{V, o0, nc, rs32, nrhs}, ev16{V, o0, nc, rs16, nrhs};
+
+    // bhat = b_e + 1/2 H_eo A_oo^-1 b_o in FP32; x32 = 0; r32 = bhat
+    DslashCall c = base_call<PrecS>(ctx, ms, nrhs, rs32, colour);
+    c.x = b;
+    c.out = tmp32;
+    c.alpha = 1.0;
+    c.diag = 2;
+    c.post = 1;
+    c.par0 = 1;
+    dslash32(ctx, c);
+    DslashCall d = base_call<PrecS>(ctx, ms, nrhs, rs32, colour);
+    d.in = tmp32;
+    d.x = b;
+    d.out = bh32;
+    d.alpha = 1.0;
+    d.beta = 0.5;
+    d.diag = 2;
+    d.par0 = 0;
+    dslash32(ctx, d);
+    DDRW_CUDA_CHECK(cudaMemsetAsync(x, 0, fb32, ctx->stream));
+    f32_to_16<P16>(ctx, ev32, rs16, bh32, r);
+
+    std::vector<KScal> hk(nrhs);
+    for (int k = 0; k < nrhs; k++) {
+        hk[k] = KScal{};
+        hk[k].thresh = thresh[k];
+        hk[k].maxiter = maxiter;
+    }
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(sc, hk.data(), sizeof(KScal) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+    if ((st = Blas<P16>::bicg_init(ctx, ev16, r, rh, p, x16, sc))) return st;
+    KScal *hs = (KScal *)ctx->h_pinned;
+    DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, sc, sizeof(KScal) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+    DDRW_SYNC(ctx);
+    std::vector<double> rr_ref(nrhs), hred(4 * nrhs);
+    std::vector<char> done(nrhs, 0);
+    for (int k = 0; k < nrhs; k++) {
+        rr_ref[k] = hs[k].rr;
+        done[k] = hs[k].active ? 0 : 1;
+    }
+    const double delta2 = 1e-2;  // reliable update when the residual fell by 10 since the last one
+    const long rs_ = rs16;
+    int it = 0;
+    bool all_done = true;
+    for (int k = 0; k < nrhs; k++) all_done &= done[k] != 0;
+    while (!all_done && it < maxiter) {
+        for (int k = 0; k < 4; k++, it++)
+            if ((st = bicg_iteration<P16>(ctx, ms, nrhs, rs_, ev16, x16, r, rh, p, v, t, tmp, sc, colour))) return st;
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, sc, sizeof(KScal) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+        DDRW_SYNC(ctx);
+        bool trigger = it >= maxiter, any_active = false;
+        for (int k = 0; k < nrhs; k++) {
+            if (done[k]) continue;
+            any_active |= hs[k].active != 0;
+            if (!hs[k].active || hs[k].rr < delta2 * rr_ref[k]) trigger = true;
+        }
+        if (!any_active) trigger = true;
+        if (!trigger) continue;
+        // reliable update of every right-hand side: x32 += x16, x16 = 0, r = bhat - Mhat x32 in FP32
+        fold_16_into_32<P16>(ctx, ev32, rs16, x16, x);
+        apply_mhat<PrecS>(ctx, ms, nrhs, rs32, x, tmp32, r32, colour);
+        Blas<PrecS>::axpby(ctx, ev32, 1.0, bh32, -1.0, r32);
+        if ((st = Blas<PrecS>::norm2(ctx, ev32, r32, red))) return st;
+        f32_to_16<P16>(ctx, ev32, rs16, r32, r);
+        if ((st = Blas<P16>::norm_dot(ctx, ev16, rh, r, red + nrhs))) return st;
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(hred.data(), red, sizeof(double) * 4 * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+        DDRW_SYNC(ctx);
+        all_done = true;
+        for (int k = 0; k < nrhs; k++) {
+            const double rr = hred[k];
+            if (!(rr == rr)) return set_error(ctx, DDRW_ENUMERIC, "NaN in a reliable update");
+            rr_ref[k] = rr;
+            if (rr <= thresh[k] || hs[k].breakdown) done[k] = 1;
+            hs[k].rr = rr;
+            hs[k].rho = make_double2(hred[nrhs + 3 * k + 1], hred[nrhs + 3 * k + 2]);
+            hs[k].active = (!done[k] && it < maxiter) ? 1 : 0;
+            all_done &= done[k] != 0;
+        }
+        DDRW_CUDA_CHECK(cudaMemcpyAsync(sc, hs, sizeof(KScal) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    *iters += it;
+    // x_o = A_oo^-1 (b_o + 1/2 H_oe x_e) in FP32
+    DslashCall e = base_call<PrecS>(ctx, ms, nrhs, rs32, colour);
+    e.in = x;
+    e.x = b;
+    e.out = x;
+    e.alpha = 1.0;
+    e.beta = 0.5;
+    e.diag = 2;
+    e.post = 1;
+    e.par0 = 1;
+    dslash32(ctx, e);
+    return DDRW_OK;
+}
+
+ddrw_status colour_bicgstab_reliable(ddrw_ctx *ctx, int pid, const MassSet &ms, const float4 *b, float4 *x, int nrhs,
+                                     const std::vector<double> &thresh, int maxiter, int *iters, int colour)
+{
+    if (pid == 16) return eo_bicgstab_reliable<PrecH>(ctx, ms, b, x, nrhs, thresh, maxiter, iters, colour);
+    return eo_bicgstab_reliable<PrecB>(ctx, ms, b, x, nrhs, thresh, maxiter, iters, colour);
+}
+
 // One inner solve of the defect correction in storage policy P: e = D^-1 rhs (rhs scaled by
 // scale_d[r] into P's storage, the solution scaled back by scale_d[nrhs + r] and added to x, which
 // is zeroed first on the first cycle).
@@ -347,6 +485,18 @@ static ddrw_status inner_solve(ddrw_ctx *ctx, const MassSet &ms, const double2 *
     if ((st = workspace(ctx, nb, fl, &bl))) return st;
     if ((st = workspace(ctx, ne, fl, &el))) return st;
     VecRange all{V, 0, V, 12 * V, nrhs};
+    if (P::ID != 32 && ctx->reliable_updates()) {
+        // 16-bit Krylov vectors with reliable updates into FP32 fields
+        float4 *b32, *x32;
+        const size_t f32 = sizeof(float4) * 6 * V * nrhs;
+        if ((st = workspace(ctx, "full_b32", f32, (void **)&b32))) return st;
+        if ((st = workspace(ctx, "full_e32", f32, (void **)&x32))) return st;
+        to_low<PrecS>(ctx, all, 6 * V, rhs, b32, scale_d);
+        if ((st = eo_bicgstab_reliable<P>(ctx, ms, b32, x32, nrhs, th, maxiter, iters))) return st;
+        if (first) DDRW_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double2) * 12 * V * nrhs, ctx->stream));
+        add_low<PrecS>(ctx, all, 6 * V, x32, x, scale_d + nrhs);
+        return DDRW_OK;
+    }
     to_low<P>(ctx, all, rsl, rhs, (E *)bl, scale_d);
     if (P::ID == 32 && ctx->outer_method == 1 && sap_supported(ctx)) {
         // Schwarz-preconditioned flexible GCR on the FP32 fields
@@ -618,8 +768,9 @@ ddrw_status full_solve64(ddrw_ctx *ctx, const MassSet &ms, const double2 *b, dou
     const long V = ctx->V, rs64 = 12 * V;
     const size_t f64 = sizeof(double2) * rs64 * nrhs;
     const bool mixed = prec != DDRW_FP64;
-    // deepest relative residual an inner solve is asked for: what its storage reliably reaches
-    const double floor = prec == DDRW_MIXED_FP32 ? 1e-6 : prec == DDRW_MIXED_FP16 ? 1e-3 : 5e-3;
+    // deepest relative residual an inner solve is asked for: what its storage reliably reaches (16-bit
+    // storage with reliable updates reaches what their FP32 residuals reach)
+    const double floor = (prec == DDRW_MIXED_FP32 || ctx->reliable_updates()) ? 1e-6 : prec == DDRW_MIXED_FP16 ? 1e-3 : 5e-3;
     ddrw_status st;
     std::vector<double> bb, rr;
     if ((st = full_norms(ctx, b, nrhs, bb))) return st;

@@ -92,16 +92,24 @@ __device__ __forceinline__ void hop_dir_multi(const GeomDev &g, const Site<BL> &
 #pragma unroll
             for (int r = 0; r < NR; r++) {
                 Spinor<R> p;
-                P::load_spinor(in + r * rstride, (int)g.V, sf, p);
                 Half<R> h, w;
-                project<MU, -1>(p, h);
-                link_mul(L, h, w);
-                if (ph < 0)
+                if constexpr (Normed<P>::value) {
+                    R n;
+                    P::load_spinor_unscaled(in + r * rstride, (int)g.V, sf, p, n);
+                    project<MU, -1>(p, h);
+                    link_mul(L, h, w);
+                    reconstruct_add_scaled<MU, -1>(acc[r], w, ph < 0 ? -n : n);
+                } else {
+                    P::load_spinor(in + r * rstride, (int)g.V, sf, p);
+                    project<MU, -1>(p, h);
+                    link_mul(L, h, w);
+                    if (ph < 0)
 #pragma unroll
-                    for (int a = 0; a < 2; a++)
+                        for (int a = 0; a < 2; a++)
 #pragma unroll
-                        for (int c = 0; c < 3; c++) w.v[a][c] = -w.v[a][c];
-                reconstruct_add<MU, -1>(acc[r], w);
+                            for (int c = 0; c < 3; c++) w.v[a][c] = -w.v[a][c];
+                    reconstruct_add<MU, -1>(acc[r], w);
+                }
             }
         }
     }
@@ -113,16 +121,24 @@ __device__ __forceinline__ void hop_dir_multi(const GeomDev &g, const Site<BL> &
 #pragma unroll
             for (int r = 0; r < NR; r++) {
                 Spinor<R> p;
-                P::load_spinor(in + r * rstride, (int)g.V, sb, p);
                 Half<R> h, w;
-                project<MU, +1>(p, h);
-                link_dag_mul(L, h, w);
-                if (ph < 0)
+                if constexpr (Normed<P>::value) {
+                    R n;
+                    P::load_spinor_unscaled(in + r * rstride, (int)g.V, sb, p, n);
+                    project<MU, +1>(p, h);
+                    link_dag_mul(L, h, w);
+                    reconstruct_add_scaled<MU, +1>(acc[r], w, ph < 0 ? -n : n);
+                } else {
+                    P::load_spinor(in + r * rstride, (int)g.V, sb, p);
+                    project<MU, +1>(p, h);
+                    link_dag_mul(L, h, w);
+                    if (ph < 0)
 #pragma unroll
-                    for (int a = 0; a < 2; a++)
+                        for (int a = 0; a < 2; a++)
 #pragma unroll
-                        for (int c = 0; c < 3; c++) w.v[a][c] = -w.v[a][c];
-                reconstruct_add<MU, +1>(acc[r], w);
+                            for (int c = 0; c < 3; c++) w.v[a][c] = -w.v[a][c];
+                    reconstruct_add<MU, +1>(acc[r], w);
+                }
             }
         }
     }
@@ -149,8 +165,23 @@ __device__ __forceinline__ void hop_tab(const GeomDev &g, int nf, int nb, int s,
 #pragma unroll
         for (int r = 0; r < NR; r++) {
             Spinor<R> p;
-            P::load_spinor(in + r * rstride, V, n, p);
             Half<R> h, w;
+            if constexpr (Normed<P>::value) {
+                R nrm;
+                P::load_spinor_unscaled(in + r * rstride, V, n, p, nrm);
+                if (flip) nrm = -nrm;
+                if (d == 0) {
+                    project<MU, -1>(p, h);
+                    link_mul(L, h, w);
+                    reconstruct_add_scaled<MU, -1>(acc[r], w, nrm);
+                } else {
+                    project<MU, +1>(p, h);
+                    link_dag_mul(L, h, w);
+                    reconstruct_add_scaled<MU, +1>(acc[r], w, nrm);
+                }
+                continue;
+            }
+            P::load_spinor(in + r * rstride, V, n, p);
             if (d == 0) {
                 project<MU, -1>(p, h);
                 link_mul(L, h, w);
@@ -247,11 +278,19 @@ __device__ __forceinline__ void hop_dir_sg(const GeomDev &g, const Site<BL> &st,
 #pragma unroll
     for (int r = 0; r < NR; r++) {
         Spinor<R> p;
-        P::load_spinor(in + r * rstride, (int)g.V, sn, p);
         Half<R> h, w;
-        project_sg<MU>(p, sg, h);
-        link_mul(L, h, w);
-        reconstruct_sg<MU>(acc[r], w, ph, sgph);
+        if constexpr (Normed<P>::value) {
+            R n;
+            P::load_spinor_unscaled(in + r * rstride, (int)g.V, sn, p, n);
+            project_sg<MU>(p, sg, h);
+            link_mul(L, h, w);
+            reconstruct_sg<MU>(acc[r], w, ph * n, sgph * n);
+        } else {
+            P::load_spinor(in + r * rstride, (int)g.V, sn, p);
+            project_sg<MU>(p, sg, h);
+            link_mul(L, h, w);
+            reconstruct_sg<MU>(acc[r], w, ph, sgph);
+        }
     }
 }
 
@@ -295,10 +334,18 @@ template <class P, int BL, int HOPSEL, int K> struct HopK {
                                                    Spinor<R> &acc)
     {
         Spinor<R> p;
-        P::decode(sr, p);
         Link<R> L;
         P::decode_link(ur, L);
         Half<R> h, w;
+        if constexpr (Normed<P>::value) {
+            P::decode_unscaled(sr, p);
+            project<MU, -DIR>(p, h);
+            if (DIR > 0) link_mul(L, h, w);
+            else link_dag_mul(L, h, w);
+            reconstruct_add_scaled<MU, -DIR>(acc, w, ph < 0 ? -sr.n : sr.n);
+            return;
+        }
+        P::decode(sr, p);
         project<MU, -DIR>(p, h);
         if (DIR > 0) link_mul(L, h, w);
         else link_dag_mul(L, h, w);

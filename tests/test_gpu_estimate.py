@@ -70,6 +70,62 @@ def test_block_solve(case, colour):
     assert info["block_iters_max"] > 0
 
 
+@pytest.mark.parametrize("form", [(1, 64, 1, 0), (1, 128, 1, 1)], ids=["unrolled", "rolled"])
+def test_mixed_block_solve_double_single_forms(case, form):
+    """Mixed block solves (FP32 persistent kernel, FP64 defect correction) whose block-restricted
+    double-single residuals run in the unrolled and in the rolled hop code: the true residual of
+    every block system by the oracle's block operator."""
+    ctx, lat, dims = case["ctx"], case["lat"], case["dims"]
+    ctx.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-12)
+    ctx.stencil_config(*form)
+    try:
+        b = synth.spinor_field(dims, seed=35, nrhs=2)
+        x = np.zeros_like(b)
+        ctx.solve_block(0, case["m2"], b, x, nrhs=2)
+        col = lat.colour()
+        for r in range(2):
+            bc = b[r].copy()
+            bc[col != 0] = 0
+            res = bc - lat.apply(case["m2"], x[r], rows=0, cols=0)
+            assert np.linalg.norm(res) / np.linalg.norm(bc) <= 1e-12
+    finally:
+        ctx.stencil_config(0)
+        ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+
+
+@pytest.mark.parametrize("prec", [binding.MIXED_FP16, binding.MIXED_BF16], ids=["fp16", "bf16"])
+def test_16bit_krylov_block_solves_with_reliable_updates(case, prec):
+    """16-bit block solves through the Krylov-loop BiCGStab on a colour's blocks with reliable
+    updates into FP32: the true residual of every block system by the oracle's block operator,
+    and the estimate through them against the oracle's chain."""
+    ctx, lat, dims = case["ctx"], case["lat"], case["dims"]
+    ctx.set_solver(prec, tol_outer=1e-10, tol_block=1e-12)
+    ctx.set_low_precision(True, True)
+    ctx.set_block_solver(1)
+    try:
+        b = synth.spinor_field(dims, seed=36, nrhs=2)
+        col = lat.colour()
+        for colour in (0, 1):
+            x = np.zeros_like(b)
+            info = ctx.solve_block(colour, case["m2"], b, x, nrhs=2)
+            for r in range(2):
+                bc = b[r].copy()
+                bc[col != colour] = 0
+                res = bc - lat.apply(case["m2"], x[r], rows=colour, cols=colour)
+                assert np.linalg.norm(res) / np.linalg.norm(bc) <= 1e-12, (colour, r)
+                assert np.max(np.abs(x[r][col != colour])) == 0.0
+            assert info["block_iters_max"] > 0
+        nhit = 1
+        eta = oc.noise_packed(2, 8, nhit, ctx.nP * 12)
+        e, _, _, _ = ctx.estimate(nhit, eta=torch.from_numpy(eta.reshape(nhit, ctx.nP, 4, 3)).cuda())
+        want = lat.exponent(case["m1"], case["m2"], lat.unpack(eta[0]))["e"]
+        assert close(e[0], want), (e[0], want)
+    finally:
+        ctx.set_block_solver(0)
+        ctx.set_low_precision(True, False)
+        ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+
+
 @pytest.mark.parametrize("colour", [0, 1])
 def test_block_solve_krylov_loop(case, colour):
     """Block solves through the graph-captured BiCGStab on all blocks of the colour at once (FP32
@@ -119,7 +175,37 @@ def test_fused_inner_products(case):
             e[fuse], _, _, _ = ctx.estimate(1, seed=2, hit_offset=3)
         assert close(e[True][0], e[False][0], tol=1e-9)
     finally:
-        ctx.fuse_reductions(True)
+        ctx.fuse_reductions(False)
+        ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+
+
+@pytest.mark.parametrize("prec", [binding.MIXED_FP16, binding.MIXED_BF16], ids=["fp16", "bf16"])
+def test_16bit_reliable_updates(case, prec):
+    """16-bit Krylov vectors with reliable updates into FP32: the full solve reaches the outer
+    tolerance by the oracle's operator in no more defect-correction cycles than FP32 storage needs
+    (the plain 16-bit form restarts more often), with 16-bit and with FP32 block solves, and the
+    estimate agrees with the oracle's exponents."""
+    ctx, lat, dims = case["ctx"], case["lat"], case["dims"]
+    b = synth.spinor_field(dims, seed=37, nrhs=2)
+    try:
+        cycles = {}
+        for reliable, block16 in ((True, True), (True, False), (False, True)):
+            ctx.set_solver(prec, tol_outer=1e-10, tol_block=1e-12)
+            ctx.set_low_precision(reliable, block16)
+            x = np.zeros_like(b)
+            info = ctx.solve_D(case["m2"], b, x, nrhs=2)
+            for r in range(2):
+                assert rel(lat.apply(case["m2"], x[r]), b[r]) <= 1e-10, (reliable, block16, r)
+            cycles[(reliable, block16)] = info["cycles"]
+        assert cycles[(True, True)] <= 3 and cycles[(True, True)] <= cycles[(False, True)], cycles
+        ctx.set_low_precision(True, True)
+        nhit = 1
+        eta = oc.noise_packed(2, 9, nhit, ctx.nP * 12)
+        e, _, _, _ = ctx.estimate(nhit, eta=torch.from_numpy(eta.reshape(nhit, ctx.nP, 4, 3)).cuda())
+        want = lat.exponent(case["m1"], case["m2"], lat.unpack(eta[0]))["e"]
+        assert close(e[0], want), (e[0], want)
+    finally:
+        ctx.set_low_precision(True, False)
         ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
 
 

@@ -38,6 +38,9 @@ def test_interpolation_and_one_flavour_match_oracle(dims, l):
             assert close(out["exponents"][i - 1, j], res["e"]), (i, j)
             assert abs(out["exponents_1f"][i - 1, j] - e1[-1]) <= 1e-8 * max(abs(e1[-1]), 1.0), (i, j)
         logw += oc.log_w(e)
+        X = np.exp(-np.array(e1))  # Eq. 12's sample form: E|X|^2 - |E X|^2 over |E X|^2
+        want_rv1 = np.sum(np.abs(X - X.mean()) ** 2) / (nhit - 1) / abs(X.mean()) ** 2
+        assert abs(out["rel_var_1f"][i - 1] - want_rv1) <= 1e-6 * max(want_rv1, 1e-12), (i, want_rv1)
         f1 = np.mean(np.exp(-np.array(e1))).real
         logw1 += np.log(abs(f1))
         sign *= np.sign(f1)
