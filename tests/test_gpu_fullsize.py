@@ -72,8 +72,9 @@ def test_mixed_estimate_matches_fp64_at_full_size(full, prec):
 # ---- direct parity with the oracle at the paper-shaped sizes (Sec. 2: 64x32^3 with 8^4 blocks,
 # 48x24^3 with 6^4 blocks): the oracle's exponents of sampled noise vectors, written by
 # tests/golden/make_fullsize_oracle.py (five FP64 CGNR solves each), against the benchmark's own
-# launch configuration (FP32 inner solves, FP64 defect correction, residual 1e-10, block
-# tolerance 1e-10, every hit and target mass of one step in one batched call)
+# launch configuration (FP16-storage inner solves with reliable updates and FP32 block solves --
+# the default -- or FP32 inner solves; FP64 defect correction, residual 1e-10, block tolerance
+# 1e-10, every hit and target mass of one step in one batched call)
 
 import json
 import os
@@ -104,11 +105,12 @@ def _check_against_golden(E, m2s, nhit, doc):
     return len(doc["entries"])
 
 
-def test_bench_configuration_matches_oracle_at_64x32x32x32(full):
+@pytest.mark.parametrize("prec", [binding.MIXED_FP16, binding.MIXED_FP32], ids=["fp16", "fp32"])
+def test_bench_configuration_matches_oracle_at_64x32x32x32(full, prec):
     ctx, lat = full
     doc = _golden("oracle_exponents_64x32x32x32.json")
     m2s, nhit = [0.018, 0.015, 0.010], 16
-    ctx.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-10)
+    ctx.set_solver(prec, tol_outer=1e-10, tol_block=1e-10)
     E, LW, _, info = ctx.estimate_masses(m2s, nhit, seed=doc["noise_seed"], hit_offset=0)
     assert _check_against_golden(E, m2s, nhit, doc) >= 1
     E = np.asarray(E, dtype=np.float64).reshape(len(m2s), nhit)
@@ -118,7 +120,8 @@ def test_bench_configuration_matches_oracle_at_64x32x32x32(full):
     assert info["true_rel_residual"] <= 1e-10
 
 
-def test_48x24x24x24_matches_oracle():
+@pytest.mark.parametrize("prec", [binding.MIXED_FP16, binding.MIXED_FP32], ids=["fp16", "fp32"])
+def test_48x24x24x24_matches_oracle(prec):
     doc = _golden("oracle_exponents_48x24x24x24.json")
     dims, l, m2s, nhit = (48, 24, 24, 24), 6, [0.015], 32
     U = synth.gauge_field(dims, doc["eps"], seed=doc["gauge_seed"])
@@ -126,7 +129,7 @@ def test_48x24x24x24_matches_oracle():
     try:
         ctx.load_gauge(torch.from_numpy(U).cuda())
         ctx.set_params(doc["csw"], doc["m1"], m2s[0])
-        ctx.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-10)
+        ctx.set_solver(prec, tol_outer=1e-10, tol_block=1e-10)
         E, _, _, info = ctx.estimate_masses(m2s, nhit, seed=doc["noise_seed"], hit_offset=0)
         assert _check_against_golden(E, m2s, nhit, doc) >= 1
         assert info["true_rel_residual"] <= 1e-10
