@@ -96,12 +96,15 @@ ddrw_status ddrw_suppP_size(ddrw_ctx *ctx, long *n_sites);
 ddrw_status ddrw_volume(ddrw_ctx *ctx, long *n_sites);
 
 /* Load the gauge field U[V][4][3][3][2] (host or device); builds the clover term with the csw of
- * the last ddrw_set_params() (csw = 0 before it).  The field is copied; the caller keeps U. */
+ * the last ddrw_set_params() (csw = 0 before it) and recomputes, in place, the in-block inverses
+ * of every mass in use.  The field is copied; the caller keeps U.  A host field goes through a
+ * device staging buffer that the context keeps for the next configuration (72 V doubles). */
 ddrw_status ddrw_load_gauge(ddrw_ctx *ctx, const double *U);
 
 /* csw (clover coefficient), m1 (ensemble mass) and m2 (target mass) of W(U, m1, m2) (Eq. 2),
  * and the time boundary condition of the quark fields (0 periodic, 1 antiperiodic).  Rebuilds the
- * clover term and the per-mass inverses of the site-diagonal part. */
+ * clover term and the per-mass inverses of the site-diagonal part; the same values again on a
+ * built configuration change nothing and return at once. */
 ddrw_status ddrw_set_params(ddrw_ctx *ctx, double csw, double m1, double m2, int antiperiodic_t);
 
 /* Solver settings: precision of the inner solves, relative true-residual target of the outer
@@ -120,6 +123,14 @@ ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, dou
  * BiCGStab.  Both reach the same FP64 true residual through the defect correction.
  * DDRW_EINVAL outside method 0..1, ncy 1..16, nmr 1..32, nkv 1..16. */
 ddrw_status ddrw_set_outer_solver(ddrw_ctx *ctx, int method, int ncy, int nmr, int nkv);
+
+/* Launch shape of the persistent block solver (Sec. 1: all blocks of a colour in one launch) for
+ * blocks of at least 512 sites per parity: form 0 one CTA of 256 threads per block and right-hand
+ * side; 1 the same with 512 threads; 2 (FP32 storage, an even number of right-hand sides per mass
+ * slot; else 1) one CTA of 512 threads per block and pair of right-hand sides, each link and clover
+ * term loaded once for both.  -1 (the default): the first launch of each shape times the candidates
+ * on its real arguments and keeps the fastest.  Same results in every form.  DDRW_EINVAL outside -1..2. */
+ddrw_status ddrw_block_config(ddrw_ctx *ctx, int form);
 
 /* The 16-bit storage precisions (DDRW_MIXED_FP16, DDRW_MIXED_BF16).  reliable_updates != 0 (the
  * default): the full-lattice inner solves keep the BiCGStab vectors in 16-bit storage with a per-site
@@ -311,7 +322,8 @@ ddrw_status ddrw_use_graphs(ddrw_ctx *ctx, int enable, long *graph_launches);
  * (unrolled, rolled, batched loads, register caps, neighbour table) with CUDA events and keeps the fastest.  Tuned choices are
  * also kept for the process, by device and lattice geometry, and reused by later contexts of the
  * same geometry.  enable = 0 uses a fixed choice; either call clears the tuned tables of the context
- * and of the process.  The report lists the tuned shapes, one per line. */
+ * and of the process.  The report lists the tuned shapes, one per line, and the launch shapes the
+ * persistent block solver chose (ddrw_block_config). */
 ddrw_status ddrw_autotune(ddrw_ctx *ctx, int enable);
 ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
 

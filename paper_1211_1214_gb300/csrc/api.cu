@@ -663,13 +663,22 @@ static ddrw_status rebuild(ddrw_ctx *ctx)
     // 36 planes of V elements each: three "fields" of 12 planes
     split64(ctx, ctx->U64, ctx->Udd, ctx->V, 0, 0, ctx->V, 0, 1, 3, 12L * ctx->V);
     split64(ctx, ctx->C64, ctx->Cdd, ctx->V, 0, 0, ctx->V, 0, 1, 3, 12L * ctx->V);
-    free_inverses(ctx);
+    // in-block inverses of the masses already in use: recomputed in place, so that the captured
+    // graphs, which hold their addresses, stay valid; a long list of masses is dropped instead
+    if (ctx->inv.size() > (size_t)MAXM + 2) free_inverses(ctx);
+    for (auto &mi : ctx->inv) {
+        build_inverse(ctx, mi.m, mi);
+        f32_to_low(ctx, mi.A32, mi.A16, 18L * ctx->V, false);
+        f32_to_low(ctx, mi.A32, mi.Ab16, 18L * ctx->V, true);
+    }
     MassInv *mi;
     ddrw_status st = mass_inverse(ctx, ctx->m1, &mi);
     if (st) return st;
     if (ctx->m2 != ctx->m1) st = mass_inverse(ctx, ctx->m2, &mi);
     if (st) return st;
-    return sync(ctx);
+    st = sync(ctx);
+    ctx->built = st == DDRW_OK;
+    return st;
 }
 
 ddrw_status ddrw_load_gauge(ddrw_ctx *ctx, const double *U)
@@ -692,16 +701,10 @@ ddrw_status ddrw_load_gauge(ddrw_ctx *ctx, const double *U)
                                         cudaMemcpyDeviceToDevice, ctx->stream));
     }
     ctx->have_gauge = true;
-    st = rebuild(ctx);
-    // the staging buffer for the gauge field is large and used once: release it
-    auto it = ctx->ws.find("stage_gauge");
-    if (it != ctx->ws.end()) {
-        clear_graphs(ctx);
-        cudaStreamSynchronize(ctx->stream);
-        cudaFree(it->second.p);
-        ctx->ws.erase(it);
-    }
-    return st;
+    ctx->built = false;
+    // the staging buffer stays for the next configuration (allocating it again would drop the
+    // captured graphs, like any workspace allocation)
+    return rebuild(ctx);
 }
 
 ddrw_status ddrw_set_params(ddrw_ctx *ctx, double csw, double m1, double m2, int antiperiodic_t)
@@ -709,10 +712,15 @@ ddrw_status ddrw_set_params(ddrw_ctx *ctx, double csw, double m1, double m2, int
     if (!ctx) return DDRW_EINVAL;
     if (!(csw == csw) || !(m1 == m1) || !(m2 == m2)) return set_error(ctx, DDRW_EINVAL, "NaN parameter");
     cudaSetDevice(ctx->device);
+    const int ap = antiperiodic_t ? 1 : 0;
+    // the same parameters on a built configuration: nothing to recompute
+    if (ctx->have_gauge && ctx->built && csw == ctx->csw && m1 == ctx->m1 && m2 == ctx->m2 && ap == ctx->antiperiodic)
+        return DDRW_OK;
     ctx->csw = csw;
     ctx->m1 = m1;
     ctx->m2 = m2;
-    ctx->antiperiodic = antiperiodic_t ? 1 : 0;
+    ctx->antiperiodic = ap;
+    ctx->built = false;
     if (!ctx->have_gauge) return DDRW_OK;
     return rebuild(ctx);
 }
@@ -737,6 +745,14 @@ ddrw_status ddrw_set_dirichlet(ddrw_ctx *ctx, int cut)
     for (int mu = 0; mu < 4 && cut > 0; mu++)
         if (ctx->dims[mu] % cut) return set_error(ctx, DDRW_EINVAL, "cut must divide every lattice dimension");
     ctx->cut = cut;
+    return DDRW_OK;
+}
+
+ddrw_status ddrw_block_config(ddrw_ctx *ctx, int form)
+{
+    if (!ctx) return DDRW_EINVAL;
+    if (form < -1 || form > 2) return set_error(ctx, DDRW_EINVAL, "block-solver launch shape must be -1, 0, 1 or 2");
+    ctx->blk_form = form;
     return DDRW_OK;
 }
 

@@ -115,6 +115,7 @@ struct ddrw_ctx {
     double csw = 0.0, m1 = 0.0, m2 = 0.0;
     int antiperiodic = 0;
     bool have_gauge = false;
+    bool built = false;  // clover term and in-block inverses match the gauge field and the parameters
     ddrw_prec prec = DDRW_FP64;
     double tol_outer = 1e-10, tol_block = 1e-13;
     int maxiter = 20000;
@@ -186,6 +187,7 @@ struct ddrw_ctx {
     int pinned_nr = 0, pinned_nt = 128, pinned_nw = 1, pinned_roll = 0;
     std::map<std::array<int, 8>, ddrw::TuneEntry> tune;
     std::map<std::array<int, 3>, int> blk_tune;  // block-solver launch shape (blocksolve.cuh)
+    int blk_form = -1;                             // pinned block-solver launch shape, -1: tuned
 
     // kernel timing (ddrw_profile): CUDA events around the instrumented launches
     bool prof_on = false;

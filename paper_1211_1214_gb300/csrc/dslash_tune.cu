@@ -198,6 +198,12 @@ ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len)
                  kv.second.roll, kv.second.ms);
         s += line;
     }
+    for (auto &kv : ctx->blk_tune) {  // persistent block solver: key (storage, l, 2 nrhs + pairs allowed)
+        char line[120];
+        snprintf(line, sizeof line, "block fp%d l=%d nrhs=%d -> form=%d\n", kv.first[0], kv.first[1], kv.first[2] / 2,
+                 kv.second);
+        s += line;
+    }
     if ((long)s.size() + 1 > len) return set_error(ctx, DDRW_EINVAL, "report buffer too small");
     memcpy(buf, s.c_str(), s.size() + 1);
     return DDRW_OK;

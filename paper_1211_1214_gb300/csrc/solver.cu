@@ -49,6 +49,71 @@ __global__ void k_bicg_cond(cudaGraphConditionalHandle h, const KScal *sc, int n
     cudaGraphSetConditional(h, (act && it < maxiter) ? 1u : 0u);
 }
 
+// sets the while-condition of a captured 16-bit Krylov loop with reliable updates: continue while no
+// right-hand side of the pass (act0) has stopped or fallen below delta2 times its residual at the
+// last reliable update, and the iteration cap is not reached
+__global__ void k_rel_cond(cudaGraphConditionalHandle h, const KScal *sc, const double *rr_ref, const int *act0,
+                           int nrhs, int *count, int step, int maxiter, double delta2)
+{
+    int any = 0, trig = 0;
+    for (int r = 0; r < nrhs; r++) {
+        if (!act0[r]) continue;
+        any = 1;
+        if (!sc[r].active || sc[r].rr < delta2 * rr_ref[r]) trig = 1;
+    }
+    int it = (*count += step);
+    cudaGraphSetConditional(h, (any && !trig && it < maxiter) ? 1u : 0u);
+}
+
+using LoopKey = std::array<uintptr_t, 13 + 2 * MAXM>;
+
+// The graph of a device-controlled Krylov loop: a conditional while-node whose body is `check`
+// iterations followed by the condition kernel (cond launches it with the node's handle); built on
+// first use of the key, then taken from ctx->graphs.
+static ddrw_status loop_graph(ddrw_ctx *ctx, const LoopKey &key, int check,
+                              const std::function<ddrw_status()> &iteration,
+                              const std::function<void(cudaGraphConditionalHandle)> &cond, cudaGraphExec_t *out)
+{
+    auto git = ctx->graphs.find(key);
+    if (git != ctx->graphs.end()) {
+        *out = git->second.exec;
+        return DDRW_OK;
+    }
+    cudaGraph_t graph = nullptr;
+    DDRW_CUDA_CHECK(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle handle;
+    DDRW_CUDA_CHECK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    DDRW_CUDA_CHECK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    DDRW_CUDA_CHECK(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    ddrw_status cap = DDRW_OK;
+    for (int k = 0; k < check && !cap; k++) cap = iteration();
+    ++ctx->launches;
+    cond(handle);
+    cudaGraph_t captured = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(ctx->stream, &captured);
+    if (cap || ec != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        if (cap) return cap;
+        return set_cuda_error(ctx, ec, "cudaStreamEndCapture", __FILE__, __LINE__);
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    if (ei != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return set_cuda_error(ctx, ei, "cudaGraphInstantiate", __FILE__, __LINE__);
+    }
+    ctx->graphs[key] = GraphEntry{graph, exec};
+    *out = exec;
+    return DDRW_OK;
+}
+
 template <class P> void stencil(ddrw_ctx *ctx, const DslashCall &c)
 {
     switch (P::ID) {
@@ -210,7 +275,7 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
         // iterations and the condition kernel; no host round trip until convergence or the cap
         int *count;
         if ((st = workspace(ctx, "eo_graph_count", sizeof(int), (void **)&count))) return st;
-        std::array<uintptr_t, 13 + 2 * MAXM> key{};
+        LoopKey key{};
         key[0] = P::ID + 1000 * (colour + 1);  // the colour selects other launches
         key[1] = (uintptr_t)nrhs;
         key[2] = (uintptr_t)maxiter;
@@ -223,43 +288,11 @@ ddrw_status eo_bicgstab(ddrw_ctx *ctx, const MassSet &ms, const typename P::SEle
             memcpy(&key[13 + 2 * k], &mk, sizeof(double));
             key[14 + 2 * k] = (uintptr_t)ainv_for(ms.inv[k], P::ID);
         }
-        auto git = ctx->graphs.find(key);
         cudaGraphExec_t exec = nullptr;
-        if (git != ctx->graphs.end()) {
-            exec = git->second.exec;
-        } else {
-            cudaGraph_t graph = nullptr;
-            DDRW_CUDA_CHECK(cudaGraphCreate(&graph, 0));
-            cudaGraphConditionalHandle handle;
-            DDRW_CUDA_CHECK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
-            cudaGraphNodeParams cp = {};
-            cp.type = cudaGraphNodeTypeConditional;
-            cp.conditional.handle = handle;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            cudaGraphNode_t node;
-            DDRW_CUDA_CHECK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            DDRW_CUDA_CHECK(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0,
-                                                          cudaStreamCaptureModeThreadLocal));
-            ddrw_status cap = DDRW_OK;
-            for (int k = 0; k < check && !cap; k++) cap = iteration();
-            ++ctx->launches;
-            k_bicg_cond<<<1, 1, 0, ctx->stream>>>(handle, sc, nrhs, count, check, maxiter);
-            cudaGraph_t captured = nullptr;
-            cudaError_t ec = cudaStreamEndCapture(ctx->stream, &captured);
-            if (cap || ec != cudaSuccess) {
-                cudaGraphDestroy(graph);
-                if (cap) return cap;
-                return set_cuda_error(ctx, ec, "cudaStreamEndCapture", __FILE__, __LINE__);
-            }
-            cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
-            if (ei != cudaSuccess) {
-                cudaGraphDestroy(graph);
-                return set_cuda_error(ctx, ei, "cudaGraphInstantiate", __FILE__, __LINE__);
-            }
-            ctx->graphs[key] = GraphEntry{graph, exec};
-        }
+        if ((st = loop_graph(ctx, key, check, iteration, [&](cudaGraphConditionalHandle h) {
+                 k_bicg_cond<<<1, 1, 0, ctx->stream>>>(h, sc, nrhs, count, check, maxiter);
+             }, &exec)))
+            return st;
         const int it0 = it;
         DDRW_CUDA_CHECK(cudaMemcpyAsync(count, &it, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
         DDRW_CUDA_CHECK(cudaGraphLaunch(exec, ctx->stream));
@@ -410,11 +443,61 @@ static ddrw_status eo_bicgstab_reliable(ddrw_ctx *ctx, const MassSet &ms, const 
     int it = 0;
     bool all_done = true;
     for (int k = 0; k < nrhs; k++) all_done &= done[k] != 0;
+    constexpr int check = 4;
+    auto iteration = [&]() -> ddrw_status {
+        return bicg_iteration<P16>(ctx, ms, nrhs, rs_, ev16, x16, r, rh, p, v, t, tmp, sc, colour);
+    };
+    // between reliable updates the iterations run as one CUDA graph (after a first eager pass that
+    // tunes the launches): a conditional while-node stops when an update is due or at the cap
+    int *count = nullptr, *act0_d = nullptr;
+    double *rref_d = nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(ctx->stream, &cs);
+    const bool graphs = ctx->use_graphs && cs == cudaStreamCaptureStatusNone;
+    if (graphs) {
+        if ((st = workspace(ctx, "rel_count", sizeof(int), (void **)&count))) return st;
+        if ((st = workspace(ctx, "rel_rref", sizeof(double) * nrhs, (void **)&rref_d))) return st;
+        if ((st = workspace(ctx, "rel_act0", sizeof(int) * nrhs, (void **)&act0_d))) return st;
+    }
+    std::vector<int> act0(nrhs);
+    bool eager_pass = true;
     while (!all_done && it < maxiter) {
-        for (int k = 0; k < 4; k++, it++)
-            if ((st = bicg_iteration<P16>(ctx, ms, nrhs, rs_, ev16, x16, r, rh, p, v, t, tmp, sc, colour))) return st;
-        DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, sc, sizeof(KScal) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
-        DDRW_SYNC(ctx);
+        if (graphs && !eager_pass) {
+            LoopKey key{};
+            key[0] = 100000 + P16::ID + 1000 * (colour + 1);
+            key[1] = (uintptr_t)nrhs;
+            key[2] = (uintptr_t)maxiter;
+            const void *ptrs[9] = {r, rh, p, v, t, tmp, x16, sc, count};
+            for (int k = 0; k < 9; k++) key[3 + k] = (uintptr_t)ptrs[k];
+            key[12] = (uintptr_t)ms.n;
+            for (int k = 0; k < ms.n; k++) {
+                double mk = ms.m[k];
+                memcpy(&key[13 + 2 * k], &mk, sizeof(double));
+                key[14 + 2 * k] = (uintptr_t)ainv_for(ms.inv[k], P16::ID);
+            }
+            cudaGraphExec_t exec = nullptr;
+            if ((st = loop_graph(ctx, key, check, iteration, [&](cudaGraphConditionalHandle h) {
+                     k_rel_cond<<<1, 1, 0, ctx->stream>>>(h, sc, rref_d, act0_d, nrhs, count, check, maxiter, delta2);
+                 }, &exec)))
+                return st;
+            for (int k = 0; k < nrhs; k++) act0[k] = done[k] ? 0 : 1;
+            DDRW_CUDA_CHECK(cudaMemcpyAsync(rref_d, rr_ref.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+            DDRW_CUDA_CHECK(cudaMemcpyAsync(act0_d, act0.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, ctx->stream));
+            const int it0 = it;
+            DDRW_CUDA_CHECK(cudaMemcpyAsync(count, &it, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+            DDRW_CUDA_CHECK(cudaGraphLaunch(exec, ctx->stream));
+            ++ctx->graph_launches;
+            DDRW_CUDA_CHECK(cudaMemcpyAsync(&it, count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+            DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, sc, sizeof(KScal) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+            DDRW_SYNC(ctx);  // (also keeps the host arrays above alive until the copies have run)
+            ctx->launches += (long)(it - it0) * 9 + (it - it0) / check;
+        } else {
+            for (int k = 0; k < check; k++, it++)
+                if ((st = iteration())) return st;
+            DDRW_CUDA_CHECK(cudaMemcpyAsync(hs, sc, sizeof(KScal) * nrhs, cudaMemcpyDeviceToHost, ctx->stream));
+            DDRW_SYNC(ctx);
+        }
+        eager_pass = false;
         bool trigger = it >= maxiter, any_active = false;
         for (int k = 0; k < nrhs; k++) {
             if (done[k]) continue;

@@ -74,8 +74,9 @@ __device__ __forceinline__ void hop_sum(const GeomDev &g, const Site<BL> &st, lo
 }
 
 // Hops of NR right-hand sides at once (fields rstride elements apart): the link of each hop is
-// loaded, and for two-row storage reconstructed, once for all NR.
-template <class P, int BL, int HOPSEL, int MU, int NR>
+// loaded, and for two-row storage reconstructed, once for all NR.  RO = false reads the input
+// through the coherent path (kernels that write their own hop input, the persistent block solver).
+template <class P, int BL, int HOPSEL, int MU, int NR, bool RO = true>
 __device__ __forceinline__ void hop_dir_multi(const GeomDev &g, const Site<BL> &st, long s,
                                               const typename P::SElem *in, long rstride,
                                               const typename P::UElem *__restrict__ U,
@@ -93,14 +94,15 @@ __device__ __forceinline__ void hop_dir_multi(const GeomDev &g, const Site<BL> &
             for (int r = 0; r < NR; r++) {
                 Spinor<R> p;
                 Half<R> h, w;
-                if constexpr (Normed<P>::value) {
+                if constexpr (Normed<P>::value && RO) {
                     R n;
                     P::load_spinor_unscaled(in + r * rstride, (int)g.V, sf, p, n);
                     project<MU, -1>(p, h);
                     link_mul(L, h, w);
                     reconstruct_add_scaled<MU, -1>(acc[r], w, ph < 0 ? -n : n);
                 } else {
-                    P::load_spinor(in + r * rstride, (int)g.V, sf, p);
+                    if (RO) P::load_spinor(in + r * rstride, (int)g.V, sf, p);
+                    else P::load_spinor_rw(in + r * rstride, (int)g.V, sf, p);
                     project<MU, -1>(p, h);
                     link_mul(L, h, w);
                     if (ph < 0)
@@ -122,14 +124,15 @@ __device__ __forceinline__ void hop_dir_multi(const GeomDev &g, const Site<BL> &
             for (int r = 0; r < NR; r++) {
                 Spinor<R> p;
                 Half<R> h, w;
-                if constexpr (Normed<P>::value) {
+                if constexpr (Normed<P>::value && RO) {
                     R n;
                     P::load_spinor_unscaled(in + r * rstride, (int)g.V, sb, p, n);
                     project<MU, +1>(p, h);
                     link_dag_mul(L, h, w);
                     reconstruct_add_scaled<MU, +1>(acc[r], w, ph < 0 ? -n : n);
                 } else {
-                    P::load_spinor(in + r * rstride, (int)g.V, sb, p);
+                    if (RO) P::load_spinor(in + r * rstride, (int)g.V, sb, p);
+                    else P::load_spinor_rw(in + r * rstride, (int)g.V, sb, p);
                     project<MU, +1>(p, h);
                     link_dag_mul(L, h, w);
                     if (ph < 0)

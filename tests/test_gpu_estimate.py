@@ -70,6 +70,33 @@ def test_block_solve(case, colour):
     assert info["block_iters_max"] > 0
 
 
+@pytest.mark.parametrize("form", [0, 1, 2], ids=["nt", "2nt", "pairs"])
+def test_block_solver_launch_shapes(case, form):
+    """The persistent block solver in each launch shape (one right-hand side per CTA of NT or 2 NT
+    threads, or pairs of right-hand sides per CTA sharing every link and clover load; blocks of at
+    least 512 sites per parity, else the single shape), FP32 inner solves with FP64 defect
+    correction, on 4 right-hand sides: the true residual of every block system by the oracle's block
+    operator, nothing written outside the colour."""
+    ctx, lat, dims = case["ctx"], case["lat"], case["dims"]
+    ctx.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-12)
+    ctx.block_config(form)
+    try:
+        b = synth.spinor_field(dims, seed=38, nrhs=4)
+        x = np.zeros_like(b)
+        info = ctx.solve_block(1, case["m1"], b, x, nrhs=4)
+        col = lat.colour()
+        for r in range(4):
+            bc = b[r].copy()
+            bc[col != 1] = 0
+            res = bc - lat.apply(case["m1"], x[r], rows=1, cols=1)
+            assert np.linalg.norm(res) / np.linalg.norm(bc) <= 1e-12, r
+            assert np.max(np.abs(x[r][col != 1])) == 0.0
+        assert info["block_iters_max"] > 0
+    finally:
+        ctx.block_config(-1)
+        ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+
+
 @pytest.mark.parametrize("form", [(1, 64, 1, 0), (1, 128, 1, 1)], ids=["unrolled", "rolled"])
 def test_mixed_block_solve_double_single_forms(case, form):
     """Mixed block solves (FP32 persistent kernel, FP64 defect correction) whose block-restricted

@@ -66,6 +66,10 @@ def test_bad_arguments(ctx):
         with pytest.raises(binding.DDRWError) as ei:
             c.stencil_config(*cfg)  # form, right-hand sides per thread or CTA shape out of range
         assert ei.value.status == 1
+    for form in (-2, 3):
+        with pytest.raises(binding.DDRWError) as ei:
+            c.block_config(form)  # no such block-solver launch shape
+        assert ei.value.status == 1
     st = c.L.ddrw_apply_D(c._h, 0.1, None, None, 1)
     assert st == 1
     assert b"bad argument" in c.L.ddrw_last_error(c._h)

@@ -119,3 +119,51 @@ def test_krylov_only_graph_mode_gives_the_same_estimate_without_whole_chunk_grap
     with pytest.raises(binding.DDRWError) as ei:
         c.use_graphs(3)
     assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("mode", [2, 1], ids=["krylov_graphs", "whole_estimate_graphs"])
+def test_new_configuration_reuses_graphs_and_inverses(mode):
+    """A context that loads a second gauge field (host buffer, as an ensemble loop does) and then
+    sets the same parameters again keeps its captured graphs and the addresses of its in-block
+    inverses, whose contents are recomputed: its estimate on the second field is bit-identical to
+    that of a fresh context on that field, and a changed target mass is picked up."""
+    dims, l, m2s = (8, 8, 8, 16), 4, [0.045, 0.04]
+    U1 = synth.gauge_field(dims, 0.25, seed=1)
+    U2 = synth.gauge_field(dims, 0.25, seed=2)
+    a = binding.Context(dims, (l,) * 4)
+    b = binding.Context(dims, (l,) * 4)
+    try:
+        for c in (a, b):
+            c.set_solver(binding.MIXED_FP16, tol_outer=1e-10, tol_block=1e-12)
+            c.use_graphs(mode)
+        a.load_gauge(U1)
+        a.set_params(1.5, 0.05, m2s[0])
+        for _ in range(3):  # eager, captured, replayed
+            a.estimate_masses(m2s, 2, seed=5)
+        n0 = a.use_graphs()
+        a.load_gauge(U2)
+        a.set_params(1.5, 0.05, m2s[0])  # unchanged: no rebuild
+        e_a = [a.estimate_masses(m2s, 2, seed=s)[0] for s in (6, 7, 8)]
+        b.load_gauge(U2)
+        b.set_params(1.5, 0.05, m2s[0])
+        e_b = [b.estimate_masses(m2s, 2, seed=s)[0] for s in (6, 7, 8)]
+        for x, y in zip(e_a, e_b):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+        assert a.use_graphs() > n0  # the graphs captured on the first field were replayed
+        # a new m1 rebuilds the inverses: the same as a fresh context with that m1
+        a.set_params(1.5, 0.06, m2s[0])
+        b.set_params(1.5, 0.06, m2s[0])
+        ea = np.asarray(a.estimate_masses(m2s, 2, seed=9)[0])
+        c = binding.Context(dims, (l,) * 4)
+        try:
+            c.set_solver(binding.MIXED_FP16, tol_outer=1e-10, tol_block=1e-12)
+            c.use_graphs(mode)
+            c.load_gauge(U2)
+            c.set_params(1.5, 0.06, m2s[0])
+            ec = np.asarray(c.estimate_masses(m2s, 2, seed=9)[0])
+        finally:
+            c.close()
+        assert np.allclose(ea, ec, rtol=1e-9, atol=1e-12)
+    finally:
+        a.close()
+        b.close()
