@@ -63,8 +63,9 @@ typedef enum {
     DDRW_MIXED_FP32 = 1, /* inner solves in FP32 storage and arithmetic; defect correction on FP64
                             fields with residuals b - D x in double-single arithmetic (ddrw_apply_D_ds) */
     DDRW_MIXED_FP16 = 2, /* inner solves on FP16 storage (per-site FP32 norm for spinors, two-row
-                            links, 16-bit clover and inverses) with FP32 arithmetic; FP64 defect
-                            correction as for DDRW_MIXED_FP32 */
+                            links, 16-bit clover and inverses) with FP32 arithmetic and reliable
+                            updates into FP32 (ddrw_set_low_precision; block solves in FP32 by
+                            default); FP64 defect correction as for DDRW_MIXED_FP32 */
     DDRW_MIXED_BF16 = 3  /* as DDRW_MIXED_FP16 with BF16 storage */
 } ddrw_prec;
 

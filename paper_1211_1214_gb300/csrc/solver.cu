@@ -10,8 +10,9 @@
 //                        is one CUDA graph: a conditional while-node whose condition kernel stops on
 //                        convergence of every right-hand side or at the iteration cap.
 //   precision:           FP64 defect correction around the inner solve:
-//                        r = b - D x (FP64 stencil), inner solve D e = r / ||r|| in FP64 (FP64 path)
-//                        or FP32 (mixed path), x += ||r|| e, until ||b - D x|| <= tol ||b||.
+//                        r = b - D x (FP64 or double-single stencil), inner solve D e = r / ||r|| in
+//                        FP64 (FP64 path), FP32, or 16-bit storage with reliable updates into FP32
+//                        (mixed paths), x += ||r|| e, until ||b - D x|| <= tol ||b||.
 #include <algorithm>
 #include <array>
 #include <cmath>
