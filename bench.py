@@ -92,6 +92,7 @@ def stencil_one_rhs(ctx, w, prec, key, hbm, tol_block):
         except binding.DDRWError:
             pass  # the iteration cap ends the solve; the launches are what is measured
     n, ms, by = ctx.profile_read(key)
+    units = ctx.profile_units(key)
     ctx.profile(False)
     ctx.use_graphs(GRAPH_MODE)
     ctx.set_solver(prec, tol_outer=1e-10, tol_block=tol_block)
@@ -102,6 +103,7 @@ def stencil_one_rhs(ctx, w, prec, key, hbm, tol_block):
     gbs = by / (ms / 1e3) / 1e9
     return {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "launches": n,
             "avg_launch_ms": ms / n, "algorithmic_bytes_per_launch": by / n,
+            "bytes_per_site_update": by / units if units else None,
             "what": "same stencil kernel, 1 right-hand side per launch (links and clover not amortised)"}
 
 
@@ -520,6 +522,19 @@ def main():
                            "site_updates_per_launch": kunits / max(nl, 1),
                            "peak_source": "profiles/alu_peaks_gb300.md (measured FP32 FMA rate)"}
     roofline["one_rhs"] = stencil_one_rhs(ctx, w, prec, key, hbm, tol_block)
+    # the batched launches' site-update rate against the most any launch of this stencil could
+    # reach with one right-hand side: the measured copy bandwidth over its compulsory bytes per
+    # site update at R = 1 (links and clover read once per site update)
+    o = roofline["one_rhs"]
+    if kms > 0 and o and o.get("bytes_per_site_update"):
+        rate = kunits / (kms / 1e3)
+        roof1 = hbm * 1e9 / o["bytes_per_site_update"]
+        roofline["site_update_rate"] = {
+            "achieved": rate, "one_rhs_hbm_roof": roof1, "unit": "site updates/s", "frac": rate / roof1,
+            "what": "site updates per second of the batched launches against the HBM roof of the same "
+                    "stencil at one right-hand side per launch (measured copy bandwidth / its compulsory "
+                    "bytes per site update); batching moves the kernel off the HBM roof, this says how "
+                    "much work per second it delivers relative to that roof"}
 
     out = {"metric": METRIC, "value": value, "unit": "estimates/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",

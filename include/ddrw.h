@@ -340,8 +340,10 @@ ddrw_status ddrw_autotune_report(ddrw_ctx *ctx, char *buf, long len);
  * other storage precisions run form 5 instead), 9 / 10 (pipelined, FP32 storage only: each thread
  * copies the neighbour spinor and link of its hops into a two-slot shared-memory ring with 16-byte
  * asynchronous copies two hops ahead of the arithmetic; at least 2 / 3 CTAs per SM; other
- * precisions run form 5); roll 2-4 and 7-10 need nr = 1, roll 5 and 6
- * nr <= 2.
+ * precisions run form 5) or 11 (fully rolled: one body for the eight hops, the direction and
+ * the signs chosen at run time; used by the double-single residual stencil, which is limited by
+ * instruction fetch, and as form 0 elsewhere); roll 2-4 and 7-11 need nr = 1, roll 5 and 6
+ * nr <= 2.  The double-single stencil runs forms 0, 1 and 11, with nr = nw = 1.
  * A launch whose right-hand sides per mass slot are not a multiple of nr * nw runs with nr = nw = 1.
  * nr = 0 returns to autotuning.  DDRW_EINVAL for values outside these ranges.  A change drops the
  * captured CUDA graphs (they are captured again with the new form on next use). */

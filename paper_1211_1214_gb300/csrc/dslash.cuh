@@ -223,7 +223,8 @@ constexpr size_t STAGED_SMEM_MAX = (size_t)62 * 128 * 16;
 
 // ROLL selects the hop code form: 0 unrolled, 1 rolled, 2 / 3 batched loads of 4 / 8 hops,
 // 4 / 5 unrolled compiled for at least 3 / 2 CTAs of 256 threads per SM (<= 85 / 128 registers),
-// 6 / 7 as 5 / 4 with the neighbours read from the neighbour table instead of computed
+// 6 / 7 as 5 / 4 with the neighbours read from the neighbour table instead of computed,
+// 11 fully rolled (one body for the eight hops; double-single storage only)
 // RED != 0 adds the inner products of the output to the epilogue (red 1: conj(w) out; red 2:
 // conj(out) x and |out|^2), one partial per warp of 32 sites, summed in FP64 by k_bicg_fin; the
 // launcher only fuses launches whose output sites fill whole CTAs (no thread leaves early)
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(256, (ROLL == 4 || ROLL == 7) ? 3 : (ROLL == 5
     const long s = (long)(a.par0 + pp) * g.vh + (long)a.blk0 * BlockShape<BL>::VBH + (i - pp * nper);
     Site<BL> st;
     int4 n0;
-    if constexpr (ROLL >= 6) {
+    if constexpr (ROLL == 6 || ROLL == 7) {
         n0 = g.nbr[s];
     } else {
         decode_site<BL>(s, g, st);
@@ -260,7 +261,10 @@ __global__ void __launch_bounds__(256, (ROLL == 4 || ROLL == 7) ? 3 : (ROLL == 5
         if constexpr (ROLL == 2 || ROLL == 3) {  // batched loads, one right-hand side: 2 -> 4 hops, 3 -> 8 hops per batch
             static_assert(NR == 1, "batched hops take one right-hand side per thread");
             hop_batched<P, BL, HOPSEL, ROLL == 2 ? 4 : 8>(g, st, (int)s, in, a.U, acc[0]);
-        } else if constexpr (ROLL >= 6) {
+        } else if constexpr (ROLL == 11) {  // fully rolled, one right-hand side
+            static_assert(NR == 1, "the fully rolled form takes one right-hand side per thread");
+            hop_fully_rolled<P, BL, HOPSEL>(g, st, (int)s, in, a.U, acc[0]);
+        } else if constexpr (ROLL == 6 || ROLL == 7) {
             hop_tab<P, HOPSEL, 0, NR>(g, n0.x, n0.y, (int)s, in, a.rstride, a.U, acc);
             hop_tab<P, HOPSEL, 1, NR>(g, n0.z, n0.w, (int)s, in, a.rstride, a.U, acc);
             const int4 n1 = g.nbr[g.V + s];  // loaded here: fewer registers live over the first hops
@@ -546,7 +550,8 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
     if (c.hopsel == 2) cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
     // double-single: one right-hand side per thread, unrolled or rolled hop code (the rolled form
     // has half the code of the unrolled one, which is instruction-fetch bound)
-    if (std::is_same<P, PrecDD>::value) cfg.nr = 1, cfg.nw = 1, cfg.roll = (cfg.roll == 1 && c.hopsel != 2) ? 1 : 0;
+    if (std::is_same<P, PrecDD>::value)
+        cfg.nr = 1, cfg.nw = 1, cfg.roll = ((cfg.roll == 1 || cfg.roll == 11) && c.hopsel != 2) ? cfg.roll : 0;
     if (!std::is_same<P, PrecDD>::value && c.hopsel == 1 && (cfg.nr != 1 || (cfg.roll != 0 && cfg.roll != 5 && cfg.roll != 6)))
         cfg.nr = 1, cfg.nw = 1, cfg.roll = 0;
     if (c.hopsel == 1 && cfg.roll == 6 && !g.nbr) cfg.roll = 5;
@@ -615,6 +620,8 @@ void launch_cfg(ddrw_ctx *ctx, const DslashCall &c, const DsArgs<P> &a, DsConfig
     if constexpr (std::is_same<P, PrecDD>::value) {  // one right-hand side per thread
         if (c.hopsel == 0 && cfg.roll == 1) k_dslash<P, BL, 0, 1, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
         else if (c.hopsel == 1 && cfg.roll == 1) k_dslash<P, BL, 1, 1, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
+        else if (c.hopsel == 0 && cfg.roll == 11) k_dslash<P, BL, 0, 1, 11><<<grid, blk, 0, ctx->stream>>>(g, a);
+        else if (c.hopsel == 1 && cfg.roll == 11) k_dslash<P, BL, 1, 1, 11><<<grid, blk, 0, ctx->stream>>>(g, a);
         else if (c.hopsel == 0) k_dslash<P, BL, 0, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
         else if (c.hopsel == 1) k_dslash<P, BL, 1, 1><<<grid, blk, 0, ctx->stream>>>(g, a);
         else k_dslash<P, BL, 2, 1><<<grid, blk, 0, ctx->stream>>>(g, a);

@@ -46,7 +46,7 @@ std::array<long, 15> process_key(const ddrw_ctx *ctx, const std::array<int, 8> &
 // right-hand sides per thread each hop code form supports
 static bool form_allowed(int nr, int roll)
 {
-    if (roll < 0 || roll > 10) return false;
+    if (roll < 0 || roll > 11) return false;
     if ((roll >= 2 && roll <= 4) || roll >= 7) return nr == 1;
     if (roll == 5 || roll == 6) return nr <= 2;
     return true;
@@ -92,18 +92,20 @@ DsConfig tuned_config(ddrw_ctx *ctx, const DslashCall &c, int prec, int bl,
     DsConfig best = def;
     float best_ms = 1e30f;
     const int nrs[3] = {1, 2, 4}, nts[3] = {64, 128, 256}, nws[2] = {1, 2}, nws8[4] = {1, 2, 4, 8};
-    for (int roll = 0; roll < 11; roll++)
+    for (int roll = 0; roll < 12; roll++)
     for (int nr : nrs) {
         // the batched and register-capped forms are for 32- and 16-bit storage: with FP64 data
-        // they spill; the staged and pipelined forms are for FP32 storage
+        // they spill; the staged and pipelined forms are for FP32 storage; the fully rolled form
+        // for the double-single residual
         if (c.nrhs % nr || rpm % nr || (roll >= 2 && prec == 64) || !form_allowed(nr, roll) ||
-            (roll >= 8 && prec != 32))
+            (roll >= 8 && roll <= 10 && prec != 32) || (roll == 11 && prec != 128))
             continue;
-        // launches restricted to the hops inside the blocks come in the unrolled, register-capped
-        // and table forms with one right-hand side per thread
-        if (c.hopsel != 0 && (nr != 1 || (roll != 0 && roll != 5 && roll != 6))) continue;
-        // double-single launches: unrolled or rolled, one right-hand side per thread, one row
-        if (prec == 128 && (nr != 1 || roll > 1)) continue;
+        // double-single launches: unrolled, rolled or fully rolled, one right-hand side per thread,
+        // one row (also for the hops inside the blocks)
+        if (prec == 128 && (nr != 1 || (roll > 1 && roll != 11))) continue;
+        // other launches restricted to the hops inside the blocks come in the unrolled,
+        // register-capped and table forms with one right-hand side per thread
+        if (prec != 128 && c.hopsel != 0 && (nr != 1 || (roll != 0 && roll != 5 && roll != 6))) continue;
         const int *nwl = roll == 8 ? nws8 : nws;
         const int nnw = roll == 8 ? 4 : 2;
         for (int iw = 0; iw < nnw; iw++)

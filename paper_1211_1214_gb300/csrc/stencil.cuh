@@ -313,6 +313,82 @@ __device__ __forceinline__ void hop_multi_rolled(const GeomDev &g, const Site<BL
     }
 }
 
+// ---- fully rolled form (one right-hand side): the eight hops share one body -- one link
+// multiply, the direction entering the spin projection and reconstruction through a switch of
+// four short cases and the signs through negations, never through multiplications (with
+// double-single numbers a multiplication by -1 would cost a two-product).  About a quarter of the
+// rolled form's code for instruction-fetch-bound storage (the double-single residual).
+
+template <typename R> __device__ __forceinline__ cpx<R> neg_if(cpx<R> a, bool n) { return n ? -a : a; }
+
+// h = psi_u + sg e_mu psi_d, sg = -1 (fwd, the (1 - g_mu) projector) or +1
+template <typename R>
+__device__ __forceinline__ void project_rt(const Spinor<R> &p, int mu, bool fwd, Half<R> &h)
+{
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const cpx<R> d0 = p.v[2][c], d1 = p.v[3][c];
+        cpx<R> e0, e1;  // e_mu psi_d
+        switch (mu) {
+        case 0: e0 = -d0; e1 = -d1; break;
+        case 1: e0 = timesMinusI(d1); e1 = timesMinusI(d0); break;
+        case 2: e0 = -d1; e1 = d0; break;
+        default: e0 = timesMinusI(d0); e1 = timesI(d1); break;
+        }
+        h.v[0][c] = p.v[0][c] + neg_if(e0, fwd);
+        h.v[1][c] = p.v[1][c] + neg_if(e1, fwd);
+    }
+}
+
+// acc += ph (w, sg e_mu^dag w), ph = -1 when flip, sg as in project_rt
+template <typename R>
+__device__ __forceinline__ void reconstruct_rt(Spinor<R> &acc, const Half<R> &w, int mu, bool fwd, bool flip)
+{
+    const bool nd = fwd != flip;  // sg ph < 0
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const cpx<R> w0 = w.v[0][c], w1 = w.v[1][c];
+        cpx<R> f0, f1;  // e_mu^dag w
+        switch (mu) {
+        case 0: f0 = -w0; f1 = -w1; break;
+        case 1: f0 = timesI(w1); f1 = timesI(w0); break;
+        case 2: f0 = w1; f1 = -w0; break;
+        default: f0 = timesI(w0); f1 = timesMinusI(w1); break;
+        }
+        acc.v[0][c] = acc.v[0][c] + neg_if(w0, flip);
+        acc.v[1][c] = acc.v[1][c] + neg_if(w1, flip);
+        acc.v[2][c] = acc.v[2][c] + neg_if(f0, nd);
+        acc.v[3][c] = acc.v[3][c] + neg_if(f1, nd);
+    }
+}
+
+template <class P, int BL, int HOPSEL>
+__device__ __forceinline__ void hop_fully_rolled(const GeomDev &g, const Site<BL> &st, int s,
+                                                 const typename P::SElem *in,
+                                                 const typename P::UElem *__restrict__ U,
+                                                 Spinor<typename P::R> &acc)
+{
+    using R = typename P::R;
+#pragma unroll 1
+    for (int k = 0; k < 8; k++) {
+        const int mu = k >> 1;
+        const bool fwd = (k & 1) == 0;
+        bool cross;
+        int phi;
+        const int sn = neighbour<BL>(st, mu, fwd ? 1 : -1, g, &cross, &phi);
+        if (!(HOPSEL == 0 || (HOPSEL == 1 && !cross) || (HOPSEL == 2 && cross))) continue;
+        Link<R> L;
+        P::load_link(U, (int)g.V, mu, fwd ? s : sn, L);
+        if (!fwd) dagger(L);
+        Spinor<R> p;
+        P::load_spinor(in, (int)g.V, sn, p);
+        Half<R> h, w;
+        project_rt(p, mu, fwd, h);
+        link_mul(L, h, w);
+        reconstruct_rt(acc, w, mu, fwd, phi < 0);
+    }
+}
+
 // ---- batched form (one right-hand side): the loads of G hops are all issued before any of them
 // is used, so a site waits for memory 8 / G times instead of 8.  Hop k = 0..7 is direction
 // mu = k / 2, forward for even k, backward for odd k.

@@ -97,11 +97,12 @@ def test_block_solver_launch_shapes(case, form):
         ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
 
 
-@pytest.mark.parametrize("form", [(1, 64, 1, 0), (1, 128, 1, 1)], ids=["unrolled", "rolled"])
+@pytest.mark.parametrize("form", [(1, 64, 1, 0), (1, 128, 1, 1), (1, 64, 1, 11)],
+                         ids=["unrolled", "rolled", "fully_rolled"])
 def test_mixed_block_solve_double_single_forms(case, form):
     """Mixed block solves (FP32 persistent kernel, FP64 defect correction) whose block-restricted
-    double-single residuals run in the unrolled and in the rolled hop code: the true residual of
-    every block system by the oracle's block operator."""
+    double-single residuals run in the unrolled, the rolled and the fully rolled hop code: the true
+    residual of every block system by the oracle's block operator."""
     ctx, lat, dims = case["ctx"], case["lat"], case["dims"]
     ctx.set_solver(binding.MIXED_FP32, tol_outer=1e-10, tol_block=1e-12)
     ctx.stencil_config(*form)

@@ -61,7 +61,7 @@ def test_bad_arguments(ctx):
     with pytest.raises(binding.DDRWError) as ei:
         c.estimate_interp(9, 2)  # at most 8 interpolation steps
     assert ei.value.status == 1
-    for cfg in [(2, 64, 1, 7), (4, 64, 1, 6), (2, 64, 1, 4), (1, 64, 1, 11), (2, 64, 1, 8), (1, 256, 1, 8),
+    for cfg in [(2, 64, 1, 7), (4, 64, 1, 6), (2, 64, 1, 4), (1, 64, 1, 12), (2, 64, 1, 11), (2, 64, 1, 8), (1, 256, 1, 8),
                 (2, 64, 1, 9), (2, 128, 1, 10), (1, 48, 1, 0), (1, 256, 2, 0)]:
         with pytest.raises(binding.DDRWError) as ei:
             c.stencil_config(*cfg)  # form, right-hand sides per thread or CTA shape out of range

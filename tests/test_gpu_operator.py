@@ -56,13 +56,14 @@ def test_apply_D_host_pointers_and_multi_rhs(setup):
         assert rel(y[r], lat.apply(0.1, x[r])) < 1e-12
 
 
-@pytest.mark.parametrize("form", [None, (1, 64, 1, 0), (1, 128, 1, 1)], ids=["tuned", "unrolled", "rolled"])
+@pytest.mark.parametrize("form", [None, (1, 64, 1, 0), (1, 128, 1, 1), (1, 64, 1, 11)],
+                         ids=["tuned", "unrolled", "rolled", "fully_rolled"])
 @pytest.mark.parametrize("m", [0.045, -0.3])
 def test_apply_D_double_single(setup, m, form):
     """The double-single stencil of the mixed defect correction: FP32 pairs carry ~48 significant
     bits and each two-sum / two-product loses a few units of 2^-48, so the result must sit within
     1e-12 of the oracle's FP64 operator -- five orders below what FP32 arithmetic could give; in
-    the tuned launch form and pinned to the unrolled and the rolled hop code."""
+    the tuned launch form and pinned to the unrolled, the rolled and the fully rolled hop code."""
     ctx, lat, dims = setup
     x = synth.spinor_field(dims, seed=7, nrhs=2)
     y = np.zeros_like(x)
