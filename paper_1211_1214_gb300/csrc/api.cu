@@ -830,11 +830,10 @@ ddrw_status ddrw_apply_block(ddrw_ctx *ctx, int rows, int cols, double m, const 
         if (rows == cols) {
             c.diag = 1;
             c.hopsel = 1;
+            dslash64(ctx, c);
         } else {
-            c.diag = 0;
-            c.hopsel = 2;
+            hop_between64(ctx, rows, fin, fout, nrhs, -0.5);  // fout is zero on every row (above)
         }
-        dslash64(ctx, c);
     } else {
         if (cols != DDRW_ALL) zero_colour64(ctx, fin, 1 - cols, nrhs);
         c.diag = 1;

@@ -335,6 +335,9 @@ struct DslashCall {
     double *red_part = nullptr;
 };
 void dslash64(ddrw_ctx *ctx, const DslashCall &c);
+// out (rows of colour `rows`) += beta H_{rows <- other colour} in: the hops between blocks in FP64,
+// one launch per direction over the face sites (hops.cu); other rows untouched
+void hop_between64(ddrw_ctx *ctx, int rows, const double2 *in, double2 *out, int nrhs, double beta);
 void dslash32(ddrw_ctx *ctx, const DslashCall &c);
 void dslash16(ddrw_ctx *ctx, const DslashCall &c);   // FP16 storage, FP32 arithmetic
 void dslashb16(ddrw_ctx *ctx, const DslashCall &c);  // BF16 storage, FP32 arithmetic

@@ -228,21 +228,11 @@ static ddrw_status apply_schur_eo64(ddrw_ctx *ctx, double m, const double2 *in, 
     return DDRW_OK;
 }
 
-// hop between blocks: out (colour rows) = -1/2 H_{rows <- other colour} in ; other rows untouched
+// hop between blocks: out (colour rows) += -1/2 H_{rows <- other colour} in (out is zero on those
+// rows before: every caller clears it); other rows untouched
 static void hop_between(ddrw_ctx *ctx, int rows, const double2 *in, double2 *out, int nrhs)
 {
-    DslashCall c;
-    c.in = in;
-    c.out = out;
-    c.rstride = 12 * ctx->V;
-    c.nrhs = nrhs;
-    c.beta = -0.5;
-    c.hopsel = 2;
-    c.par0 = 0;
-    c.npar = 2;
-    c.blk0 = rows == DDRW_BLACK ? 0 : ctx->nblk_c;
-    c.nblk = ctx->nblk_c;
-    dslash64(ctx, c);
+    hop_between64(ctx, rows, in, out, nrhs, -0.5);
 }
 
 static double elapsed(std::chrono::steady_clock::time_point t0)

@@ -381,7 +381,7 @@ void gamma5(ddrw_ctx *ctx, const double2 *x, double2 *y, int nrhs)
     k_gamma5<<<(unsigned)((n * nrhs + 255) / 256), 256, 0, ctx->stream>>>(n, ctx->V, nrhs, n, x, y);
 }
 
-void hop_between64(ddrw_ctx *ctx, int rows, const double2 *in, double2 *out, int nrhs)
+void hop_between_rows64(ddrw_ctx *ctx, int rows, const double2 *in, double2 *out, int nrhs)
 {
     DslashCall c;
     c.in = in;
@@ -464,7 +464,7 @@ extern "C" ddrw_status ddrw_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64
     if (st == DDRW_ENOCONV) conv = st;
     else if (st) return st;
     DDRW_CUDA_CHECK(cudaMemsetAsync(T1, 0, f1, ctx->stream));
-    hop_between64(ctx, DDRW_BLACK, T2, T1, nhit);
+    hop_between_rows64(ctx, DDRW_BLACK, T2, T1, nhit);
     GeomDev g = geom_dev(ctx);
     {
         dim3 grid((unsigned)((V + 127) / 128), (unsigned)nhit);
@@ -479,10 +479,10 @@ extern "C" ddrw_status ddrw_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64
         return DDRW_OK;
     };
     DDRW_CUDA_CHECK(cudaMemsetAsync(T1, 0, f2, ctx->stream));
-    hop_between64(ctx, DDRW_WHITE, V2, T1, R2);  // E v
+    hop_between_rows64(ctx, DDRW_WHITE, V2, T1, R2);  // E v
     if ((st = bsolve(DDRW_WHITE, T1, A))) return st;  // a = W^-1 E v
     DDRW_CUDA_CHECK(cudaMemsetAsync(T1, 0, f2, ctx->stream));
-    hop_between64(ctx, DDRW_BLACK, A, T1, R2);  // C a
+    hop_between_rows64(ctx, DDRW_BLACK, A, T1, R2);  // C a
     if ((st = bsolve(DDRW_BLACK, T1, Q))) return st;  // q = B^-1 C a
     // g5 z in both slots
     gamma5(ctx, Zf, T1, nhit);
@@ -490,7 +490,7 @@ extern "C" ddrw_status ddrw_force(ddrw_ctx *ctx, int nhit, uint64_t seed, uint64
     if ((st = bsolve(DDRW_BLACK, T1, T2))) return st;  // B^-1 g5 z
     gamma5(ctx, T2, ZT, R2);                            // zt = g5 B^-1 g5 z
     DDRW_CUDA_CHECK(cudaMemsetAsync(T1, 0, f2, ctx->stream));
-    hop_between64(ctx, DDRW_WHITE, T2, T1, R2);  // E g5 zt
+    hop_between_rows64(ctx, DDRW_WHITE, T2, T1, R2);  // E g5 zt
     if ((st = bsolve(DDRW_WHITE, T1, T2))) return st;
     gamma5(ctx, T2, WT, R2);  // wt = g5 W^-1 E g5 zt
     // rho = q - a (into Q), sigma = a - v (into A)
