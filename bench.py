@@ -70,7 +70,9 @@ def aggregate_rate(world: int, units_per_rank_step: int, steps: int, t_max_ms: f
 
 GRAPH_MODE = 2  # ddrw_use_graphs mode of the timed steps (--graph-mode)
 FLOPS_PER_SITE_UPDATE = 1872.0  # hopping 1320 + clover 504 + diagonal 48 flops per site and right-hand side
-FP32_FMA_TFLOPS = 70.06  # measured FP32 FMA throughput of one GB300 (profiles/alu_peaks_gb300.md)
+# FP32 FMA peak of one GB300 from its unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop
+# x 2.07 GHz (the maximum SM clock, the clock the bench runs at)
+FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def stencil_one_rhs(ctx, w, prec, key, hbm, tol_block):
@@ -520,7 +522,7 @@ def main():
         roofline["alu"] = {"achieved": tflops, "peak": FP32_FMA_TFLOPS, "unit": "TFLOP/s",
                            "frac": tflops / FP32_FMA_TFLOPS, "flops_per_site_update": FLOPS_PER_SITE_UPDATE,
                            "site_updates_per_launch": kunits / max(nl, 1),
-                           "peak_source": "profiles/alu_peaks_gb300.md (measured FP32 FMA rate)"}
+                           "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (unit counts and maximum SM clock)"}
     roofline["one_rhs"] = stencil_one_rhs(ctx, w, prec, key, hbm, tol_block)
     # the batched launches' site-update rate against the most any launch of this stencil could
     # reach with one right-hand side: the measured copy bandwidth over its compulsory bytes per
