@@ -125,6 +125,14 @@ ddrw_status ddrw_set_solver(ddrw_ctx *ctx, ddrw_prec prec, double tol_outer, dou
  * DDRW_EINVAL outside method 0..1, ncy 1..16, nmr 1..32, nkv 1..16. */
 ddrw_status ddrw_set_outer_solver(ddrw_ctx *ctx, int method, int ncy, int nmr, int nkv);
 
+/* Right-hand sides per chunk of the batched estimates (ddrw_estimate, ddrw_estimate_masses,
+ * ddrw_estimate_interp, ddrw_force): max_rhs = 0 (the default) sizes the chunks from the free
+ * device memory (about 4 KB per site and right-hand side); max_rhs >= 1 caps them, which leaves
+ * memory to the caller or exercises the chunking.  Whole masses go into one chunk while their hits
+ * fit, else one mass and as many hits as fit; the results agree with one chunk to the solver
+ * tolerances.  DDRW_EINVAL for max_rhs < 0. */
+ddrw_status ddrw_set_max_rhs(ddrw_ctx *ctx, int max_rhs);
+
 /* Launch shape of the persistent block solver (Sec. 1: all blocks of a colour in one launch) for
  * blocks of at least 512 sites per parity: form 0 one CTA of 256 threads per block and right-hand
  * side; 1 the same with 512 threads; 2 (FP32 storage, an even number of right-hand sides per mass

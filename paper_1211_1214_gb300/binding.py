@@ -23,7 +23,7 @@ _STATUS = {0: "DDRW_OK", 1: "DDRW_EINVAL", 2: "DDRW_ENOMEM", 3: "DDRW_ECUDA", 4:
 #: every entry point declared in include/ddrw.h
 EXPORTS = ["ddrw_create", "ddrw_destroy", "ddrw_last_error", "ddrw_suppP_size", "ddrw_volume", "ddrw_load_gauge",
            "ddrw_set_params", "ddrw_set_solver", "ddrw_set_outer_solver", "ddrw_set_block_solver",
-           "ddrw_fuse_reductions", "ddrw_set_low_precision", "ddrw_block_config", "ddrw_set_dirichlet",
+           "ddrw_fuse_reductions", "ddrw_set_low_precision", "ddrw_block_config", "ddrw_set_max_rhs", "ddrw_set_dirichlet",
            "ddrw_block_factor_nested", "ddrw_apply_sap", "ddrw_apply_D", "ddrw_apply_block", "ddrw_solve_block",
            "ddrw_solve_D", "ddrw_apply_schur", "ddrw_apply_dA", "ddrw_solve_schur", "ddrw_noise", "ddrw_estimate",
            "ddrw_estimate_masses", "ddrw_profile", "ddrw_profile_read", "ddrw_solve_block_noalloc",
@@ -86,6 +86,7 @@ def load(path: str | None = None):
         "ddrw_fuse_reductions": (st, [vp, ctypes.c_int]),
         "ddrw_set_low_precision": (st, [vp, ctypes.c_int, ctypes.c_int]),
         "ddrw_block_config": (st, [vp, ctypes.c_int]),
+        "ddrw_set_max_rhs": (st, [vp, ctypes.c_int]),
         "ddrw_block_factor_nested": (st, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, dp, dp, dp]),
         "ddrw_apply_D": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
         "ddrw_apply_D_ds": (st, [vp, ctypes.c_double, dp, dp, ctypes.c_int]),
@@ -330,6 +331,10 @@ class Context:
         """16-bit precisions: reliable updates in the inner solves; 16-bit or FP32 block solves."""
         self._check(self.L.ddrw_set_low_precision(self._h, int(bool(reliable_updates)), int(bool(block_solves_16bit))),
                     "ddrw_set_low_precision")
+
+    def set_max_rhs(self, max_rhs=0):
+        """Right-hand sides per chunk of the batched estimates (0: sized from free device memory)."""
+        self._check(self.L.ddrw_set_max_rhs(self._h, int(max_rhs)), "ddrw_set_max_rhs")
 
     def block_config(self, form=-1):
         """Persistent block-solver launch shape: -1 tuned, 0 / 1 one right-hand side per CTA of 256 /

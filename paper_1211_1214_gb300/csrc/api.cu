@@ -748,6 +748,14 @@ ddrw_status ddrw_set_dirichlet(ddrw_ctx *ctx, int cut)
     return DDRW_OK;
 }
 
+ddrw_status ddrw_set_max_rhs(ddrw_ctx *ctx, int max_rhs)
+{
+    if (!ctx) return DDRW_EINVAL;
+    if (max_rhs < 0) return set_error(ctx, DDRW_EINVAL, "max_rhs must be >= 0");
+    ctx->max_rhs = max_rhs;
+    return DDRW_OK;
+}
+
 ddrw_status ddrw_block_config(ddrw_ctx *ctx, int form)
 {
     if (!ctx) return DDRW_EINVAL;

@@ -70,6 +70,32 @@ def test_block_solve(case, colour):
     assert info["block_iters_max"] > 0
 
 
+@pytest.mark.parametrize("max_rhs", [1, 3])
+def test_chunked_estimates_agree_with_one_chunk(case, max_rhs):
+    """The batched estimates split into chunks of at most max_rhs right-hand sides (one mass and
+    some of its hits per chunk) give the one-chunk exponents and log W to the solver tolerance: the
+    mass sweep of Eq. 3 over two target masses and the N = 2 interpolation of Eq. 8, FP16 storage."""
+    ctx, m1, m2 = case["ctx"], case["m1"], case["m2"]
+    m2s, nhit = [m2, 0.5 * (m1 + m2)], 4
+    ctx.set_solver(binding.MIXED_FP16, tol_outer=1e-10, tol_block=1e-10)
+    try:
+        E0, L0, _, _ = ctx.estimate_masses(m2s, nhit, seed=13, hit_offset=2)
+        I0 = ctx.estimate_interp(2, 2, seed=14, hit_offset=1)
+        ctx.set_max_rhs(max_rhs)
+        E1, L1, _, _ = ctx.estimate_masses(m2s, nhit, seed=13, hit_offset=2)
+        I1 = ctx.estimate_interp(2, 2, seed=14, hit_offset=1)
+    finally:
+        ctx.set_max_rhs(0)
+        ctx.set_solver(binding.FP64, tol_outer=1e-10, tol_block=1e-13)
+    E0, E1 = np.asarray(E0).reshape(-1), np.asarray(E1).reshape(-1)
+    assert np.all(np.abs(E1 - E0) <= 1e-8 * np.maximum(np.abs(E0), 1.0)), (E0, E1)
+    for a, b in zip(np.asarray(L1).reshape(-1), np.asarray(L0).reshape(-1)):
+        assert close(a, b)
+    a, b = np.asarray(I1["exponents"]).reshape(-1), np.asarray(I0["exponents"]).reshape(-1)
+    assert np.all(np.abs(a - b) <= 1e-8 * np.maximum(np.abs(b), 1.0))
+    assert close(I1["logW"], I0["logW"])
+
+
 @pytest.mark.parametrize("form", [0, 1, 2], ids=["nt", "2nt", "pairs"])
 def test_block_solver_launch_shapes(case, form):
     """The persistent block solver in each launch shape (one right-hand side per CTA of NT or 2 NT

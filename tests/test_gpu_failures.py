@@ -70,6 +70,9 @@ def test_bad_arguments(ctx):
         with pytest.raises(binding.DDRWError) as ei:
             c.block_config(form)  # no such block-solver launch shape
         assert ei.value.status == 1
+    with pytest.raises(binding.DDRWError) as ei:
+        c.set_max_rhs(-1)  # chunks hold at least one right-hand side (0: from free memory)
+    assert ei.value.status == 1
     st = c.L.ddrw_apply_D(c._h, 0.1, None, None, 1)
     assert st == 1
     assert b"bad argument" in c.L.ddrw_last_error(c._h)
