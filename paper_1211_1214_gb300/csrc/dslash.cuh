@@ -281,7 +281,34 @@ __global__ void __launch_bounds__(256, (ROLL == 4 || ROLL == 7) ? 3 : (ROLL == 5
 #pragma unroll
         for (int r = 0; r < NR; r++) scale(acc[r], a.beta);
     }
-    if (a.diag) {
+    if constexpr (std::is_same<P, PrecDD>::value) {
+        // double-single: one chirality body run twice (the clover multiply in FP32 pairs is large,
+        // and this kernel is limited by instruction fetch)
+        if (a.diag) {
+            const typename P::SElem *x = a.x + roff;
+#pragma unroll 1
+            for (int ch = 0; ch < 2; ch++) {
+                R c[36];
+                cpx<R> v6[6], o6[6];
+                P::load_chiral(x, g.V, s, ch, v6);
+                if (a.diag == 1) {
+                    P::load_clover(a.Cl, g.V, s, ch, c);
+                    herm6_mul<R>(c, a.mass4[r0 / a.rpm], v6, o6);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 6; k++) o6[k] = v6[k];
+                }
+                if (ch == 0) {
+#pragma unroll
+                    for (int k = 0; k < 6; k++) acc[0].v[k / 3][k % 3] = acc[0].v[k / 3][k % 3] + a.alpha * o6[k];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 6; k++)
+                        acc[0].v[2 + k / 3][k % 3] = acc[0].v[2 + k / 3][k % 3] + a.alpha * o6[k];
+                }
+            }
+        }
+    } else if (a.diag) {
         const typename P::SElem *x = a.x + roff;
 #pragma unroll
         for (int ch = 0; ch < 2; ch++) {
