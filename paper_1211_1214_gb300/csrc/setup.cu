@@ -72,18 +72,77 @@ __global__ void k_bw_links(long V, const int4 *__restrict__ nbr, const float4 *_
 
 template <int BL> void clover_launch(ddrw_ctx *ctx);
 
-// A(m)^-1 = ((4 + m) + C_ch)^-1 per chirality, Gauss-Jordan with partial pivoting in FP64
-__global__ void k_inverse(long V, const double2 *__restrict__ C64, double mass, double2 *A64, float4 *A32)
+// The inverse of the Hermitian 6x6 block A = (4 + m) + H (H packed: 6 real diagonal entries, then
+// the 15 upper entries at 6 + 2 herm_off(i, j)) by the factorisation A = L D L^dag (L unit lower
+// triangular, D real diagonal) without pivoting, then A^-1 = X^dag D^-1 X with X = L^-1; all in
+// registers with the loops unrolled.  Returns false if a pivot is not clearly nonzero (then the
+// caller falls back to Gauss-Jordan with partial pivoting).
+__device__ __forceinline__ bool herm6_inverse_ldl(const double *r, double mass, double *o)
 {
-    long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= V) return;
-    for (int ch = 0; ch < 2; ch++) {
-        double r[36];
-        for (int k = 0; k < 18; k++) {
-            double2 v = C64[((long)ch * 18 + k) * V + s];
-            r[2 * k] = v.x;
-            r[2 * k + 1] = v.y;
+    cpx<double> L[6][6];
+    double d[6], dinv[6];
+    double scale = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; i++) scale = fmax(scale, fabs(4.0 + mass + r[i]));
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+        double dj = 4.0 + mass + r[j];
+#pragma unroll
+        for (int k = 0; k < j; k++) dj -= (L[j][k].re * L[j][k].re + L[j][k].im * L[j][k].im) * d[k];
+        if (!(fabs(dj) > 1e-10 * scale)) return false;
+        d[j] = dj;
+        dinv[j] = 1.0 / dj;
+#pragma unroll
+        for (int i = j + 1; i < 6; i++) {
+            const int q = 6 + 2 * herm_off(j, i);
+            cpx<double> a = {r[q], -r[q + 1]};  // A[i][j] = conj(A[j][i])
+#pragma unroll
+            for (int k = 0; k < j; k++) {
+                const cpx<double> t = cmulc(L[j][k], L[i][k]);  // conj(L[j][k]) L[i][k]
+                a = {a.re - d[k] * t.re, a.im - d[k] * t.im};
+            }
+            L[i][j] = {a.re * dinv[j], a.im * dinv[j]};
         }
+    }
+    // X = L^-1 (unit lower triangular)
+    cpx<double> X[6][6];
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+#pragma unroll
+        for (int i = j + 1; i < 6; i++) {
+            cpx<double> a = {-L[i][j].re, -L[i][j].im};
+#pragma unroll
+            for (int k = j + 1; k < i; k++) a = a - cmul(L[i][k], X[k][j]);
+            X[i][j] = a;
+        }
+    }
+    // A^-1_ij = sum_{k >= max(i, j)} conj(X_ki) X_kj / d_k  (X_kk = 1)
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        double s = dinv[i];
+#pragma unroll
+        for (int k = i + 1; k < 6; k++) s += (X[k][i].re * X[k][i].re + X[k][i].im * X[k][i].im) * dinv[k];
+        o[i] = s;
+#pragma unroll
+        for (int j = i + 1; j < 6; j++) {
+            cpx<double> s2 = {X[j][i].re * dinv[j], -X[j][i].im * dinv[j]};  // k = j: conj(X_ji) X_jj
+#pragma unroll
+            for (int k = j + 1; k < 6; k++) {
+                const cpx<double> t = cmulc(X[k][i], X[k][j]);
+                s2 = {s2.re + t.re * dinv[k], s2.im + t.im * dinv[k]};
+            }
+            const int q = 6 + 2 * herm_off(i, j);
+            o[q] = s2.re;
+            o[q + 1] = s2.im;
+        }
+    }
+    return true;
+}
+
+// the same by Gauss-Jordan with partial pivoting (any nonsingular block)
+__device__ __noinline__ void herm6_inverse_gj(const double *r, double mass, double *o)
+{
+    {
         cpx<double> A[6][12];
         for (int i = 0; i < 6; i++)
             for (int j = 0; j < 12; j++) A[i][j] = {0.0, 0.0};
@@ -115,7 +174,6 @@ __global__ void k_inverse(long V, const double2 *__restrict__ C64, double mass, 
                 for (int j = 0; j < 12; j++) A[i][j] = A[i][j] - cmul(f, A[c][j]);
             }
         }
-        double o[36];
         for (int i = 0; i < 6; i++) o[i] = A[i][6 + i].re;
         for (int i = 0; i < 6; i++)
             for (int j = i + 1; j < 6; j++) {
@@ -124,7 +182,37 @@ __global__ void k_inverse(long V, const double2 *__restrict__ C64, double mass, 
                 o[k] = 0.5 * (A[i][6 + j].re + A[j][6 + i].re);
                 o[k + 1] = 0.5 * (A[i][6 + j].im - A[j][6 + i].im);
             }
+    }
+}
+
+// A(m)^-1 = ((4 + m) + C_ch)^-1 per chirality in FP64 (LDL^dag, Gauss-Jordan if a pivot vanishes)
+__global__ void k_inverse(long V, const double2 *__restrict__ C64, double mass, double2 *A64, float4 *A32)
+{
+    long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+#pragma unroll 1
+    for (int ch = 0; ch < 2; ch++) {
+        double r[36];
+#pragma unroll
+        for (int k = 0; k < 18; k++) {
+            double2 v = C64[((long)ch * 18 + k) * V + s];
+            r[2 * k] = v.x;
+            r[2 * k + 1] = v.y;
+        }
+        double o[36];
+        if (!herm6_inverse_ldl(r, mass, o)) {
+            // rare: copies in local memory for the pivoting fallback, so that r and o stay in
+            // registers on the common path
+            double rr[36], oo[36];
+#pragma unroll
+            for (int k = 0; k < 36; k++) rr[k] = r[k];
+            herm6_inverse_gj(rr, mass, oo);
+#pragma unroll
+            for (int k = 0; k < 36; k++) o[k] = oo[k];
+        }
+#pragma unroll
         for (int k = 0; k < 18; k++) A64[((long)ch * 18 + k) * V + s] = make_double2(o[2 * k], o[2 * k + 1]);
+#pragma unroll
         for (int k = 0; k < 9; k++)
             A32[((long)ch * 9 + k) * V + s] =
                 make_float4((float)o[4 * k], (float)o[4 * k + 1], (float)o[4 * k + 2], (float)o[4 * k + 3]);
